@@ -1,0 +1,834 @@
+/*
+ * polypic_oracle.c -- plain, slow FP64 CPU oracle for the PolyPIC transfers.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls
+ * this file: only tests/, the smoke check and the CPU-baseline leg of the
+ * benchmark use it.  It shares no code, header, table or constant with the CUDA
+ * library; the two are written independently from the paper's equations.
+ *
+ * Paper: "Using The Polynomial Particle-in-Cell Method for Liquid-Fabric
+ * Interaction" (arXiv 2308.01060).
+ *
+ *   Section 3.1, Eqs 1-5   PIC particle-to-grid (P2G) of mass and momentum
+ *   Section 3.1, Eqs 6-8   PIC grid-to-particle (G2P), read per component
+ *   Section 3.2, Eqs 9-10  APIC transfer and its grad-w velocity derivative
+ *   Section 3.3, Eq 11     monomial modes s(z) = prod z_b^{i_b}
+ *   Section 3.3, Eq 12     affine map xi (optional here, flag `map`)
+ *   Section 3.3, Eq 13     PolyPIC P2G with N_r modes
+ *   Section 3.3, Eq 14     orthogonalised quadratic factor g_b
+ *   Section 3.4, Eqs 15-20 fluid and solid (absorbed-mass) transfers
+ *
+ * Everything is written the obvious way: loops over particles, grids and the
+ * 3x3x3 stencil nodes, every mode value s_r evaluated directly at every node,
+ * every least-squares denominator d_r summed directly as sum_i w_i s_r(z_i)^2.
+ * There is no sum factorisation, no blocking and no closed-form shortcut.
+ *
+ * Discrete decisions (a particle's cell, the lowest stencil node and the
+ * near-degenerate quadratic guard) are taken in FP32 from the FP32 position,
+ * exactly as the library documents them, so that both sides take the same
+ * decision; all arithmetic after the decision is FP64.
+ *
+ * Readings taken where the paper is silent or garbled (each also listed in
+ * the design doc):
+ *   - N(x) is the quadratic B-spline (Eq 14's dx^2/4 is its second moment).
+ *   - Eq 14's printed symbols are read as g(z) = z^2 - (mu3/mu2) z - mu2, the
+ *     Gram-Schmidt orthogonalisation of z^2 against {1, z} under the 1-D
+ *     B-spline weights (mu_n = sum_k w_k z_k^n), z = x_i - x_p.
+ *   - Modes are evaluated with the particle's current position (constant map)
+ *     unless `map` = 1, which applies Eq 12's affine map to the offsets.
+ *   - If q = 1 - 4t^2 < 2^-10 on an axis (t = particle offset from the middle
+ *     stencil node, in cells), the G2P fit sets the coefficient of every mode
+ *     with a quadratic factor on that axis to 0.
+ *   - Eqs 6-8 are read per component: v_pa = sum_i w_ipa v~_ia.
+ *   - Eq 20's denominator is the node total sum_p (m_s,p + m_abs,p) w_ipa.
+ *   - Advection is forward Euler with v_p = c_p0, clamped to
+ *     [1.5 dx, (n - 1.5) dx] per axis instead of deleting particles.
+ *
+ * Build: plain C99, -O2 -ffp-contract=off (no fused multiply-add, so the FP32
+ * decisions round exactly as documented).  Callers pass flat arrays.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG (-1)
+#define OR_ERR_DOMAIN (-2)
+#define OR_ERR_NOT_CONVERGED (-3)
+
+/* ------------------------------------------------------------------------ */
+/* Quadratic B-spline kernel N(r) and dN/dr (Section 3.1, w_ipa = N(x_p - x_ia)) */
+
+static double bspline2(double r)
+{
+    double a = fabs(r);
+    if (a < 0.5) return 0.75 - a * a;
+    if (a < 1.5) { double b = 1.5 - a; return 0.5 * b * b; }
+    return 0.0;
+}
+
+static double bspline2_deriv(double r)
+{
+    double a = fabs(r), sgn = r < 0.0 ? -1.0 : 1.0;
+    if (a < 0.5) return -2.0 * r;
+    if (a < 1.5) return -sgn * (1.5 - a);
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Canonical mode order (Eq 11 with the Eq 14 substitution): r <-> (a,b,c),
+ * the per-axis degrees along x, y, z.  r = 0: (000); r = 1..3: (100), (010),
+ * (001); r = 4..7: (110), (101), (011), (111); r = 8..26: the remaining
+ * triples with a 2 in them, in lexicographic order of (c, b, a).  Section 3.3
+ * counts the 2^d multilinear modes first, so N_r = 1, 4, 8, 27 are prefixes. */
+
+static int g_modes[27][3];
+static int g_modes_ready = 0;
+
+static void build_modes(void)
+{
+    if (g_modes_ready) return;
+    static const int first8[8][3] = {
+        {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1},
+        {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
+    int r = 0;
+    for (; r < 8; ++r) {
+        g_modes[r][0] = first8[r][0];
+        g_modes[r][1] = first8[r][1];
+        g_modes[r][2] = first8[r][2];
+    }
+    for (int c = 0; c < 3; ++c)
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a)
+                if (a == 2 || b == 2 || c == 2) {
+                    g_modes[r][0] = a; g_modes[r][1] = b; g_modes[r][2] = c;
+                    ++r;
+                }
+    g_modes_ready = 1;
+}
+
+void or_mode_abc(int r, int *abc)
+{
+    build_modes();
+    abc[0] = g_modes[r][0]; abc[1] = g_modes[r][1]; abc[2] = g_modes[r][2];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell key and stable sort (an implementation device; the paper has none).
+ *
+ * cell (i,j,k): i = clamp(floor(fl(x * inv_dx)), 0, n_x - 1) with the product
+ * rounded once in FP32 and inv_dx = (float)(1.0 / dx).
+ * key: tiles of 8x8x4 cells in row-major tile order, each tile split into
+ * 2x2x2 blocks of 4x4x2 cells, blocks in x-fastest order, cells in a block in
+ * x-fastest order:  key = tile*256 + block_in_tile*32 + cell_in_block.      */
+
+static float inv_dx_f32(double dx) { return (float)(1.0 / dx); }
+
+static int cell_of(float x, float inv_dx, int n)
+{
+    float v = x * inv_dx;
+    float f = floorf(v);
+    if (!(f >= 0.0f)) return 0;               /* also catches NaN */
+    if (f > (float)(n - 1)) return n - 1;
+    return (int)f;
+}
+
+uint32_t or_num_keys(int nx, int ny, int nz)
+{
+    uint32_t tx = (uint32_t)((nx + 7) / 8), ty = (uint32_t)((ny + 7) / 8), tz = (uint32_t)((nz + 3) / 4);
+    return tx * ty * tz * 256u;
+}
+
+uint32_t or_cell_key(int i, int j, int k, int nx, int ny)
+{
+    int tiles_x = (nx + 7) / 8, tiles_y = (ny + 7) / 8;
+    int tile = ((k / 4) * tiles_y + (j / 8)) * tiles_x + (i / 8);
+    int blk = ((i / 4) % 2) + 2 * ((j / 4) % 2) + 4 * ((k / 2) % 2);
+    int cell = (i % 4) + 4 * (j % 4) + 16 * (k % 2);
+    return (uint32_t)(tile * 256 + blk * 32 + cell);
+}
+
+void or_keys(int64_t np, const float *x, const float *y, const float *z,
+             int nx, int ny, int nz, double dx, uint32_t *key)
+{
+    float inv = inv_dx_f32(dx);
+    for (int64_t p = 0; p < np; ++p) {
+        int i = cell_of(x[p], inv, nx), j = cell_of(y[p], inv, ny), k = cell_of(z[p], inv, nz);
+        key[p] = or_cell_key(i, j, k, nx, ny);
+    }
+}
+
+/* Stable counting sort: perm[j] = index of the j-th particle in (key, index)
+ * order; cell_start[k] = first sorted slot with key >= k, cell_start[nkeys] = np. */
+void or_stable_sort(int64_t np, const uint32_t *key, uint32_t nkeys,
+                    uint32_t *perm, uint32_t *cell_start)
+{
+    memset(cell_start, 0, sizeof(uint32_t) * ((size_t)nkeys + 1));
+    for (int64_t p = 0; p < np; ++p) cell_start[key[p] + 1] += 1;
+    for (uint32_t k = 0; k < nkeys; ++k) cell_start[k + 1] += cell_start[k];
+    uint32_t *fill = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)nkeys + 1));
+    memcpy(fill, cell_start, sizeof(uint32_t) * ((size_t)nkeys + 1));
+    for (int64_t p = 0; p < np; ++p) perm[fill[key[p]]++] = (uint32_t)p;
+    free(fill);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One-axis stencil of a particle on one face grid.
+ *
+ * Face grid a holds velocity component a at ((i + o_x) dx, (j + o_y) dx,
+ * (k + o_z) dx) with o_b = 0 if b == a and 1/2 otherwise (the MAC grid of
+ * Section 3).  Along one axis the particle touches nodes base..base+2 where
+ * base = floor(X - 1/2), X = x/dx - o (FP32 decision).  Weights are
+ * N(X - node), offsets z = x_node - x_p.  The 1-D basis (Eq 11 with Eq 14):
+ * f0 = 1, f1 = z, f2 = z^2 - kappa z - mu2 with mu_n = sum_k w_k z_k^n and
+ * kappa = mu3/mu2 (Gram-Schmidt of z^2 against {1, z}; sum w = 1 and
+ * sum w z = 0 for this kernel, which the tests pin).                        */
+
+typedef struct {
+    int base;
+    double w[3], dw[3];   /* weights and dw/dx_p */
+    double z[3];          /* node - particle (physical) */
+    double mu2, kappa;    /* g(z) = z^2 - kappa z - mu2 */
+    double dmu2, dkappa;  /* derivatives w.r.t. x_p */
+    int guard;            /* 1: quadratic factor on this axis is suppressed in G2P */
+} axis_stencil;
+
+static void axis_stencil_eval(double xb, double dx, int face, axis_stencil *s)
+{
+    /* FP32 decisions, one rounding per operation */
+    float xf = (float)xb;
+    float v = xf * inv_dx_f32(dx);
+    float X32 = face ? v : v - 0.5f;
+    float fb = floorf(X32 - 0.5f);
+    float t32 = X32 - (fb + 1.0f);
+    float one_m = 1.0f - 2.0f * t32;
+    float one_p = 1.0f + 2.0f * t32;
+    float q32 = one_m * one_p;
+    s->base = (int)fb;
+    s->guard = q32 < 0x1p-10f ? 1 : 0;
+
+    /* FP64 arithmetic */
+    double X = xb / dx - (face ? 0.0 : 0.5);
+    double mu[5] = {0, 0, 0, 0, 0}, dmu[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+        double node = (double)(s->base + k);
+        s->w[k] = bspline2(X - node);
+        s->dw[k] = bspline2_deriv(X - node) / dx;
+        s->z[k] = (node - X) * dx;
+    }
+    for (int k = 0; k < 3; ++k) {
+        double zpow[4] = {1.0, s->z[k], s->z[k] * s->z[k], s->z[k] * s->z[k] * s->z[k]};
+        for (int n = 0; n < 4; ++n) {
+            mu[n] += s->w[k] * zpow[n];
+            /* d/dx_p of w z^n = dw z^n - n w z^(n-1), since dz/dx_p = -1 */
+            dmu[n] += s->dw[k] * zpow[n] - (n > 0 ? (double)n * s->w[k] * zpow[n - 1] : 0.0);
+        }
+    }
+    s->mu2 = mu[2];
+    s->kappa = mu[3] / mu[2];
+    s->dmu2 = dmu[2];
+    s->dkappa = (dmu[3] * mu[2] - mu[3] * dmu[2]) / (mu[2] * mu[2]);
+}
+
+/* f_a(z) and d f_a / d x_p for the particle's axis basis; z is the (possibly
+ * mapped) offset, dz its derivative w.r.t. x_p along this axis. */
+static double basis_f(const axis_stencil *s, int a, double z)
+{
+    if (a == 0) return 1.0;
+    if (a == 1) return z;
+    return z * z - s->kappa * z - s->mu2;
+}
+
+static double basis_df(const axis_stencil *s, int a, double z, double dz)
+{
+    if (a == 0) return 0.0;
+    if (a == 1) return dz;
+    return 2.0 * z * dz - s->dkappa * z - s->kappa * dz - s->dmu2;
+}
+
+/* Exposed for the pins: one axis of one particle. */
+int or_stencil_1d(double xb, double dx, int face, int *base, double *w, double *z,
+                  double *mu2, double *kappa, int *guard)
+{
+    axis_stencil s;
+    axis_stencil_eval(xb, dx, face, &s);
+    *base = s.base;
+    for (int k = 0; k < 3; ++k) { w[k] = s.w[k]; z[k] = s.z[k]; }
+    *mu2 = s.mu2; *kappa = s.kappa; *guard = s.guard;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+
+static int in_domain(double x, double y, double zc, int nx, int ny, int nz, double dx)
+{
+    float inv = inv_dx_f32(dx);
+    float vx = (float)x * inv, vy = (float)y * inv, vz = (float)zc * inv;
+    return vx >= 1.0f && vx < (float)(nx - 1) &&
+           vy >= 1.0f && vy < (float)(ny - 1) &&
+           vz >= 1.0f && vz < (float)(nz - 1);
+}
+
+static void face_dims(int alpha, int nx, int ny, int nz, int d[3])
+{
+    d[0] = nx + (alpha == 0);
+    d[1] = ny + (alpha == 1);
+    d[2] = nz + (alpha == 2);
+}
+
+/* Particle p on face grid alpha: its three axis stencils. */
+static void particle_stencils(double px, double py, double pz, int alpha, double dx,
+                              axis_stencil st[3])
+{
+    axis_stencil_eval(px, dx, alpha == 0, &st[0]);
+    axis_stencil_eval(py, dx, alpha == 1, &st[1]);
+    axis_stencil_eval(pz, dx, alpha == 2, &st[2]);
+}
+
+/* Mode value s_r at offset z (3 components), Eq 11 with g from Eq 14. */
+static double mode_value(const axis_stencil st[3], int r, const double zz[3])
+{
+    return basis_f(&st[0], g_modes[r][0], zz[0]) *
+           basis_f(&st[1], g_modes[r][1], zz[1]) *
+           basis_f(&st[2], g_modes[r][2], zz[2]);
+}
+
+/* Affine map of Eq 12 applied to the node offset: z' = (I + dt C)^-1 z, with
+ * C_ab = coefficient of mode z_b for component a (the linear modes r = 1..3).
+ * Falls back to the identity when |det(I + dt C)| < 1e-6.                  */
+static void affine_matrix(const double *coeff, int R, int64_t np, int64_t p, double dt, double M[3][3])
+{
+    double A[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double c = (R >= 4) ? coeff[((int64_t)a * R + 1 + b) * np + p] : 0.0;
+            A[a][b] = (a == b ? 1.0 : 0.0) + dt * c;
+        }
+    double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1])
+               - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
+               + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (fabs(det) < 1e-6) {
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) M[a][b] = (a == b);
+        return;
+    }
+    M[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / det;
+    M[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / det;
+    M[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / det;
+    M[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / det;
+    M[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / det;
+    M[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / det;
+    M[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / det;
+    M[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / det;
+    M[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / det;
+}
+
+/* Exposed for the pins: nodes, weights, mode values and the least-squares
+ * denominators d_r = sum_i w_i s_r(z_i)^2 of one particle on grid alpha.
+ * node: [27][3], w: [27], s: [27][R], d: [R], guard: [3].                   */
+int or_particle_modes(double px, double py, double pz, int alpha, int R,
+                      double dx, int *node, double *w, double *s, double *d, int *guard)
+{
+    build_modes();
+    axis_stencil st[3];
+    particle_stencils(px, py, pz, alpha, dx, st);
+    for (int r = 0; r < R; ++r) d[r] = 0.0;
+    int n = 0;
+    for (int kz = 0; kz < 3; ++kz)
+        for (int ky = 0; ky < 3; ++ky)
+            for (int kx = 0; kx < 3; ++kx, ++n) {
+                double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
+                node[3 * n + 0] = st[0].base + kx;
+                node[3 * n + 1] = st[1].base + ky;
+                node[3 * n + 2] = st[2].base + kz;
+                w[n] = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
+                for (int r = 0; r < R; ++r) {
+                    s[n * R + r] = mode_value(st, r, zz);
+                    d[r] += w[n] * s[n * R + r] * s[n * R + r];
+                }
+            }
+    for (int b = 0; b < 3; ++b) guard[b] = st[b].guard;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* P2G: Eqs 1, 4 (mass), Eq 13 (PolyPIC momentum), Eqs 15-18 (phase masses).
+ *   m_ia  += mt_p w_ipa
+ *   mv_ia += mt_p w_ipa sum_{r<R} c_pra s_r(z_ipa)
+ * mt_p = mass[p] (+ mass_abs[p] for solids, Eq 18).  Grids are zeroed first.
+ * coeff: [3][R][np].  Grid a has dims face_dims(a), x fastest.
+ * Returns OR_ERR_DOMAIN if a particle lies outside [dx, (n-1) dx).          */
+int or_p2g(int64_t np, const double *x, const double *y, const double *z,
+           const double *mass, const double *mass_abs, const double *coeff, int R,
+           int nx, int ny, int nz, double dx, int map, double dt,
+           double *gm0, double *gm1, double *gm2, double *gp0, double *gp1, double *gp2)
+{
+    build_modes();
+    if (R != 1 && R != 4 && R != 8 && R != 27) return OR_ERR_ARG;
+    double *gm[3] = {gm0, gm1, gm2}, *gp[3] = {gp0, gp1, gp2};
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        size_t cnt = (size_t)d[0] * d[1] * d[2];
+        memset(gm[a], 0, cnt * sizeof(double));
+        memset(gp[a], 0, cnt * sizeof(double));
+    }
+    for (int64_t p = 0; p < np; ++p)
+        if (!in_domain(x[p], y[p], z[p], nx, ny, nz, dx)) return OR_ERR_DOMAIN;
+
+    for (int64_t p = 0; p < np; ++p) {
+        double mt = mass[p] + (mass_abs ? mass_abs[p] : 0.0);
+        double M[3][3];
+        if (map == 1) affine_matrix(coeff, R, np, p, dt, M);
+        for (int a = 0; a < 3; ++a) {
+            int d[3]; face_dims(a, nx, ny, nz, d);
+            axis_stencil st[3];
+            particle_stencils(x[p], y[p], z[p], a, dx, st);
+            for (int kz = 0; kz < 3; ++kz)
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx) {
+                        double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
+                        double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
+                        if (map == 1) {
+                            double zm[3];
+                            for (int i = 0; i < 3; ++i)
+                                zm[i] = M[i][0] * zz[0] + M[i][1] * zz[1] + M[i][2] * zz[2];
+                            zz[0] = zm[0]; zz[1] = zm[1]; zz[2] = zm[2];
+                        }
+                        double S = 0.0;
+                        for (int r = 0; r < R; ++r)
+                            S += coeff[((int64_t)a * R + r) * np + p] * mode_value(st, r, zz);
+                        int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
+                        size_t idx = ((size_t)iz * d[1] + iy) * d[0] + ix;
+                        gm[a][idx] += mt * w;
+                        gp[a][idx] += mt * w * S;
+                    }
+        }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid update (the paper delegates it to the host simulator; the stated
+ * minimal form):  v = mv/m where m > 0, else 0 (Eq 5); v~ = v + dt g_a;
+ * with a solid grid, implicit two-phase drag on faces where both masses are
+ * positive: u' = u / (1 + dt K (1/m_f + 1/m_s)) for u = v_f - v_s, keeping
+ * the mass-weighted mean; then v~_a = 0 on the wall faces i_a in {0, n_a}.   */
+static void wall_zero(int a, const int d[3], double *v)
+{
+    for (int k = 0; k < d[2]; ++k)
+        for (int j = 0; j < d[1]; ++j)
+            for (int i = 0; i < d[0]; ++i) {
+                int ia = (a == 0) ? i : (a == 1) ? j : k;
+                if (ia == 0 || ia == d[a] - 1) v[((size_t)k * d[1] + j) * d[0] + i] = 0.0;
+            }
+}
+
+void or_grid_update(int nx, int ny, int nz, double dt, double gx, double gy, double gz,
+                    double drag_k,
+                    const double *fm0, const double *fm1, const double *fm2,
+                    const double *fp0, const double *fp1, const double *fp2,
+                    double *fv0, double *fv1, double *fv2,
+                    const double *sm0, const double *sm1, const double *sm2,
+                    const double *sp0, const double *sp1, const double *sp2,
+                    double *sv0, double *sv1, double *sv2)
+{
+    const double *fm[3] = {fm0, fm1, fm2}, *fp[3] = {fp0, fp1, fp2};
+    const double *sm[3] = {sm0, sm1, sm2}, *sp[3] = {sp0, sp1, sp2};
+    double *fv[3] = {fv0, fv1, fv2}, *sv[3] = {sv0, sv1, sv2};
+    double g[3] = {gx, gy, gz};
+    int solid = sm0 != NULL;
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        size_t cnt = (size_t)d[0] * d[1] * d[2];
+        for (size_t i = 0; i < cnt; ++i) {
+            double vf = fm[a][i] > 0.0 ? fp[a][i] / fm[a][i] : 0.0;
+            vf += dt * g[a];
+            if (solid) {
+                double vs = sm[a][i] > 0.0 ? sp[a][i] / sm[a][i] : 0.0;
+                vs += dt * g[a];
+                if (fm[a][i] > 0.0 && sm[a][i] > 0.0 && drag_k > 0.0) {
+                    double mf = fm[a][i], ms = sm[a][i];
+                    double mean = (mf * vf + ms * vs) / (mf + ms);
+                    double u = (vf - vs) / (1.0 + dt * drag_k * (1.0 / mf + 1.0 / ms));
+                    vf = mean + ms / (mf + ms) * u;
+                    vs = mean - mf / (mf + ms) * u;
+                }
+                sv[a][i] = vs;
+            }
+            fv[a][i] = vf;
+        }
+        wall_zero(a, d, fv[a]);
+        if (solid) wall_zero(a, d, sv[a]);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* G2P: Eqs 6-8 per component plus the PolyPIC fit (Section 3.3, decoupled
+ * least squares over an orthogonal basis):
+ *   c_pra = sum_i w_ipa s_r(z_ipa) v~_ia / d_r,   d_r = sum_i w_ipa s_r^2,
+ * with the guard; v_pa = c_p0a; x_p <- clamp(x_p + dt v_p, 1.5dx, (n-1.5)dx).
+ * apic_grad = 1 (R = 4 only) replaces the linear modes by Eq 10:
+ *   c_p(1+b)a = sum_i (d w_ipa / d x_pb) v~_ia.
+ * coeff_out: [3][R][np]; positions written to xo, yo, zo (may alias nothing). */
+int or_g2p(int64_t np, const double *x, const double *y, const double *z,
+           const double *gv0, const double *gv1, const double *gv2, int R,
+           int nx, int ny, int nz, double dx, double dt, int apic_grad,
+           double *coeff_out, double *xo, double *yo, double *zo)
+{
+    build_modes();
+    if (R != 1 && R != 4 && R != 8 && R != 27) return OR_ERR_ARG;
+    if (apic_grad && R != 4) return OR_ERR_ARG;
+    const double *gv[3] = {gv0, gv1, gv2};
+    for (int64_t p = 0; p < np; ++p)
+        if (!in_domain(x[p], y[p], z[p], nx, ny, nz, dx)) return OR_ERR_DOMAIN;
+    int n3[3] = {nx, ny, nz};
+    for (int64_t p = 0; p < np; ++p) {
+        double pos[3] = {x[p], y[p], z[p]};
+        double vp[3];
+        for (int a = 0; a < 3; ++a) {
+            int d[3]; face_dims(a, nx, ny, nz, d);
+            axis_stencil st[3];
+            particle_stencils(x[p], y[p], z[p], a, dx, st);
+            double num[27], den[27], gradw[3] = {0, 0, 0};
+            for (int r = 0; r < R; ++r) { num[r] = 0.0; den[r] = 0.0; }
+            for (int kz = 0; kz < 3; ++kz)
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx) {
+                        double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
+                        double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
+                        int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
+                        double v = gv[a][((size_t)iz * d[1] + iy) * d[0] + ix];
+                        for (int r = 0; r < R; ++r) {
+                            double s = mode_value(st, r, zz);
+                            num[r] += w * s * v;
+                            den[r] += w * s * s;
+                        }
+                        if (apic_grad) {
+                            gradw[0] += st[0].dw[kx] * st[1].w[ky] * st[2].w[kz] * v;
+                            gradw[1] += st[0].w[kx] * st[1].dw[ky] * st[2].w[kz] * v;
+                            gradw[2] += st[0].w[kx] * st[1].w[ky] * st[2].dw[kz] * v;
+                        }
+                    }
+            for (int r = 0; r < R; ++r) {
+                int guarded = (g_modes[r][0] == 2 && st[0].guard) ||
+                              (g_modes[r][1] == 2 && st[1].guard) ||
+                              (g_modes[r][2] == 2 && st[2].guard);
+                double c = guarded ? 0.0 : num[r] / den[r];
+                if (apic_grad && r >= 1) c = gradw[r - 1];
+                coeff_out[((int64_t)a * R + r) * np + p] = c;
+            }
+            vp[a] = coeff_out[((int64_t)a * R + 0) * np + p];
+        }
+        double out[3];
+        for (int a = 0; a < 3; ++a) {
+            double lo = 1.5 * dx, hi = ((double)n3[a] - 1.5) * dx;
+            double xn = pos[a] + dt * vp[a];
+            out[a] = xn < lo ? lo : (xn > hi ? hi : xn);
+        }
+        xo[p] = out[0]; yo[p] = out[1]; zo[p] = out[2];
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoints (transposes of the steps above, constant map, FP64).
+ *
+ * P2G adjoint.  Given lm_a = dL/dm_ia and lp_a = dL/d(mv)_ia on the three
+ * grids, writes lc = dL/dc_pra ([3][R][np]) and adds the position terms to
+ * lx, ly, lz (which the caller zeroes or pre-loads):
+ *   dL/dc_pra  = mt_p sum_i w s_r lp_ia
+ *   dL/dx_pb  += mt_p sum_{a,i} [dw/dx_b (S lp + lm) + w sum_r c_r ds_r/dx_b lp]  */
+int or_p2g_adjoint(int64_t np, const double *x, const double *y, const double *z,
+                   const double *mass, const double *mass_abs, const double *coeff, int R,
+                   int nx, int ny, int nz, double dx,
+                   const double *lm0, const double *lm1, const double *lm2,
+                   const double *lp0, const double *lp1, const double *lp2,
+                   double *lc, double *lx, double *ly, double *lz)
+{
+    build_modes();
+    if (R != 1 && R != 4 && R != 8 && R != 27) return OR_ERR_ARG;
+    const double *lm[3] = {lm0, lm1, lm2}, *lp[3] = {lp0, lp1, lp2};
+    double *lpos[3] = {lx, ly, lz};
+    for (int64_t p = 0; p < np; ++p)
+        if (!in_domain(x[p], y[p], z[p], nx, ny, nz, dx)) return OR_ERR_DOMAIN;
+    for (int64_t p = 0; p < np; ++p) {
+        double mt = mass[p] + (mass_abs ? mass_abs[p] : 0.0);
+        for (int a = 0; a < 3; ++a) {
+            int d[3]; face_dims(a, nx, ny, nz, d);
+            axis_stencil st[3];
+            particle_stencils(x[p], y[p], z[p], a, dx, st);
+            double acc_c[27];
+            for (int r = 0; r < R; ++r) acc_c[r] = 0.0;
+            for (int kz = 0; kz < 3; ++kz)
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx) {
+                        int k3[3] = {kx, ky, kz};
+                        double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
+                        double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
+                        int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
+                        size_t idx = ((size_t)iz * d[1] + iy) * d[0] + ix;
+                        double LP = lp[a][idx], LM = lm[a][idx];
+                        double S = 0.0;
+                        for (int r = 0; r < R; ++r) {
+                            double s = mode_value(st, r, zz);
+                            S += coeff[((int64_t)a * R + r) * np + p] * s;
+                            acc_c[r] += mt * w * s * LP;
+                        }
+                        for (int b = 0; b < 3; ++b) {
+                            double dwb = 1.0;
+                            for (int e = 0; e < 3; ++e)
+                                dwb *= (e == b) ? st[e].dw[k3[e]] : st[e].w[k3[e]];
+                            double dS = 0.0;
+                            for (int r = 0; r < R; ++r) {
+                                double ds = 1.0;
+                                for (int e = 0; e < 3; ++e) {
+                                    int deg = g_modes[r][e];
+                                    ds *= (e == b) ? basis_df(&st[e], deg, zz[e], -1.0)
+                                                   : basis_f(&st[e], deg, zz[e]);
+                                }
+                                dS += coeff[((int64_t)a * R + r) * np + p] * ds;
+                            }
+                            lpos[b][p] += mt * (dwb * (S * LP + LM) + w * dS * LP);
+                        }
+                    }
+            for (int r = 0; r < R; ++r) lc[((int64_t)a * R + r) * np + p] = acc_c[r];
+        }
+    }
+    return OR_OK;
+}
+
+/* Grid-update adjoint (single phase, no drag): given lv_a = dL/dv~_ia,
+ * writes lm_a = dL/dm_ia and lp_a = dL/d(mv)_ia.  Wall faces and faces with
+ * m = 0 pass no gradient.                                                    */
+void or_grid_update_adjoint(int nx, int ny, int nz,
+                            const double *fm0, const double *fm1, const double *fm2,
+                            const double *fp0, const double *fp1, const double *fp2,
+                            const double *lv0, const double *lv1, const double *lv2,
+                            double *lm0, double *lm1, double *lm2,
+                            double *lp0, double *lp1, double *lp2)
+{
+    const double *fm[3] = {fm0, fm1, fm2}, *fp[3] = {fp0, fp1, fp2}, *lv[3] = {lv0, lv1, lv2};
+    double *lm[3] = {lm0, lm1, lm2}, *lp[3] = {lp0, lp1, lp2};
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        for (int k = 0; k < d[2]; ++k)
+            for (int j = 0; j < d[1]; ++j)
+                for (int i = 0; i < d[0]; ++i) {
+                    size_t idx = ((size_t)k * d[1] + j) * d[0] + i;
+                    int ia = (a == 0) ? i : (a == 1) ? j : k;
+                    int wall = (ia == 0 || ia == d[a] - 1);
+                    double m = fm[a][idx];
+                    if (wall || !(m > 0.0)) { lm[a][idx] = 0.0; lp[a][idx] = 0.0; continue; }
+                    lp[a][idx] = lv[a][idx] / m;
+                    lm[a][idx] = -lv[a][idx] * fp[a][idx] / (m * m);
+                }
+    }
+}
+
+/* G2P adjoint with the advection.  Given lc_out = dL/dc'_pra ([3][R][np]) and
+ * lxo = dL/dx'_p, adds dL/dv~_ia to lv0..2 (the caller zeroes them) and adds
+ * dL/dx_p to lx, ly, lz.  Clamped axes pass no gradient through the advection. */
+int or_g2p_adjoint(int64_t np, const double *x, const double *y, const double *z,
+                   const double *gv0, const double *gv1, const double *gv2, int R,
+                   int nx, int ny, int nz, double dx, double dt,
+                   const double *lc_out, const double *lxo, const double *lyo, const double *lzo,
+                   double *lv0, double *lv1, double *lv2,
+                   double *lx, double *ly, double *lz)
+{
+    build_modes();
+    if (R != 1 && R != 4 && R != 8 && R != 27) return OR_ERR_ARG;
+    const double *gv[3] = {gv0, gv1, gv2};
+    double *lv[3] = {lv0, lv1, lv2};
+    const double *lpo[3] = {lxo, lyo, lzo};
+    double *lpos[3] = {lx, ly, lz};
+    int n3[3] = {nx, ny, nz};
+    for (int64_t p = 0; p < np; ++p)
+        if (!in_domain(x[p], y[p], z[p], nx, ny, nz, dx)) return OR_ERR_DOMAIN;
+    for (int64_t p = 0; p < np; ++p) {
+        double pos[3] = {x[p], y[p], z[p]};
+        for (int a = 0; a < 3; ++a) {
+            int d[3]; face_dims(a, nx, ny, nz, d);
+            axis_stencil st[3];
+            particle_stencils(x[p], y[p], z[p], a, dx, st);
+            /* forward quantities: num_r, den_r and their x-derivatives */
+            double num[27], den[27], dnum[27][3], dden[27][3];
+            for (int r = 0; r < R; ++r) {
+                num[r] = den[r] = 0.0;
+                for (int b = 0; b < 3; ++b) dnum[r][b] = dden[r][b] = 0.0;
+            }
+            for (int kz = 0; kz < 3; ++kz)
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx) {
+                        int k3[3] = {kx, ky, kz};
+                        double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
+                        double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
+                        int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
+                        double v = gv[a][((size_t)iz * d[1] + iy) * d[0] + ix];
+                        for (int r = 0; r < R; ++r) {
+                            double s = mode_value(st, r, zz);
+                            num[r] += w * s * v;
+                            den[r] += w * s * s;
+                            for (int b = 0; b < 3; ++b) {
+                                double dwb = 1.0, ds = 1.0;
+                                for (int e = 0; e < 3; ++e) {
+                                    dwb *= (e == b) ? st[e].dw[k3[e]] : st[e].w[k3[e]];
+                                    int deg = g_modes[r][e];
+                                    ds *= (e == b) ? basis_df(&st[e], deg, zz[e], -1.0)
+                                                   : basis_f(&st[e], deg, zz[e]);
+                                }
+                                dnum[r][b] += (dwb * s + w * ds) * v;
+                                dden[r][b] += dwb * s * s + 2.0 * w * s * ds;
+                            }
+                        }
+                    }
+            /* adjoint seed on the output coefficients, plus advection */
+            double mu[27];
+            for (int r = 0; r < R; ++r) mu[r] = lc_out[((int64_t)a * R + r) * np + p];
+            double c0 = num[0] / den[0];
+            double lo = 1.5 * dx, hi = ((double)n3[a] - 1.5) * dx;
+            double xn = pos[a] + dt * c0;
+            if (xn >= lo && xn <= hi) {
+                mu[0] += dt * lpo[a][p];
+                lpos[a][p] += lpo[a][p];
+            }
+            for (int r = 0; r < R; ++r) {
+                int guarded = (g_modes[r][0] == 2 && st[0].guard) ||
+                              (g_modes[r][1] == 2 && st[1].guard) ||
+                              (g_modes[r][2] == 2 && st[2].guard);
+                if (guarded || mu[r] == 0.0) continue;
+                double c = num[r] / den[r];
+                for (int b = 0; b < 3; ++b)
+                    lpos[b][p] += mu[r] * (dnum[r][b] - c * dden[r][b]) / den[r];
+            }
+            for (int kz = 0; kz < 3; ++kz)
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx) {
+                        double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
+                        double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
+                        int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
+                        double acc = 0.0;
+                        for (int r = 0; r < R; ++r) {
+                            int guarded = (g_modes[r][0] == 2 && st[0].guard) ||
+                                          (g_modes[r][1] == 2 && st[1].guard) ||
+                                          (g_modes[r][2] == 2 && st[2].guard);
+                            if (guarded) continue;
+                            acc += mu[r] * w * mode_value(st, r, zz) / den[r];
+                        }
+                        lv[a][((size_t)iz * d[1] + iy) * d[0] + ix] += acc;
+                    }
+        }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pressure projection (delegated to the host simulator in the paper; the
+ * stated minimal form): cell-centred pressure on fluid cells (fluid[c] != 0),
+ * p = 0 in non-fluid cells, zero normal velocity at the walls.  For a fluid
+ * cell c:  sum_{non-wall neighbours n} (p_c - p_n) = -(rho dx^2 / dt) div_c,
+ * div_c = sum_a (v_a(c + e_a) - v_a(c)) / dx.  Solved by Jacobi-preconditioned
+ * CG to ||r|| <= rtol ||b||; then v_a -= dt/(rho dx) (p_right - p_left) on
+ * every non-wall face with a fluid cell on at least one side.  Returns the
+ * iteration count, or OR_ERR_NOT_CONVERGED.                                */
+int or_pcg_project(int nx, int ny, int nz, double dx, double dt, double rho,
+                   const uint8_t *fluid, double *v0, double *v1, double *v2,
+                   double *pressure, double rtol, int maxiter)
+{
+    double *v[3] = {v0, v1, v2};
+    int n3[3] = {nx, ny, nz};
+    size_t nc = (size_t)nx * ny * nz;
+    double *b = calloc(nc, sizeof(double)), *r = calloc(nc, sizeof(double));
+    double *zv = calloc(nc, sizeof(double)), *pd = calloc(nc, sizeof(double));
+    double *Ap = calloc(nc, sizeof(double)), *diag = calloc(nc, sizeof(double));
+#define CIDX(i, j, k) (((size_t)(k) * ny + (j)) * nx + (i))
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = CIDX(i, j, k);
+                pressure[c] = 0.0;
+                if (!fluid[c]) continue;
+                int ijk[3] = {i, j, k};
+                double div = 0.0;
+                int nn = 0;
+                for (int a = 0; a < 3; ++a) {
+                    int d[3]; face_dims(a, nx, ny, nz, d);
+                    int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                    hi[a] += 1;
+                    double vl = v[a][((size_t)lo[2] * d[1] + lo[1]) * d[0] + lo[0]];
+                    double vh = v[a][((size_t)hi[2] * d[1] + hi[1]) * d[0] + hi[0]];
+                    div += (vh - vl) / dx;
+                    if (ijk[a] > 0) nn++;
+                    if (ijk[a] < n3[a] - 1) nn++;
+                }
+                b[c] = -(rho * dx * dx / dt) * div;
+                diag[c] = (double)nn;
+            }
+    /* A p for fluid cells */
+#define APPLY(src, dst)                                                          \
+    for (int k = 0; k < nz; ++k)                                                 \
+        for (int j = 0; j < ny; ++j)                                             \
+            for (int i = 0; i < nx; ++i) {                                       \
+                size_t c = CIDX(i, j, k);                                        \
+                if (!fluid[c]) { dst[c] = 0.0; continue; }                       \
+                double s = diag[c] * src[c];                                     \
+                if (i > 0 && fluid[CIDX(i - 1, j, k)]) s -= src[CIDX(i - 1, j, k)]; \
+                if (i < nx - 1 && fluid[CIDX(i + 1, j, k)]) s -= src[CIDX(i + 1, j, k)]; \
+                if (j > 0 && fluid[CIDX(i, j - 1, k)]) s -= src[CIDX(i, j - 1, k)]; \
+                if (j < ny - 1 && fluid[CIDX(i, j + 1, k)]) s -= src[CIDX(i, j + 1, k)]; \
+                if (k > 0 && fluid[CIDX(i, j, k - 1)]) s -= src[CIDX(i, j, k - 1)]; \
+                if (k < nz - 1 && fluid[CIDX(i, j, k + 1)]) s -= src[CIDX(i, j, k + 1)]; \
+                dst[c] = s;                                                      \
+            }
+    double bnorm = 0.0;
+    for (size_t c = 0; c < nc; ++c) { r[c] = b[c]; bnorm += b[c] * b[c]; }
+    bnorm = sqrt(bnorm);
+    int it = 0, converged = bnorm == 0.0;
+    double rz = 0.0;
+    for (size_t c = 0; c < nc; ++c) {
+        zv[c] = fluid[c] ? r[c] / diag[c] : 0.0;
+        pd[c] = zv[c];
+        rz += r[c] * zv[c];
+    }
+    while (!converged && it < maxiter) {
+        APPLY(pd, Ap);
+        double pAp = 0.0;
+        for (size_t c = 0; c < nc; ++c) pAp += pd[c] * Ap[c];
+        double alpha = rz / pAp;
+        double rn = 0.0;
+        for (size_t c = 0; c < nc; ++c) {
+            pressure[c] += alpha * pd[c];
+            r[c] -= alpha * Ap[c];
+            rn += r[c] * r[c];
+        }
+        ++it;
+        if (sqrt(rn) <= rtol * bnorm) { converged = 1; break; }
+        double rz_new = 0.0;
+        for (size_t c = 0; c < nc; ++c) {
+            zv[c] = fluid[c] ? r[c] / diag[c] : 0.0;
+            rz_new += r[c] * zv[c];
+        }
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (size_t c = 0; c < nc; ++c) pd[c] = zv[c] + beta * pd[c];
+    }
+    /* velocity update on interior faces touching a fluid cell */
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        for (int k = 0; k < d[2]; ++k)
+            for (int j = 0; j < d[1]; ++j)
+                for (int i = 0; i < d[0]; ++i) {
+                    int f[3] = {i, j, k};
+                    if (f[a] == 0 || f[a] == n3[a]) continue;
+                    int lo[3] = {i, j, k};
+                    lo[a] -= 1;
+                    size_t cl = CIDX(lo[0], lo[1], lo[2]), ch = CIDX(i, j, k);
+                    if (!fluid[cl] && !fluid[ch]) continue;
+                    v[a][((size_t)k * d[1] + j) * d[0] + i] -=
+                        dt / (rho * dx) * (pressure[ch] - pressure[cl]);
+                }
+    }
+#undef APPLY
+#undef CIDX
+    free(b); free(r); free(zv); free(pd); free(Ap); free(diag);
+    return converged ? it : OR_ERR_NOT_CONVERGED;
+}

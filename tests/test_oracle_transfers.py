@@ -1,0 +1,503 @@
+"""Pins of the oracle's transfers against what the paper and the mathematics fix
+(host only, no GPU).
+
+  * stable sort == numpy's stable argsort; key layout properties
+  * P2G conserves mass and linear momentum (Eqs 1-5, 13)
+  * round-trips: constant / affine / multilinear / triquadratic / arbitrary
+    fields are reproduced by G2P then P2G for the mode counts that span them
+    (Section 3.3; the lossless claim of the abstract and Section 5)
+  * N_r = 1 is PIC (Eqs 1-8) and N_r = 4 is APIC with B_p D_p^-1 (Eq 9),
+    both written independently below
+  * brute-force all-pairs evaluation on tiny grids
+  * free fall, energy non-increase, adjoint identities, two-phase drag,
+    absorbed mass (Eqs 18-20), pressure projection
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import bruteforce
+from paper_2308_01060_gb300 import scenes
+
+
+def _safe_positions(rng, P, n, lo=3, hi=None, eps=0.06):
+    """Positions whose fractional cell offset avoids the degenerate bands of
+    both grid offsets (frac near 0 or near 1/2), so no guard fires."""
+    hi = (n - 3) if hi is None else hi
+    out = []
+    while len(out) < P:
+        v = rng.uniform(lo, hi, size=3)
+        f = v - np.floor(v)
+        if np.all((np.abs(f - 0.5) > eps) & (f > eps) & (f < 1 - eps)):
+            out.append(v)
+    return np.array(out).T / n
+
+
+def _modes(R):
+    return [oracle.mode_abc(r) for r in range(R)]
+
+
+# --------------------------------------------------------------------- sort
+
+def test_stable_sort_matches_numpy():
+    rng = np.random.default_rng(0)
+    n = (16, 24, 12)
+    dx = 1.0 / 16
+    x = np.stack([rng.uniform(0, n[b] * dx, 5000) for b in range(3)]).astype(np.float32)
+    key = oracle.keys(x, n, dx)
+    nk = oracle.num_keys(n)
+    perm, cs = oracle.stable_sort(key, nk)
+    assert np.array_equal(perm, np.argsort(key, kind="stable").astype(np.uint32))
+    assert np.array_equal(cs, np.searchsorted(np.sort(key), np.arange(nk + 1)).astype(np.uint32))
+
+
+def test_key_layout_blocks_and_tiles():
+    """The key is a bijection on cells; each 4x4x2 block and each 8x8x4 tile
+    occupies one contiguous key range; tiles follow in row-major order."""
+    n = (16, 16, 8)
+    nk = oracle.num_keys(n)
+    keys = {}
+    for i, j, k in itertools.product(range(n[0]), range(n[1]), range(n[2])):
+        keys[(i, j, k)] = oracle.cell_key(i, j, k, n)
+    assert len(set(keys.values())) == len(keys)
+    assert max(keys.values()) < nk
+    for bi, bj, bk in itertools.product(range(4), range(4), range(4)):
+        ks = sorted(keys[(4 * bi + a, 4 * bj + b, 2 * bk + c)]
+                    for a in range(4) for b in range(4) for c in range(2))
+        assert ks == list(range(ks[0], ks[0] + 32)) and ks[0] % 32 == 0
+    for ti, tj, tk in itertools.product(range(2), range(2), range(2)):
+        ks = sorted(keys[(8 * ti + a, 8 * tj + b, 4 * tk + c)]
+                    for a in range(8) for b in range(8) for c in range(4))
+        assert ks[0] == 256 * ((tk * 2 + tj) * 2 + ti)
+        assert ks == list(range(ks[0], ks[0] + 256))
+
+
+def test_key_uses_fp32_product():
+    n = (32, 32, 32)
+    dx = 1.0 / 32
+    x = np.array([[np.nextafter(np.float32(0.5), np.float32(0))], [0.3], [0.3]], np.float32)
+    key = oracle.keys(x, n, dx)
+    i = int(np.floor(np.float32(x[0, 0] * np.float32(32.0))))
+    assert key[0] == oracle.cell_key(i, 9, 9, n)
+
+
+# --------------------------------------------------------------------- P2G
+
+@pytest.mark.parametrize("R", [1, 4, 8, 27])
+def test_p2g_conserves_mass_and_momentum(R):
+    sc = scenes.parity_scene(n=16, R=R, seed=3, random_mode_init=True)
+    f = sc.fluid
+    gm, gp = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx)
+    msum = f.mass.astype(np.float64).sum()
+    for a in range(3):
+        assert abs(gm[a].sum() - msum) <= 1e-13 * msum
+        mom = np.dot(f.mass.astype(np.float64), f.coeff[a, 0].astype(np.float64))
+        scale = np.dot(f.mass.astype(np.float64), np.abs(f.coeff[a, 0].astype(np.float64)))
+        assert abs(gp[a].sum() - mom) <= 1e-12 * scale
+
+
+def test_p2g_absorbed_mass_eq18_20():
+    """Eq 18: solid momentum weight is m_s + m_abs; Eq 20: its velocity divides
+    by the node total of (m_s + m_abs) w."""
+    sc = scenes.parity_scene(n=12, R=8, seed=4, random_mode_init=True)
+    f = sc.fluid
+    mabs = np.random.default_rng(0).uniform(0, 2, f.n).astype(np.float32) * f.mass
+    gm1, gp1 = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx, mass_abs=mabs)
+    gm2, gp2 = oracle.p2g(f.x, f.mass.astype(np.float64) + mabs, f.coeff, sc.n, sc.dx)
+    for a in range(3):
+        assert np.allclose(gm1[a], gm2[a], rtol=1e-14, atol=0)
+        assert np.allclose(gp1[a], gp2[a], rtol=1e-13, atol=1e-18)
+    gv = oracle.grid_update(sc.n, 0.0, (0, 0, 0), gm1, gp1)
+    for a in range(3):
+        sel = gm1[a] > 0
+        idx = [slice(None)] * 3
+        idx[2 - a] = slice(1, -1)
+        inside = np.zeros_like(sel)
+        inside[tuple(idx)] = True
+        sel &= inside
+        assert np.allclose(gv[a][sel], gp1[a][sel] / gm1[a][sel], rtol=1e-14)
+
+
+def test_bruteforce_matches_stencil_oracle():
+    rng = np.random.default_rng(5)
+    n = (6, 6, 6)
+    dx = 1 / 6
+    for R in (1, 4, 8, 27):
+        P = 12
+        x = _safe_positions(rng, P, 6, lo=1.1, hi=4.9)
+        mass = rng.uniform(0.5, 1.5, P)
+        deg = scenes.mode_degrees(R)
+        coeff = rng.standard_normal((3, R, P)) / (dx ** deg)[None, :, None]
+        gm, gp = oracle.p2g(x, mass, coeff, n, dx)
+        bm, bp = bruteforce.p2g(x, mass, coeff, n, dx, _modes(R))
+        for a in range(3):
+            assert np.allclose(gm[a], bm[a], rtol=1e-13, atol=1e-15)
+            assert np.allclose(gp[a], bp[a], rtol=1e-12, atol=1e-12 * np.abs(bp[a]).max())
+        gv = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+        c, _ = oracle.g2p(x, gv, R, n, dx, 0.0)
+        cb = bruteforce.g2p_fit(x, gv, n, dx, _modes(R))
+        assert np.allclose(c, cb, rtol=1e-10, atol=1e-10 * np.abs(cb).max())
+
+
+# --------------------------------------------------------------------- round trips
+
+def _field(kind, rng, xf):
+    """A scalar field of the given polynomial class evaluated at positions xf."""
+    x, y, z = xf
+    if kind == "constant":
+        return np.full_like(x, rng.standard_normal())
+    if kind == "affine":
+        a = rng.standard_normal(4)
+        return a[0] + a[1] * x + a[2] * y + a[3] * z
+    if kind == "multilinear":
+        a = rng.standard_normal(8)
+        return sum(a[4 * i + 2 * j + k] * x ** i * y ** j * z ** k
+                   for i in range(2) for j in range(2) for k in range(2))
+    if kind == "triquadratic":
+        a = rng.standard_normal(27)
+        return sum(a[9 * i + 3 * j + k] * x ** i * y ** j * z ** k
+                   for i in range(3) for j in range(3) for k in range(3))
+    return rng.standard_normal(x.shape)  # arbitrary
+
+
+@pytest.mark.parametrize("R,kind", [(1, "constant"), (4, "constant"), (4, "affine"),
+                                    (8, "affine"), (8, "multilinear"), (27, "multilinear"),
+                                    (27, "triquadratic"), (27, "arbitrary")])
+def test_round_trip_reproduces_spanned_fields(R, kind):
+    """G2P then P2G at fixed positions returns v~ on every face with m > 0
+    whenever the field lies in the span of the first R modes (27 modes span
+    every field on the 3x3x3 stencil: the lossless transfer)."""
+    rng = np.random.default_rng(100 * R + ["constant", "affine", "multilinear",
+                                           "triquadratic", "arbitrary"].index(kind))
+    n = (10, 10, 10)
+    dx = 0.1
+    P = 300
+    x = _safe_positions(rng, P, 10)
+    mass = rng.uniform(0.5, 1.5, P)
+    gv = [_field(kind, rng, scenes.face_positions(a, n, dx)) for a in range(3)]
+    c, _ = oracle.g2p(x, gv, R, n, dx, 0.0)
+    gm, gp = oracle.p2g(x, mass, c, n, dx)
+    for a in range(3):
+        m = gm[a] > 0
+        v = gp[a][m] / gm[a][m]
+        assert np.allclose(v, gv[a][m], rtol=1e-11, atol=1e-11 * np.abs(gv[a]).max())
+
+
+def test_round_trip_fails_outside_span():
+    """Control: an affine-only transfer does not reproduce a quadratic field."""
+    rng = np.random.default_rng(9)
+    n = (10, 10, 10)
+    dx = 0.1
+    x = _safe_positions(rng, 200, 10)
+    mass = np.ones(200)
+    gv = [_field("triquadratic", rng, scenes.face_positions(a, n, dx)) for a in range(3)]
+    c, _ = oracle.g2p(x, gv, 4, n, dx, 0.0)
+    gm, gp = oracle.p2g(x, mass, c, n, dx)
+    m = gm[0] > 0
+    assert np.max(np.abs(gp[0][m] / gm[0][m] - gv[0][m])) > 1e-4
+
+
+@pytest.mark.parametrize("R", [1, 4, 8, 27])
+def test_grid_energy_never_increases(R):
+    rng = np.random.default_rng(20 + R)
+    n = (10, 10, 10)
+    dx = 0.1
+    P = 400
+    x = _safe_positions(rng, P, 10)
+    mass = rng.uniform(0.5, 1.5, P)
+    gm, _ = oracle.p2g(x, mass, np.zeros((3, R, P)), n, dx)
+    gv = [rng.standard_normal(gm[a].shape) * (gm[a] > 0) for a in range(3)]
+    ke0 = sum(0.5 * np.sum(gm[a] * gv[a] ** 2) for a in range(3))
+    c, _ = oracle.g2p(x, gv, R, n, dx, 0.0)
+    _, gp = oracle.p2g(x, mass, c, n, dx)
+    ke1 = sum(0.5 * np.sum(gp[a][gm[a] > 0] ** 2 / gm[a][gm[a] > 0]) for a in range(3))
+    if R == 27:
+        assert abs(ke1 - ke0) <= 1e-11 * ke0
+    else:
+        assert ke1 <= ke0 * (1 + 1e-13)
+        assert ke1 < ke0
+
+
+# --------------------------------------------------------------------- PIC / APIC truncation
+
+def _all_faces(n, dx, alpha, x):
+    """Independent all-faces weights: w (P, faces), offsets (P, faces, 3)."""
+    fx = np.stack([f.ravel() for f in scenes.face_positions(alpha, n, dx)], axis=1)
+    d = x.T[:, None, :] - fx[None, :, :]
+    w = np.prod(bruteforce.bspline2(d / dx), axis=2)
+    return w, -d
+
+
+def test_single_mode_is_pic():
+    """N_r = 1 reduces to PIC: Eqs 1-5 for P2G and Eqs 6-8 (per component) for G2P."""
+    rng = np.random.default_rng(30)
+    n = (8, 8, 8)
+    dx = 1 / 8
+    P = 60
+    x = _safe_positions(rng, P, 8)
+    mass = rng.uniform(0.5, 1.5, P)
+    vp = rng.standard_normal((3, P))
+    gm, gp = oracle.p2g(x, mass, vp[:, None, :], n, dx)
+    gv = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+    c, xn = oracle.g2p(x, gv, 1, n, dx, 1e-3)
+    for a in range(3):
+        w, _ = _all_faces(n, dx, a, x)
+        assert np.allclose(gm[a].ravel(), (mass[:, None] * w).sum(0), rtol=1e-13, atol=1e-16)
+        assert np.allclose(gp[a].ravel(), (mass[:, None] * w * vp[a][:, None]).sum(0),
+                           rtol=1e-12, atol=1e-14)
+        v_pic = w @ gv[a].ravel()
+        assert np.allclose(c[a, 0], v_pic, rtol=1e-12, atol=1e-13)
+        assert np.allclose(xn[a], x[a] + 1e-3 * v_pic, rtol=0, atol=1e-15)
+
+
+def test_four_modes_are_apic():
+    """N_r = 4 reduces to APIC (Eq 9 / Jiang et al.): v_p = sum w v~,
+    C_p = B_p D_p^-1 with B_p = sum w v~ (x_i - x_p)^T, D_p = dx^2/4 I, and
+    (mv)_i = sum m w (v_p + C_p (x_i - x_p))."""
+    rng = np.random.default_rng(31)
+    n = (8, 8, 8)
+    dx = 1 / 8
+    P = 60
+    x = _safe_positions(rng, P, 8)
+    mass = rng.uniform(0.5, 1.5, P)
+    gv = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+    c, _ = oracle.g2p(x, gv, 4, n, dx, 0.0)
+    for a in range(3):
+        w, z = _all_faces(n, dx, a, x)
+        v = w @ gv[a].ravel()
+        B = np.einsum("pf,f,pfb->pb", w, gv[a].ravel(), z)
+        C = B / (dx * dx / 4)
+        assert np.allclose(c[a, 0], v, rtol=1e-12, atol=1e-13)
+        assert np.allclose(c[a, 1:4], C.T, rtol=1e-10, atol=1e-10 * np.abs(C).max())
+    gm, gp = oracle.p2g(x, mass, c, n, dx)
+    for a in range(3):
+        w, z = _all_faces(n, dx, a, x)
+        mv = np.einsum("p,pf,pf->f", mass, w, c[a, 0][:, None] + np.einsum("bp,pfb->pf", c[a, 1:4], z))
+        assert np.allclose(gp[a].ravel(), mv, rtol=1e-11, atol=1e-12 * np.abs(mv).max())
+
+
+def test_apic_grad_w_reproduces_affine_and_differs_in_general():
+    """Eq 10 (c = sum grad w v~) is exact for affine fields but is not the
+    affine truncation for quadratic B-splines in general."""
+    rng = np.random.default_rng(32)
+    n = (8, 8, 8)
+    dx = 1 / 8
+    x = _safe_positions(rng, 40, 8)
+    A = rng.standard_normal((3, 4))
+    gv = [A[a, 0] + sum(A[a, 1 + b] * scenes.face_positions(a, n, dx)[b] for b in range(3))
+          for a in range(3)]
+    cg, _ = oracle.g2p(x, gv, 4, n, dx, 0.0, apic_grad=True)
+    for a in range(3):
+        assert np.allclose(cg[a, 1:4], A[a, 1:4][:, None], rtol=1e-10, atol=1e-10)
+    gv = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+    cg, _ = oracle.g2p(x, gv, 4, n, dx, 0.0, apic_grad=True)
+    ct, _ = oracle.g2p(x, gv, 4, n, dx, 0.0)
+    assert np.allclose(cg[:, 0], ct[:, 0])
+    assert np.max(np.abs(cg[:, 1:] - ct[:, 1:])) > 1e-3 * np.max(np.abs(ct[:, 1:]))
+
+
+# --------------------------------------------------------------------- step-level
+
+def test_free_fall():
+    """A resting block away from the walls, no projection: after one step every
+    particle has c_0 = dt g exactly and no higher modes; x advances by dt^2 g."""
+    n = (16, 16, 16)
+    dx = 1 / 16
+    rng = np.random.default_rng(40)
+    cells = scenes.box_cells(n, (6, 6, 6), (10, 10, 10))
+    x = scenes.seed_cells(cells, 8, dx, rng)
+    P = x.shape[1]
+    mass = np.full(P, 1000 * dx ** 3 / 8)
+    dt = 1e-3
+    g = (0.0, -9.81, 0.0)
+    c, xn, _ = oracle.step(x, mass, np.zeros((3, 27, P)), n, dx, dt, g)
+    for a in range(3):
+        assert np.allclose(c[a, 0], dt * g[a], rtol=1e-13, atol=1e-16)
+        # FP64 cancellation in sum_i w g (small d_2) leaves ~1e-11 relative residue
+        assert np.max(np.abs(c[a, 1:]) * dx ** scenes.mode_degrees(27)[1:, None]) < 1e-10 * dt * 9.81
+        assert np.allclose(xn[a], x[a].astype(np.float64) + dt * dt * g[a], rtol=0, atol=1e-15)
+
+
+def test_advection_clamps_to_margin():
+    """Particles leaving the domain are clamped to [1.5 dx, (n - 1.5) dx] per
+    axis (the paper deletes them instead; a fixed count is kept here)."""
+    n = (8, 8, 8)
+    dx = 1 / 8
+    x = np.array([[1.6 * dx, 6.4 * dx, 4.2 * dx], [4.3 * dx, 4.4 * dx, 1.55 * dx],
+                  [6.3 * dx, 2.2 * dx, 4.4 * dx]])
+    gv = [np.full(oracle.face_shape(a, n), s) for a, s in enumerate((-50.0, 50.0, -50.0))]
+    _, xn = oracle.g2p(x, gv, 1, n, dx, 0.1)
+    lo, hi = 1.5 * dx, 6.5 * dx
+    assert np.all(xn >= lo - 1e-15) and np.all(xn <= hi + 1e-15)
+    # velocities carry x down, y up, z down: every particle ends on a bound
+    assert np.allclose(xn[0], lo) and np.allclose(xn[1], hi) and np.allclose(xn[2], lo)
+
+
+def test_two_phase_drag_solves_implicit_euler():
+    rng = np.random.default_rng(41)
+    n = (6, 6, 6)
+    shapes = [oracle.face_shape(a, n) for a in range(3)]
+    fm = [rng.uniform(0.1, 2, s) for s in shapes]
+    sm = [rng.uniform(0.1, 2, s) for s in shapes]
+    fp = [rng.standard_normal(s) * m for s, m in zip(shapes, fm)]
+    sp = [rng.standard_normal(s) * m for s, m in zip(shapes, sm)]
+    dt, K = 1e-3, 50.0
+    fv, sv = oracle.grid_update(n, dt, (0, 0, 0), fm, fp, sm, sp, drag_k=K)
+    for a in range(3):
+        idx = [slice(None)] * 3
+        idx[2 - a] = slice(1, -1)
+        idx = tuple(idx)
+        vf0, vs0 = fp[a] / fm[a], sp[a] / sm[a]
+        rel = fv[a] - sv[a]
+        # m_f (v_f' - v_f) = -dt K (v_f' - v_s'),  m_s (v_s' - v_s) = +dt K (v_f' - v_s')
+        assert np.allclose((fm[a] * (fv[a] - vf0))[idx], (-dt * K * rel)[idx], rtol=1e-10, atol=1e-14)
+        assert np.allclose((sm[a] * (sv[a] - vs0))[idx], (dt * K * rel)[idx], rtol=1e-10, atol=1e-14)
+        # walls hold zero normal velocity
+        wall = [slice(None)] * 3
+        wall[2 - a] = 0
+        assert np.all(fv[a][tuple(wall)] == 0) and np.all(sv[a][tuple(wall)] == 0)
+
+
+# --------------------------------------------------------------------- adjoints
+
+def _fd_setup(R, seed):
+    rng = np.random.default_rng(seed)
+    n = (8, 8, 8)
+    dx = 1 / 8
+    P = 30
+    x = _safe_positions(rng, P, 8, eps=0.1)
+    mass = rng.uniform(0.5, 1.5, P)
+    deg = scenes.mode_degrees(R)
+    coeff = rng.standard_normal((3, R, P)) / (dx ** deg)[None, :, None]
+    return rng, n, dx, x, mass, coeff
+
+
+@pytest.mark.parametrize("R", [1, 4, 27])
+def test_p2g_adjoint_dot_product_and_position_fd(R):
+    rng, n, dx, x, mass, coeff = _fd_setup(R, 50 + R)
+    lm = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+    lp = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+
+    def J(xx, cc):
+        gm, gp = oracle.p2g(xx, mass, cc, n, dx)
+        return sum(np.sum(gm[a] * lm[a]) + np.sum(gp[a] * lp[a]) for a in range(3))
+
+    lc, lx = oracle.p2g_adjoint(x, mass, coeff, n, dx, lm, lp)
+    # linear in c: <P2G(c), lp> = <c, P2G^T lp>
+    gm, gp = oracle.p2g(x, mass, coeff, n, dx)
+    lhs = sum(np.sum(gp[a] * lp[a]) for a in range(3))
+    assert abs(lhs - np.sum(lc * coeff)) <= 1e-12 * (abs(lhs) + np.abs(lc * coeff).sum())
+    # position terms: central differences
+    for _ in range(3):
+        dxp = rng.standard_normal(x.shape)
+        h = 1e-6 * dx
+        fd = (J(x + h * dxp, coeff) - J(x - h * dxp, coeff)) / (2 * h)
+        an = np.sum(lx * dxp)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), np.abs(lx).sum() * 1e-3)
+
+
+@pytest.mark.parametrize("R", [1, 4, 27])
+def test_g2p_adjoint_dot_product_and_position_fd(R):
+    rng, n, dx, x, mass, _ = _fd_setup(R, 60 + R)
+    dt = 2e-3
+    gv = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+    deg = scenes.mode_degrees(R)
+    mu = rng.standard_normal((3, R, x.shape[1])) * (dx ** deg)[None, :, None]
+    nu = rng.standard_normal(x.shape)
+
+    def J(xx, vv):
+        c, xo = oracle.g2p(xx, vv, R, n, dx, dt)
+        return np.sum(c * mu) + np.sum(xo * nu)
+
+    lv, lx = oracle.g2p_adjoint(x, gv, R, n, dx, dt, mu, nu)
+    # linear in v~ (no clamping here): J(v) - J(0) = <v, G2P^T(mu, nu)>
+    j0 = J(x, [np.zeros_like(a) for a in gv])
+    lhs = J(x, gv) - j0
+    rhs = sum(np.sum(lv[a] * gv[a]) for a in range(3))
+    assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + 1e-30 + np.abs(rhs))
+    for _ in range(3):
+        dxp = rng.standard_normal(x.shape)
+        h = 1e-6 * dx
+        fd = (J(x + h * dxp, gv) - J(x - h * dxp, gv)) / (2 * h)
+        an = np.sum(lx * dxp)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), np.abs(lx).sum() * 1e-3)
+
+
+def test_grid_update_adjoint_fd():
+    rng = np.random.default_rng(70)
+    n = (6, 6, 6)
+    fm = [rng.uniform(0.5, 2, oracle.face_shape(a, n)) for a in range(3)]
+    fm[0][2, 2, 2] = 0.0
+    fp = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+    lv = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+
+    def J(m, p):
+        v = oracle.grid_update(n, 1e-3, (0, -9.81, 0), m, p)
+        return sum(np.sum(v[a] * lv[a]) for a in range(3))
+
+    lm, lp = oracle.grid_update_adjoint(n, fm, fp, lv)
+    dm = [rng.standard_normal(a.shape) * (a > 0) for a in fm]
+    dp = [rng.standard_normal(a.shape) for a in fp]
+    h = 1e-6
+    fd = (J([a + h * b for a, b in zip(fm, dm)], [a + h * b for a, b in zip(fp, dp)])
+          - J([a - h * b for a, b in zip(fm, dm)], [a - h * b for a, b in zip(fp, dp)])) / (2 * h)
+    an = sum(np.sum(lm[a] * dm[a]) + np.sum(lp[a] * dp[a]) for a in range(3))
+    assert abs(fd - an) <= 1e-7 * abs(an)
+
+
+# --------------------------------------------------------------------- projection
+
+def _laplacian_matrix(n, fluid):
+    import scipy.sparse as sp
+    nx, ny, nz = n
+    idx = -np.ones(fluid.shape, dtype=np.int64)
+    cells = np.argwhere(fluid)
+    idx[tuple(cells.T)] = np.arange(len(cells))
+    rows, cols, vals = [], [], []
+    for r, (k, j, i) in enumerate(cells):
+        nn = 0
+        for dk, dj, di in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]:
+            kk, jj, ii = k + dk, j + dj, i + di
+            if not (0 <= kk < nz and 0 <= jj < ny and 0 <= ii < nx):
+                continue      # wall: zero normal flux
+            nn += 1
+            if fluid[kk, jj, ii]:
+                rows.append(r); cols.append(idx[kk, jj, ii]); vals.append(-1.0)
+        rows.append(r); cols.append(r); vals.append(float(nn))
+    return sp.csr_matrix((vals, (rows, cols)), shape=(len(cells), len(cells))), cells
+
+
+def test_pcg_projection_matches_direct_solve_and_is_divergence_free():
+    import scipy.sparse.linalg as spla
+    rng = np.random.default_rng(80)
+    n = (12, 10, 8)
+    dx, dt, rho = 1 / 12, 1e-3, 1000.0
+    fluid = np.zeros((n[2], n[1], n[0]), dtype=bool)
+    fluid[1:6, 1:8, 2:10] = True
+    fluid[6, 3:5, 4:6] = True
+    v = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+    for a in range(3):       # walls carry no normal velocity
+        idx = [slice(None)] * 3
+        idx[2 - a] = 0
+        v[a][tuple(idx)] = 0
+        idx[2 - a] = -1
+        v[a][tuple(idx)] = 0
+    vp, p, it = oracle.pcg_project(n, dx, dt, rho, fluid, v, rtol=1e-12, maxiter=2000)
+    assert it > 0
+    # divergence of the projected field vanishes in every fluid cell
+    div = (np.diff(vp[0], axis=2) + np.diff(vp[1], axis=1) + np.diff(vp[2], axis=0)) / dx
+    div0 = (np.diff(v[0], axis=2) + np.diff(v[1], axis=1) + np.diff(v[2], axis=0)) / dx
+    assert np.max(np.abs(div[fluid])) <= 1e-9 * np.max(np.abs(div0[fluid]))
+    # pressure equals a direct sparse solve of the same Poisson problem
+    A, cells = _laplacian_matrix(n, fluid)
+    b = -(rho * dx * dx / dt) * div0[fluid]
+    p_direct = spla.spsolve(A.tocsc(), b)
+    assert np.allclose(p[fluid], p_direct, rtol=1e-8, atol=1e-8 * np.abs(p_direct).max())
+    assert np.all(p[~fluid] == 0)
+    # idempotent
+    vp2, _, _ = oracle.pcg_project(n, dx, dt, rho, fluid, vp, rtol=1e-12, maxiter=2000) \
+        if np.abs(div[fluid]).max() > 0 else (vp, None, None)
+    for a in range(3):
+        assert np.allclose(vp2[a], vp[a], rtol=0, atol=1e-8 * np.abs(vp[a]).max())
