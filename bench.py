@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Throughput of the PolyPIC transfer step on one GB300.
+
+Workload: the fluid dam break on a 128^3 grid (a 64 x 128 x 64-cell block at 8
+particles per cell, seeded inside the 2-cell margin: 3,813,248 particles), 27
+modes per velocity component, FP32 coefficients, dt = 5e-4, gravity -9.81,
+zero initial velocity.  A step is one pass of the whole transfer path through
+the C ABI: stable cell sort, P2G, grid update, G2P with advection; the
+particle state ping-pongs between two buffers (G2P writes it in sorted order).
+
+Printed (rank 0, one JSON line): whole-job M particle-steps/s over the timed
+steps, the per-phase split, the roofline of the dominant call, the variants
+(APIC = 4-mode truncation, BF16 and FP16 per-particle-scaled coefficients),
+an end-to-end figure with host buffers, the clocks seen while timing, and the
+FP64 CPU oracle timed on a bounded sample on the host.
+
+--impl reference times that oracle alone (the only reference available: the
+paper's own code is a CPU simulator that is not available here).
+--gpus N (under torchrun) runs N independent replicas, one per GPU: the
+transfers do not shard in this build, so no collective is involved.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PolyPIC P2G+G2P M particle-steps/s vs plain FP32 form; % HBM roofline"
+UNIT = "M particle-steps/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="grid cells per axis (default 128)")
+    ap.add_argument("--variants", default="apic4,bf16,f16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- workload
+
+def algorithmic_bytes(R: int, fmt: str):
+    """Per particle-step bytes of the P2G and G2P calls.  P2G reads x, m and
+    c; G2P reads x and writes x and c; the grid term (P2G writes of m and mv,
+    G2P reads of v~ on 3 face grids: 36 B per cell at 8 particles per cell) is
+    split 24/12 between them."""
+    cbytes = 12 * R if fmt == "f32" else 6 * R + 4
+    p2g = 16 + cbytes + 24 / 8
+    g2p = 24 + cbytes + 12 / 8
+    return p2g, g2p
+
+
+def launches_per_step(num_keys: int) -> int:
+    """Kernels of ours per step: keys + 3-kernel count scan, 5 per radix pass
+    (histogram, 3-kernel scan, scatter), P2G blocks + 3 reductions, grid
+    update, G2P."""
+    bits = max(1, int(np.ceil(np.log2(num_keys))))
+    passes = (bits + 7) // 8
+    return 4 + 5 * passes + 4 + 1 + 1
+
+
+def make_state(pp, ctx, scene, device):
+    f = scene.fluid
+    a = pp.upload_particles(ctx, f.x, f.mass, None, device=device)
+    b = ctx.new_particles(a.count, device=device)
+    return a, b
+
+
+def run_variant(pp, torch, scene, R, fmt, steps, warmup, device):
+    ctx = pp.Context(scene.n, scene.dx, R, coeff_format=fmt)
+    src, dst = make_state(pp, ctx, scene, device)
+    g = ctx.new_grid(device=device)
+    ws = ctx.workspace(src.count, device=device)
+    prm = pp.UpdateSettings(dt=scene.dt)
+    stream = torch.cuda.current_stream()
+
+    def step(s, d, ev=None):
+        pp.polypic_sort(ctx, s, ws, stream)
+        if ev is not None:
+            ev[0].record(stream)
+        pp.polypic_p2g(ctx, s, g, ws, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        pp.polypic_grid_update(ctx, g, prm, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+        pp.polypic_g2p(ctx, g, s, d, scene.dt, ws, stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(warmup):
+        step(src, dst)
+        src, dst = dst, src
+    torch.cuda.synchronize()
+    st = pp.polypic_check_device_status(ctx)
+    if st != 0:
+        raise RuntimeError(f"device status {pp.STATUS_NAMES.get(st)} during warm-up")
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    start, end = E(), E()
+    evs = [[E(), E(), E(), E()] for _ in range(steps)]
+    starts = [E() for _ in range(steps)]
+    start.record(stream)
+    for k in range(steps):
+        starts[k].record(stream)
+        step(src, dst, evs[k])
+        src, dst = dst, src
+    end.record(stream)
+    torch.cuda.synchronize()
+    total_ms = start.elapsed_time(end)
+    ph = np.zeros(4)
+    for k in range(steps):
+        ph[0] += starts[k].elapsed_time(evs[k][0])
+        ph[1] += evs[k][0].elapsed_time(evs[k][1])
+        ph[2] += evs[k][1].elapsed_time(evs[k][2])
+        ph[3] += evs[k][2].elapsed_time(evs[k][3])
+    st = pp.polypic_check_device_status(ctx)
+    return {"ctx": ctx, "count": src.count, "total_ms": total_ms,
+            "phase_ms": (ph / steps).tolist(), "status": pp.STATUS_NAMES.get(st)}
+
+
+def run_e2e(pp, torch, scene, R, steps, device):
+    """Through the C ABI with host buffers: every step copies the particle
+    state in from pinned host memory and the new state back out."""
+    ctx = pp.Context(scene.n, scene.dx, R)
+    f = scene.fluid
+    P = f.n
+    dev_in, dev_out = make_state(pp, ctx, scene, device)
+    g = ctx.new_grid(device=device)
+    ws = ctx.workspace(P, device=device)
+    prm = pp.UpdateSettings(dt=scene.dt)
+    h_x = torch.from_numpy(f.x).pin_memory()
+    h_m = torch.from_numpy(f.mass).pin_memory()
+    h_c = torch.zeros((3, R, P), dtype=torch.float32).pin_memory()
+    h_xo = torch.empty((3, P), dtype=torch.float32).pin_memory()
+    h_co = torch.empty((3, R, P), dtype=torch.float32).pin_memory()
+    stream = torch.cuda.current_stream()
+    h2d = (h_x.numel() + h_m.numel() + h_c.numel()) * 4
+    d2h = (h_xo.numel() + h_co.numel()) * 4
+
+    def step():
+        dev_in.x.copy_(h_x, non_blocking=True)
+        dev_in.mass.copy_(h_m, non_blocking=True)
+        dev_in.coeff.copy_(h_c, non_blocking=True)
+        pp.polypic_sort(ctx, dev_in, ws, stream)
+        pp.polypic_p2g(ctx, dev_in, g, ws, stream)
+        pp.polypic_grid_update(ctx, g, prm, stream=stream)
+        pp.polypic_g2p(ctx, g, dev_in, dev_out, scene.dt, ws, stream)
+        h_xo.copy_(dev_out.x, non_blocking=True)
+        h_co.copy_(dev_out.coeff, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"value": P / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def cpu_baseline(scene, R, target_s=12.0):
+    """FP64 CPU oracle (single thread, as it stands) on a bounded sample of the
+    same workload: the first S particles of the scene on the full grid, one
+    step each; S grows until the run takes a few seconds."""
+    import oracle
+    f = scene.fluid
+    S = 2000
+    while True:
+        x = f.x[:, :S]
+        m = f.mass[:S]
+        c = np.zeros((3, R, S))
+        t0 = time.perf_counter()
+        oracle.step(x, m, c, scene.n, scene.dx, scene.dt)
+        el = time.perf_counter() - t0
+        if el > target_s / 3 or S >= f.n:
+            break
+        S = min(f.n, int(S * max(2.0, (target_s / 3) / max(el, 1e-3))))
+    return {"value": S / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{S} of {f.n} particles, one full step (P2G, grid update, G2P) on the "
+                      f"{scene.n[0]}^3 grid, FP64, single thread", "seconds": el}
+
+
+# ---------------------------------------------------------------- arms
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2308_01060_gb300 import scenes
+    import oracle
+    oracle.build()
+    scene = scenes.dam_break_scene(n=args.n, R=27)
+    f = scene.fluid
+    S = 20000
+    x = f.x[:, :S]
+    m = f.mass[:S]
+    c = np.zeros((3, 27, S))
+    for _ in range(max(args.warmup, 0)):
+        oracle.step(x, m, c, scene.n, scene.dx, scene.dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        c_new, x_new, _ = oracle.step(x, m, c, scene.n, scene.dx, scene.dt)
+        x, c = x_new, c_new
+    el = time.perf_counter() - t0
+    value = S * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"dam_break_{args.n}^3, 27 modes, dt 5e-4",
+                       "sample_particles_per_step": S},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{S} of {f.n} particles per step on the full grid"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def our_arm(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    from paper_2308_01060_gb300 import polypic as pp
+    from paper_2308_01060_gb300 import scenes
+    pp.load_library()
+
+    scene = scenes.dam_break_scene(n=args.n, R=27)
+    P = scene.fluid.n
+    hbm, peak_kind = peaks()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # headline: 27 modes, FP32 coefficients
+    barrier()
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    sampler.start()
+    t_wall = time.perf_counter()
+    main = run_variant(pp, torch, scene, 27, "f32", args.steps, args.warmup, device)
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    ms = main["total_ms"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = P * world * args.steps / (ms * 1e-3) / 1e6
+    ms_step = ms / args.steps
+
+    p2g_b, g2p_b = algorithmic_bytes(27, "f32")
+    ph = main["phase_ms"]
+    p2g_gbs = P * p2g_b / (ph[1] * 1e-3) / 1e9
+    g2p_gbs = P * g2p_b / (ph[3] * 1e-3) / 1e9
+    pair_gbs = P * (p2g_b + g2p_b) / ((ph[1] + ph[3]) * 1e-3) / 1e9
+    dominant = "p2g" if ph[1] >= ph[3] else "g2p"
+    dom_gbs = p2g_gbs if dominant == "p2g" else g2p_gbs
+    roofline = {
+        "bound": "hbm", "achieved": round(dom_gbs, 1), "peak": hbm, "unit": "GB/s",
+        "frac": round(dom_gbs / hbm, 4), "traffic": None,
+        "kernel": "polypic_p2g (k_p2g_blocks + 3 x k_p2g_reduce)" if dominant == "p2g"
+        else "polypic_g2p (k_g2p_tiles)",
+        "algorithmic_bytes_per_particle": p2g_b if dominant == "p2g" else g2p_b,
+        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+        else "fallback 6800 GB/s",
+    }
+
+    variants = {}
+    for v in [s for s in args.variants.split(",") if s]:
+        R, fmt = (4, "f32") if v == "apic4" else (27, v)
+        r = run_variant(pp, torch, scene, R, fmt, args.steps, args.warmup, device)
+        pb, gb = algorithmic_bytes(R, fmt)
+        vph = r["phase_ms"]
+        variants[v] = {
+            "modes": R, "coeff_format": fmt,
+            "value": P * args.steps / (r["total_ms"] * 1e-3) / 1e6,
+            "ms_per_step": r["total_ms"] / args.steps,
+            "phase_ms": [round(x, 4) for x in vph],
+            "p2g_g2p_gbs": round(P * (pb + gb) / ((vph[1] + vph[3]) * 1e-3) / 1e9, 1),
+            "speedup_vs_f32_step": round(ms_step / (r["total_ms"] / args.steps), 3),
+            "speedup_vs_f32_p2g_g2p": round((ph[1] + ph[3]) / (vph[1] + vph[3]), 3),
+            "status": r["status"],
+        }
+        del r
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(pp, torch, scene, 27, args.e2e_steps, device)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e["ms_per_step"]], device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = P * world / (float(t.item()) * 1e-3) / 1e6
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scene, 27)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": f"dam_break_{args.n}^3: {args.n // 2}x{args.n}x{args.n // 2}-cell block, "
+                            f"8 particles/cell, 27 modes, FP32 coefficients, dt 5e-4",
+                "particles_per_gpu": P, "grid": list(scene.n), "modes": 27,
+                "step": "sort + P2G + grid update + G2P/advect (C ABI calls)",
+                "l2": f"inputs larger than L2 ({P * (16 + 324) / 1e9:.2f} GB of particle state "
+                      f"read per step vs 129 MB L2); no flush",
+                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            },
+            "phase_ms": {"sort": round(ph[0], 4), "p2g": round(ph[1], 4),
+                         "grid_update": round(ph[2], 4), "g2p": round(ph[3], 4)},
+            "p2g_g2p_only": {"value": round(P * world / ((ph[1] + ph[3]) * 1e-3) / 1e6, 3),
+                             "unit": UNIT, "gbs": round(pair_gbs, 1),
+                             "frac_of_peak": round(pair_gbs / hbm, 4)},
+            "roofline": roofline,
+            "variants": variants,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step(main["ctx"].num_keys) * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "device_status": main["status"],
+            "wall_s_headline": round(wall, 2),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

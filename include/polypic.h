@@ -1,0 +1,267 @@
+/*
+ * polypic.h -- C ABI of libpolypic, a GB300 (sm_103a) implementation of the
+ * polynomial particle-in-cell (PolyPIC) particle<->grid transfers of
+ * "Using The Polynomial Particle-in-Cell Method for Liquid-Fabric
+ * Interaction" (arXiv 2308.01060), with the APIC transfer as its affine-mode
+ * truncation.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Domain: the box [0, n_x dx] x [0, n_y dx] x [0, n_z dx] of n_x n_y n_z
+ *    cells.  Staggered MAC grid (Section 3): face grid a stores velocity
+ *    component a at ((i + o_x) dx, (j + o_y) dx, (k + o_z) dx) with o_b = 0
+ *    for b == a and 1/2 otherwise.  Face grid a has dims
+ *    (n_x + [a==0], n_y + [a==1], n_z + [a==2]) and is stored x fastest:
+ *    index = (k * d_y + j) * d_x + i.
+ *  - Weights: quadratic B-spline, w_ipa = N(x_p - x_ia) = prod_b N(.)
+ *    (Section 3.1; quadratic per Eq 14's dx^2/4).
+ *  - Modes (Section 3.3, Eq 11 with the Eq 14 substitution): per axis
+ *    f_0 = 1, f_1 = z, f_2 = g(z) = z^2 - (mu3/mu2) z - mu2 with
+ *    z = x_node - x_p and mu_n the B-spline-weighted moments of the particle's
+ *    three stencil nodes; s_r = f_a(z_x) f_b(z_y) f_c(z_z).  Canonical order
+ *    r <-> (a,b,c): r = 0 (000); 1..3 (100)(010)(001); 4..7 (110)(101)(011)
+ *    (111); 8..26 the triples containing a 2 in lexicographic order of
+ *    (c, b, a).  num_modes = 1 (PIC), 4 (APIC), 8 (the paper's setting),
+ *    27 (full PolyPIC) take prefixes of this order.
+ *  - Particle arrays are structure-of-arrays in device memory owned by the
+ *    caller.  Coefficients are laid out [3][num_modes][count]: element
+ *    (a, r, p) at (a * num_modes + r) * count + p.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream).  Arguments are validated on the host before anything
+ *    is launched; a bad argument returns an error and launches nothing.  No
+ *    C++ exception crosses this interface.
+ *  - Conditions found on the device (a particle outside the valid region, a
+ *    non-finite velocity) latch bits of a device status word in the context;
+ *    polypic_check_device_status() synchronises the stream, returns the first
+ *    latched condition and clears it.  Kernels never trap.
+ *  - Scratch memory is the caller's `ws` buffer (device memory of at least
+ *    polypic_workspace_bytes() bytes, 256-byte aligned).  The library itself
+ *    owns only the context (a few bytes of device memory for the status
+ *    word).  Calls that share a workspace must not overlap on the GPU.
+ *  - Decisions that pick an integer (a particle's cell, the lowest stencil
+ *    node, the quadratic-mode guard) are taken in FP32 with every operation
+ *    rounded separately (no fused multiply-add) from the FP32 position, so
+ *    that any reimplementation following this text takes the same decision:
+ *       v = fl(x * inv_dx), inv_dx = (float)(1.0 / dx)
+ *       cell = clamp(floor(v), 0, n - 1)
+ *       X = v (face axis, o = 0) or fl(v - 0.5) (other axes, o = 1/2)
+ *       base = floor(fl(X - 0.5)), t = fl(X - (base + 1)) in [-1/2, 1/2)
+ *       guard = fl(fl(1 - 2t) * fl(1 + 2t)) < 2^-10.
+ *  - Valid particles satisfy 1 <= v < n - 1 on every axis; the transfers
+ *    skip any other particle and latch POLYPIC_ERR_OUT_OF_DOMAIN.
+ */
+#ifndef POLYPIC_H
+#define POLYPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum polypic_status {
+    POLYPIC_OK = 0,
+    POLYPIC_ERR_INVALID_ARG = 1,   /* bad pointer, size, or enum value */
+    POLYPIC_ERR_UNSUPPORTED = 2,   /* valid but not implemented combination */
+    POLYPIC_ERR_OUT_OF_DOMAIN = 3, /* a particle outside 1 <= x/dx < n-1 */
+    POLYPIC_ERR_NONFINITE = 4,     /* a NaN or Inf reached a velocity */
+    POLYPIC_ERR_NOT_CONVERGED = 5, /* PCG hit its iteration cap */
+    POLYPIC_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    POLYPIC_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+    POLYPIC_ERR_WORKSPACE = 8      /* ws NULL, misaligned, or too small */
+} polypic_status;
+
+enum {
+    POLYPIC_COEFF_F32 = 0,   /* float c_pra, physical units */
+    POLYPIC_COEFF_BF16 = 1,  /* bfloat16 codes with a per-particle FP32 scale */
+    POLYPIC_COEFF_F16 = 2    /* IEEE half codes with a per-particle FP32 scale */
+};
+
+enum { POLYPIC_MAP_CONSTANT = 0, POLYPIC_MAP_AFFINE = 1 };
+enum { POLYPIC_APIC_TRUNCATION = 0, POLYPIC_APIC_GRAD_W = 1 };
+
+/* Adjoint flags. */
+enum { POLYPIC_ADJ_ACCUMULATE = 1 };   /* add into the outputs instead of overwriting */
+
+typedef struct polypic_ctx polypic_ctx;
+
+/* Problem definition.  Fixed for the life of a context. */
+typedef struct polypic_config {
+    int32_t n[3];          /* cells per axis, each >= 4 */
+    double dx;             /* cell width (> 0) */
+    int32_t num_modes;     /* N_r: 1, 4, 8 or 27 */
+    int32_t coeff_format;  /* POLYPIC_COEFF_* */
+    int32_t map;           /* POLYPIC_MAP_CONSTANT (Eq 12's affine map: UNSUPPORTED) */
+    int32_t apic_variant;  /* POLYPIC_APIC_TRUNCATION (Eq 10's grad-w form: UNSUPPORTED) */
+} polypic_config;
+
+/* One phase of particles (Section 3.4: fluid, or solid with absorbed mass).
+ * All pointers are device memory owned by the caller.
+ *   x[3]        [count] float positions (in)
+ *   mass        [count] float particle mass m_p (in)
+ *   mass_abs    [count] float absorbed fluid mass, or NULL for fluid (Eq 18)
+ *   coeff       [3][num_modes][count]: float for POLYPIC_COEFF_F32; for the
+ *               16-bit formats uint16 codes of c_pra dx^L_r / s_p, where L_r
+ *               is the total degree of mode r and s_p = max |c_pra dx^L_r|
+ *   coeff_scale [count] float s_p (16-bit formats only, else NULL)
+ *   key, perm   [count] uint32, written by polypic_sort
+ *   cell_start  [polypic_num_keys() + 1] uint32, written by polypic_sort   */
+typedef struct polypic_particles {
+    int64_t count;
+    float *x[3];
+    float *mass;
+    float *mass_abs;
+    void *coeff;
+    float *coeff_scale;
+    uint32_t *key;
+    uint32_t *perm;
+    uint32_t *cell_start;
+} polypic_particles;
+
+/* The three face grids of one phase (device memory, caller-owned). */
+typedef struct polypic_grid {
+    float *mass[3];   /* m_ia   (Eqs 1, 4) */
+    float *mom[3];    /* (mv)_ia (Eqs 3, 13) */
+    float *vel[3];    /* v~_ia after the grid update */
+} polypic_grid;
+
+typedef struct polypic_update_params {
+    float dt;
+    float gravity[3];
+    float drag_k;        /* two-phase drag coefficient K (kg/s per face), 0 = none */
+    float rho;           /* fluid density for the projection */
+    int32_t project;     /* 1: pressure projection on fluid cells */
+    int32_t pcg_maxiter;
+    double pcg_rtol;
+} polypic_update_params;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Validates *cfg and allocates the context (and its device status word) on
+ * the current device.  Returns INVALID_ARG / UNSUPPORTED / CUDA on failure,
+ * leaving *out NULL. */
+polypic_status polypic_create(const polypic_config *cfg, polypic_ctx **out);
+void polypic_destroy(polypic_ctx *ctx);
+
+/* Number of sort keys K (cell_start has K + 1 entries).  Keys order cells in
+ * tiles of 8x8x4 cells (row-major tile order); a tile is 2x2x2 blocks of
+ * 4x4x2 cells (x fastest); cells in a block are x fastest:
+ *   key = tile * 256 + block_in_tile * 32 + cell_in_block.  Returns -1 for a
+ * NULL context. */
+int64_t polypic_num_keys(const polypic_ctx *ctx);
+
+/* Key of cell (i, j, k) under the layout above (host helper). */
+uint32_t polypic_cell_key(const polypic_ctx *ctx, int32_t i, int32_t j, int32_t k);
+
+/* dims[0..2] of face grid `axis` (0, 1, 2). */
+polypic_status polypic_grid_dims(const polypic_ctx *ctx, int32_t axis, int32_t dims[3]);
+
+/* Bytes of scratch needed by any call on phases of up to n_fluid and n_solid
+ * particles (0 on a NULL context). */
+size_t polypic_workspace_bytes(const polypic_ctx *ctx, int64_t n_fluid, int64_t n_solid);
+
+/* ---- forward transfers --------------------------------------------------- */
+
+/* Bit-exact stable counting sort of the particles by cell key (an
+ * implementation device; the paper has none).  Writes p->key (key of each
+ * particle), p->perm (perm[j] = index of the j-th particle in (key, index)
+ * order) and p->cell_start (first sorted slot of each key; entry K = count).
+ * Latches OUT_OF_DOMAIN for particles outside the valid region. */
+polypic_status polypic_sort(polypic_ctx *ctx, polypic_particles *p, void *ws, size_t ws_bytes,
+                            void *stream);
+
+/* P2G, Eqs 1-5 and 13 (fluid, Eqs 15-17; solid with m_s + m_abs, Eqs 18-19):
+ *   m_ia  = sum_p mt_p w_ipa
+ *   mv_ia = sum_p mt_p w_ipa sum_{r<N_r} c_pra s_r(x_ia - x_p)
+ * with the modes evaluated at the particle's current position.  Needs
+ * p->perm and p->cell_start from polypic_sort on the same positions.
+ * Overwrites g->mass and g->mom (every face).  Deterministic: the result is
+ * bit-identical from run to run (fixed summation order, no float atomics). */
+polypic_status polypic_p2g(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
+                           void *ws, size_t ws_bytes, void *stream);
+
+/* Grid update (delegated to the host simulator by the paper; this minimal
+ * form): v = mv/m where m > 0 else 0 (Eq 5, Eq 20 for the solid grid);
+ * v~ = v + dt g; with a solid grid and drag_k > 0, implicit two-phase drag on
+ * faces where both masses are positive, u' = u / (1 + dt K (1/m_f + 1/m_s))
+ * for u = v_f - v_s, keeping the mass-weighted mean; v~_a = 0 on the wall
+ * faces i_a in {0, n_a}; optional pressure projection (Jacobi-PCG on cells
+ * holding fluid particles, FP64 dot products and norms) needs
+ * fluid_particles->cell_start.  Writes fluid->vel (and solid->vel).
+ * `solid` and `fluid_particles` may be NULL. */
+polypic_status polypic_grid_update(polypic_ctx *ctx, polypic_grid *fluid, polypic_grid *solid,
+                                   const polypic_particles *fluid_particles,
+                                   const polypic_update_params *params, void *ws,
+                                   size_t ws_bytes, void *stream);
+
+/* G2P (Eqs 6-8 per component, and the decoupled least-squares mode fit of
+ * Section 3.3): c_pra = sum_i w s_r v~_ia / d_r with d_r = sum_i w s_r^2,
+ * setting to 0 the coefficient of every mode with a quadratic factor on an
+ * axis where the guard holds; v_p = c_p0; x_p <- clamp(x_p + dt v_p,
+ * 1.5 dx, (n - 1.5) dx).  Reads `in` (positions, masses) through in->perm and
+ * writes the new state of the particle in sorted slot j = 0..count-1 to
+ * out->x, out->mass, out->mass_abs (if non-NULL), out->coeff and
+ * out->coeff_scale: `out` must not alias `in`. */
+polypic_status polypic_g2p(polypic_ctx *ctx, const polypic_grid *g, const polypic_particles *in,
+                           polypic_particles *out, float dt, void *ws, size_t ws_bytes,
+                           void *stream);
+
+/* One transfer step of each phase: sort, P2G, grid update, G2P
+ * (Figure 2's step with PolyPIC transfers).  solid_in / solid_out / gs may be
+ * NULL for a fluid-only step.  New states go to fluid_out / solid_out in
+ * sorted order. */
+polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
+                            polypic_particles *fluid_out, polypic_particles *solid_in,
+                            polypic_particles *solid_out, polypic_grid *gf, polypic_grid *gs,
+                            const polypic_update_params *params, void *ws, size_t ws_bytes,
+                            void *stream);
+
+/* ---- adjoints (constant map, single phase, no projection) ---------------- *
+ * Transposes of the forward calls at the forward state.  Adjoint particle
+ * data reuse polypic_particles (x[3] = dL/dx, coeff = dL/dc as float
+ * [3][num_modes][count]) and adjoint grids reuse polypic_grid (mass = dL/dm,
+ * mom = dL/d(mv), vel = dL/dv~).  Outputs are overwritten unless flags has
+ * POLYPIC_ADJ_ACCUMULATE.  Supported for POLYPIC_COEFF_F32 only.            */
+
+/* Adjoint of polypic_g2p at (g->vel, in positions): given bar_out->coeff and
+ * bar_out->x (dL/d of the outputs, in sorted slot order), writes
+ * bar_grid->vel = dL/dv~ and bar_in->x = dL/dx of the inputs (input order,
+ * through in->perm), including the advection and the position dependence of
+ * w, s_r and d_r.  Clamped axes pass no gradient. */
+polypic_status polypic_g2p_adjoint(polypic_ctx *ctx, const polypic_grid *g,
+                                   const polypic_particles *in, float dt,
+                                   const polypic_particles *bar_out, polypic_grid *bar_grid,
+                                   polypic_particles *bar_in, int32_t flags, void *ws,
+                                   size_t ws_bytes, void *stream);
+
+/* Adjoint of polypic_grid_update (single phase, no drag, no projection):
+ * given bar_out->vel, writes bar_in->mass and bar_in->mom from g->mass and
+ * g->mom.  Wall faces and faces with m = 0 pass no gradient. */
+polypic_status polypic_grid_update_adjoint(polypic_ctx *ctx, const polypic_grid *g,
+                                           const polypic_update_params *params,
+                                           const polypic_grid *bar_out, polypic_grid *bar_in,
+                                           void *ws, size_t ws_bytes, void *stream);
+
+/* Adjoint of polypic_p2g at the state `in`: given bar_grid->mass and
+ * bar_grid->mom, writes bar_in->coeff = dL/dc and bar_in->x = dL/dx (input
+ * order, through in->perm). */
+polypic_status polypic_p2g_adjoint(polypic_ctx *ctx, const polypic_particles *in,
+                                   const polypic_grid *bar_grid, polypic_particles *bar_in,
+                                   int32_t flags, void *ws, size_t ws_bytes, void *stream);
+
+/* ---- status -------------------------------------------------------------- */
+
+/* Synchronises `stream`, returns the first latched device condition
+ * (OUT_OF_DOMAIN, NONFINITE, NOT_CONVERGED, TIMEOUT) or OK, and clears it.
+ * Returns CUDA if an earlier asynchronous launch failed. */
+polypic_status polypic_check_device_status(polypic_ctx *ctx, void *stream);
+
+/* Static description of a status code. */
+const char *polypic_status_string(polypic_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYPIC_H */

@@ -1,0 +1,447 @@
+// api.cu -- the C ABI of libpolypic (declared in include/polypic.h).
+//
+// Every entry point validates its arguments on the host, lays the caller's
+// workspace out, and launches kernels on the caller's stream.  No C++
+// exception escapes (allocation uses nothrow); errors come back as
+// polypic_status values.
+#include <cmath>
+#include <new>
+
+#include "g2p.cuh"
+#include "grid.cuh"
+#include "p2g.cuh"
+#include "pcg.cuh"
+#include "adjoint.cuh"
+#include "polypic_internal.cuh"
+#include "sort.cuh"
+
+using namespace polypic;
+
+namespace {
+
+polypic_status from_cuda(cudaError_t e) { return e == cudaSuccess ? POLYPIC_OK : POLYPIC_ERR_CUDA; }
+
+bool valid_modes(int r) { return r == 1 || r == 4 || r == 8 || r == 27; }
+
+int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+size_t required_ws(const polypic_ctx *c, int64_t nf, int64_t ns) {
+    int64_t n = max64(nf, ns);
+    size_t a = sort_scratch_bytes(n, c->num_keys);
+    size_t b = p2g_scratch_bytes(c->num_keys);
+    size_t d = pcg_scratch_bytes(c->geom);
+    size_t m = a > b ? a : b;
+    m = m > d ? m : d;
+    return m + 4096;
+}
+
+polypic_status check_ws(const polypic_ctx *c, int64_t count, const void *ws, size_t ws_bytes) {
+    size_t need = required_ws(c, count, 0);
+    if (!ws || ((uintptr_t)ws & 255u) != 0 || ws_bytes < need) return POLYPIC_ERR_WORKSPACE;
+    return POLYPIC_OK;
+}
+
+polypic_status check_positions(const polypic_particles *p) {
+    if (!p || p->count < 0 || p->count >= ((int64_t)1 << 31)) return POLYPIC_ERR_INVALID_ARG;
+    if (p->count > 0 && (!p->x[0] || !p->x[1] || !p->x[2])) return POLYPIC_ERR_INVALID_ARG;
+    return POLYPIC_OK;
+}
+
+polypic_status check_sorted(const polypic_particles *p) {
+    polypic_status s = check_positions(p);
+    if (s != POLYPIC_OK) return s;
+    if (!p->cell_start || (p->count > 0 && !p->perm)) return POLYPIC_ERR_INVALID_ARG;
+    return POLYPIC_OK;
+}
+
+polypic_status check_coeff(const polypic_ctx *c, const polypic_particles *p) {
+    if (p->count == 0) return POLYPIC_OK;
+    if (!p->coeff || !p->mass) return POLYPIC_ERR_INVALID_ARG;
+    if (c->cfg.coeff_format != POLYPIC_COEFF_F32 && !p->coeff_scale) return POLYPIC_ERR_INVALID_ARG;
+    return POLYPIC_OK;
+}
+
+bool grid_ok(const polypic_grid *g, bool need_mass, bool need_mom, bool need_vel) {
+    if (!g) return false;
+    for (int a = 0; a < 3; ++a) {
+        if (need_mass && !g->mass[a]) return false;
+        if (need_mom && !g->mom[a]) return false;
+        if (need_vel && !g->vel[a]) return false;
+    }
+    return true;
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+polypic_status do_sort(polypic_ctx *c, polypic_particles *p, void *ws, size_t ws_bytes,
+                       cudaStream_t s) {
+    if (p->count > 0 && !p->key) return POLYPIC_ERR_INVALID_ARG;
+    Workspace W{static_cast<char *>(ws), ws_bytes, 0};
+    return from_cuda(sort_particles(c->geom, c->num_keys, p->count, p->x[0], p->x[1], p->x[2],
+                                    p->key, p->perm, p->cell_start, c->d_status, W, s));
+}
+
+polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *g, void *ws,
+                      size_t ws_bytes, cudaStream_t s) {
+    P2GArgs P{};
+    P.g = c->geom;
+    P.count = p->count;
+    P.x = p->x[0];
+    P.y = p->x[1];
+    P.z = p->x[2];
+    P.mass = p->mass;
+    P.mass_abs = p->mass_abs;
+    P.coeff = p->coeff;
+    P.scale = p->coeff_scale;
+    P.perm = p->perm;
+    P.cell_start = p->cell_start;
+    P.status = c->d_status;
+    P.nblocks = (uint32_t)(c->num_keys / 32);
+    for (int l = 0; l < 7; ++l) P.dxpow[l] = (float)std::pow(c->cfg.dx, (double)l);
+    Workspace W{static_cast<char *>(ws), ws_bytes, 0};
+    P.scratch = W.take<float>((size_t)P.nblocks * kRegionFloats);
+    return from_cuda(p2g(P, g->mass, g->mom, c->cfg.num_modes, c->cfg.coeff_format, s));
+}
+
+polypic_status do_g2p(polypic_ctx *c, const polypic_grid *g, const polypic_particles *in,
+                      polypic_particles *out, float dt, cudaStream_t s) {
+    G2PArgs A{};
+    A.g = c->geom;
+    A.count = in->count;
+    A.dt = dt;
+    for (int a = 0; a < 3; ++a) A.vel[a] = g->vel[a];
+    A.x = in->x[0];
+    A.y = in->x[1];
+    A.z = in->x[2];
+    A.mass = in->mass;
+    A.mass_abs = in->mass_abs;
+    A.perm = in->perm;
+    A.cell_start = in->cell_start;
+    A.ox = out->x[0];
+    A.oy = out->x[1];
+    A.oz = out->x[2];
+    A.omass = out->mass;
+    A.omass_abs = in->mass_abs ? out->mass_abs : nullptr;
+    A.ocoeff = out->coeff;
+    A.oscale = out->coeff_scale;
+    A.status = c->d_status;
+    for (int l = 0; l < 7; ++l) A.inv_dxpow[l] = (float)std::pow(c->cfg.dx, -(double)l);
+    int64_t tiles = c->num_keys / 256;
+    return from_cuda(g2p(A, tiles, c->cfg.num_modes, c->cfg.coeff_format, s));
+}
+
+polypic_status check_g2p_out(const polypic_ctx *c, const polypic_particles *in,
+                             const polypic_particles *out) {
+    if (!out || out->count != in->count) return POLYPIC_ERR_INVALID_ARG;
+    if (in->count == 0) return POLYPIC_OK;
+    if (!out->x[0] || !out->x[1] || !out->x[2] || !out->mass || !out->coeff)
+        return POLYPIC_ERR_INVALID_ARG;
+    if (c->cfg.coeff_format != POLYPIC_COEFF_F32 && !out->coeff_scale) return POLYPIC_ERR_INVALID_ARG;
+    if (in->mass_abs && !out->mass_abs) return POLYPIC_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (out->x[a] == in->x[b]) return POLYPIC_ERR_INVALID_ARG;
+    if (out->mass == in->mass || out->coeff == in->coeff) return POLYPIC_ERR_INVALID_ARG;
+    return POLYPIC_OK;
+}
+
+polypic_status check_params(const polypic_update_params *u) {
+    if (!u || !std::isfinite(u->dt) || !std::isfinite(u->gravity[0]) ||
+        !std::isfinite(u->gravity[1]) || !std::isfinite(u->gravity[2]) ||
+        !std::isfinite(u->drag_k) || u->drag_k < 0.0f)
+        return POLYPIC_ERR_INVALID_ARG;
+    if (u->project) {
+        if (!(u->rho > 0.0f) || u->pcg_maxiter <= 0 || !(u->pcg_rtol > 0.0))
+            return POLYPIC_ERR_INVALID_ARG;
+    }
+    return POLYPIC_OK;
+}
+
+polypic_status do_grid_update(polypic_ctx *c, polypic_grid *fluid, polypic_grid *solid,
+                              const polypic_particles *fp, const polypic_update_params *u,
+                              void *ws, size_t ws_bytes, cudaStream_t s) {
+    GridUpdateArgs U{};
+    U.g = c->geom;
+    U.dt = u->dt;
+    for (int a = 0; a < 3; ++a) {
+        U.gravity[a] = u->gravity[a];
+        U.fm[a] = fluid->mass[a];
+        U.fp[a] = fluid->mom[a];
+        U.fv[a] = fluid->vel[a];
+        U.sm[a] = solid ? solid->mass[a] : nullptr;
+        U.sp[a] = solid ? solid->mom[a] : nullptr;
+        U.sv[a] = solid ? solid->vel[a] : nullptr;
+    }
+    U.drag_k = u->drag_k;
+    polypic_status st = from_cuda(grid_update(U, s));
+    if (st != POLYPIC_OK || !u->project) return st;
+    Workspace W{static_cast<char *>(ws), ws_bytes, 0};
+    return pcg_project(c->geom, c->num_keys, fp->cell_start, fluid->vel, u->dt, u->rho,
+                       u->pcg_maxiter, u->pcg_rtol, c->d_status, W, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+polypic_status polypic_create(const polypic_config *cfg, polypic_ctx **out) {
+    if (!out) return POLYPIC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cfg) return POLYPIC_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (cfg->n[a] < 4 || cfg->n[a] > 2048) return POLYPIC_ERR_INVALID_ARG;
+    if (!(cfg->dx > 0.0) || !std::isfinite(cfg->dx)) return POLYPIC_ERR_INVALID_ARG;
+    if (!valid_modes(cfg->num_modes)) return POLYPIC_ERR_INVALID_ARG;
+    if (cfg->coeff_format < POLYPIC_COEFF_F32 || cfg->coeff_format > POLYPIC_COEFF_F16)
+        return POLYPIC_ERR_INVALID_ARG;
+    if (cfg->map == POLYPIC_MAP_AFFINE) return POLYPIC_ERR_UNSUPPORTED;
+    if (cfg->map != POLYPIC_MAP_CONSTANT) return POLYPIC_ERR_INVALID_ARG;
+    if (cfg->apic_variant == POLYPIC_APIC_GRAD_W) return POLYPIC_ERR_UNSUPPORTED;
+    if (cfg->apic_variant != POLYPIC_APIC_TRUNCATION) return POLYPIC_ERR_INVALID_ARG;
+
+    GridGeom g{};
+    for (int a = 0; a < 3; ++a) g.n[a] = cfg->n[a];
+    g.tiles[0] = (cfg->n[0] + 7) / 8;
+    g.tiles[1] = (cfg->n[1] + 7) / 8;
+    g.tiles[2] = (cfg->n[2] + 3) / 4;
+    int64_t K = (int64_t)g.tiles[0] * g.tiles[1] * g.tiles[2] * 256;
+    // scans handle up to 256 * 256 chunks of 4096 keys
+    if (K + 1 > (int64_t)kScanThreads * 256 * kScanTile) return POLYPIC_ERR_UNSUPPORTED;
+    g.dx = (float)cfg->dx;
+    g.inv_dx = (float)(1.0 / cfg->dx);
+    for (int a = 0; a < 3; ++a) {
+        g.lo[a] = (float)(1.5 * cfg->dx);
+        g.hi[a] = (float)(((double)cfg->n[a] - 1.5) * cfg->dx);
+    }
+
+    polypic_ctx *c = new (std::nothrow) polypic_ctx;
+    if (!c) return POLYPIC_ERR_CUDA;
+    c->cfg = *cfg;
+    c->geom = g;
+    c->num_keys = K;
+    c->d_status = nullptr;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaMalloc(&c->d_status, 4 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, 4 * sizeof(uint32_t)) != cudaSuccess) {
+        if (c->d_status) cudaFree(c->d_status);
+        delete c;
+        return POLYPIC_ERR_CUDA;
+    }
+    *out = c;
+    return POLYPIC_OK;
+}
+
+void polypic_destroy(polypic_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+int64_t polypic_num_keys(const polypic_ctx *ctx) { return ctx ? ctx->num_keys : -1; }
+
+uint32_t polypic_cell_key(const polypic_ctx *ctx, int32_t i, int32_t j, int32_t k) {
+    if (!ctx) return 0xffffffffu;
+    return cell_key(ctx->geom, i, j, k);
+}
+
+polypic_status polypic_grid_dims(const polypic_ctx *ctx, int32_t axis, int32_t dims[3]) {
+    if (!ctx || !dims || axis < 0 || axis > 2) return POLYPIC_ERR_INVALID_ARG;
+    for (int b = 0; b < 3; ++b) dims[b] = ctx->cfg.n[b] + (b == axis ? 1 : 0);
+    return POLYPIC_OK;
+}
+
+size_t polypic_workspace_bytes(const polypic_ctx *ctx, int64_t n_fluid, int64_t n_solid) {
+    if (!ctx || n_fluid < 0 || n_solid < 0) return 0;
+    return required_ws(ctx, n_fluid, n_solid);
+}
+
+polypic_status polypic_sort(polypic_ctx *ctx, polypic_particles *p, void *ws, size_t ws_bytes,
+                            void *stream) {
+    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s = check_sorted(p);
+    if (s != POLYPIC_OK) return s;
+    if ((s = check_ws(ctx, p->count, ws, ws_bytes)) != POLYPIC_OK) return s;
+    return do_sort(ctx, p, ws, ws_bytes, as_stream(stream));
+}
+
+polypic_status polypic_p2g(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
+                           void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s = check_sorted(p);
+    if (s != POLYPIC_OK) return s;
+    if ((s = check_coeff(ctx, p)) != POLYPIC_OK) return s;
+    if (!grid_ok(g, true, true, false)) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_ws(ctx, p->count, ws, ws_bytes)) != POLYPIC_OK) return s;
+    return do_p2g(ctx, p, g, ws, ws_bytes, as_stream(stream));
+}
+
+polypic_status polypic_grid_update(polypic_ctx *ctx, polypic_grid *fluid, polypic_grid *solid,
+                                   const polypic_particles *fluid_particles,
+                                   const polypic_update_params *params, void *ws,
+                                   size_t ws_bytes, void *stream) {
+    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    if (!grid_ok(fluid, true, true, true)) return POLYPIC_ERR_INVALID_ARG;
+    if (solid && !grid_ok(solid, true, true, true)) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s = check_params(params);
+    if (s != POLYPIC_OK) return s;
+    if (params->project) {
+        if (!fluid_particles || !fluid_particles->cell_start) return POLYPIC_ERR_INVALID_ARG;
+        if ((s = check_ws(ctx, 0, ws, ws_bytes)) != POLYPIC_OK) return s;
+    }
+    return do_grid_update(ctx, fluid, solid, fluid_particles, params, ws, ws_bytes,
+                          as_stream(stream));
+}
+
+polypic_status polypic_g2p(polypic_ctx *ctx, const polypic_grid *g, const polypic_particles *in,
+                           polypic_particles *out, float dt, void *ws, size_t ws_bytes,
+                           void *stream) {
+    (void)ws;
+    (void)ws_bytes;
+    if (!ctx || !std::isfinite(dt)) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s = check_sorted(in);
+    if (s != POLYPIC_OK) return s;
+    if (in->count > 0 && !in->mass) return POLYPIC_ERR_INVALID_ARG;
+    if (!grid_ok(g, false, false, true)) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_g2p_out(ctx, in, out)) != POLYPIC_OK) return s;
+    return do_g2p(ctx, g, in, out, dt, as_stream(stream));
+}
+
+polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
+                            polypic_particles *fluid_out, polypic_particles *solid_in,
+                            polypic_particles *solid_out, polypic_grid *gf, polypic_grid *gs,
+                            const polypic_update_params *params, void *ws, size_t ws_bytes,
+                            void *stream) {
+    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    const bool solid = solid_in != nullptr;
+    if (solid && (!solid_out || !gs)) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s;
+    if ((s = check_sorted(fluid_in)) != POLYPIC_OK) return s;
+    if (fluid_in->count > 0 && !fluid_in->key) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_coeff(ctx, fluid_in)) != POLYPIC_OK) return s;
+    if ((s = check_g2p_out(ctx, fluid_in, fluid_out)) != POLYPIC_OK) return s;
+    if (solid) {
+        if ((s = check_sorted(solid_in)) != POLYPIC_OK) return s;
+        if (solid_in->count > 0 && !solid_in->key) return POLYPIC_ERR_INVALID_ARG;
+        if ((s = check_coeff(ctx, solid_in)) != POLYPIC_OK) return s;
+        if ((s = check_g2p_out(ctx, solid_in, solid_out)) != POLYPIC_OK) return s;
+        if (!grid_ok(gs, true, true, true)) return POLYPIC_ERR_INVALID_ARG;
+    }
+    if (!grid_ok(gf, true, true, true)) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_params(params)) != POLYPIC_OK) return s;
+    const int64_t nmax = max64(fluid_in->count, solid ? solid_in->count : 0);
+    if ((s = check_ws(ctx, nmax, ws, ws_bytes)) != POLYPIC_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    if ((s = do_sort(ctx, fluid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
+    if ((s = do_p2g(ctx, fluid_in, gf, ws, ws_bytes, st)) != POLYPIC_OK) return s;
+    if (solid) {
+        if ((s = do_sort(ctx, solid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
+        if ((s = do_p2g(ctx, solid_in, gs, ws, ws_bytes, st)) != POLYPIC_OK) return s;
+    }
+    if ((s = do_grid_update(ctx, gf, solid ? gs : nullptr, fluid_in, params, ws, ws_bytes, st)) !=
+        POLYPIC_OK)
+        return s;
+    if ((s = do_g2p(ctx, gf, fluid_in, fluid_out, params->dt, st)) != POLYPIC_OK) return s;
+    if (solid && (s = do_g2p(ctx, gs, solid_in, solid_out, params->dt, st)) != POLYPIC_OK) return s;
+    return POLYPIC_OK;
+}
+
+polypic_status polypic_g2p_adjoint(polypic_ctx *ctx, const polypic_grid *g,
+                                   const polypic_particles *in, float dt,
+                                   const polypic_particles *bar_out, polypic_grid *bar_grid,
+                                   polypic_particles *bar_in, int32_t flags, void *ws,
+                                   size_t ws_bytes, void *stream) {
+    if (!ctx || !std::isfinite(dt)) return POLYPIC_ERR_INVALID_ARG;
+    if (ctx->cfg.coeff_format != POLYPIC_COEFF_F32) return POLYPIC_ERR_UNSUPPORTED;
+    polypic_status s = check_sorted(in);
+    if (s != POLYPIC_OK) return s;
+    if (!grid_ok(g, false, false, true) || !grid_ok(bar_grid, false, false, true))
+        return POLYPIC_ERR_INVALID_ARG;
+    if (!bar_out || !bar_in || bar_out->count != in->count || bar_in->count != in->count)
+        return POLYPIC_ERR_INVALID_ARG;
+    if (in->count > 0 && (!bar_out->coeff || !bar_out->x[0] || !bar_out->x[1] || !bar_out->x[2] ||
+                          !bar_in->x[0] || !bar_in->x[1] || !bar_in->x[2]))
+        return POLYPIC_ERR_INVALID_ARG;
+    if ((flags & ~POLYPIC_ADJ_ACCUMULATE) != 0) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_ws(ctx, in->count, ws, ws_bytes)) != POLYPIC_OK) return s;
+    Workspace W{static_cast<char *>(ws), ws_bytes, 0};
+    return from_cuda(adjoint_g2p(ctx->geom, ctx->num_keys, ctx->cfg.num_modes, (float)ctx->cfg.dx,
+                                 g, in, dt, bar_out, bar_grid, bar_in,
+                                 (flags & POLYPIC_ADJ_ACCUMULATE) != 0, ctx->d_status, W,
+                                 as_stream(stream)));
+}
+
+polypic_status polypic_grid_update_adjoint(polypic_ctx *ctx, const polypic_grid *g,
+                                           const polypic_update_params *params,
+                                           const polypic_grid *bar_out, polypic_grid *bar_in,
+                                           void *ws, size_t ws_bytes, void *stream) {
+    (void)ws;
+    (void)ws_bytes;
+    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s = check_params(params);
+    if (s != POLYPIC_OK) return s;
+    if (params->project || params->drag_k != 0.0f) return POLYPIC_ERR_UNSUPPORTED;
+    if (!grid_ok(g, true, true, false) || !grid_ok(bar_out, false, false, true) ||
+        !grid_ok(bar_in, true, true, false))
+        return POLYPIC_ERR_INVALID_ARG;
+    GridAdjointArgs U{};
+    U.g = ctx->geom;
+    for (int a = 0; a < 3; ++a) {
+        U.fm[a] = g->mass[a];
+        U.fp[a] = g->mom[a];
+        U.lv[a] = bar_out->vel[a];
+        U.lm[a] = bar_in->mass[a];
+        U.lp[a] = bar_in->mom[a];
+    }
+    return from_cuda(grid_update_adjoint(U, as_stream(stream)));
+}
+
+polypic_status polypic_p2g_adjoint(polypic_ctx *ctx, const polypic_particles *in,
+                                   const polypic_grid *bar_grid, polypic_particles *bar_in,
+                                   int32_t flags, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    if (ctx->cfg.coeff_format != POLYPIC_COEFF_F32) return POLYPIC_ERR_UNSUPPORTED;
+    polypic_status s = check_sorted(in);
+    if (s != POLYPIC_OK) return s;
+    if ((s = check_coeff(ctx, in)) != POLYPIC_OK) return s;
+    if (!grid_ok(bar_grid, true, true, false)) return POLYPIC_ERR_INVALID_ARG;
+    if (!bar_in || bar_in->count != in->count) return POLYPIC_ERR_INVALID_ARG;
+    if (in->count > 0 && (!bar_in->coeff || !bar_in->x[0] || !bar_in->x[1] || !bar_in->x[2]))
+        return POLYPIC_ERR_INVALID_ARG;
+    if ((flags & ~POLYPIC_ADJ_ACCUMULATE) != 0) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_ws(ctx, in->count, ws, ws_bytes)) != POLYPIC_OK) return s;
+    Workspace W{static_cast<char *>(ws), ws_bytes, 0};
+    return from_cuda(adjoint_p2g(ctx->geom, ctx->num_keys, ctx->cfg.num_modes, (float)ctx->cfg.dx,
+                                 in, bar_grid, bar_in, (flags & POLYPIC_ADJ_ACCUMULATE) != 0,
+                                 ctx->d_status, W, as_stream(stream)));
+}
+
+polypic_status polypic_check_device_status(polypic_ctx *ctx, void *stream) {
+    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return POLYPIC_ERR_CUDA;
+    uint32_t h = 0;
+    if (cudaMemcpy(&h, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return POLYPIC_ERR_CUDA;
+    if (h && cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return POLYPIC_ERR_CUDA;
+    if (h & kFlagOutOfDomain) return POLYPIC_ERR_OUT_OF_DOMAIN;
+    if (h & kFlagNonFinite) return POLYPIC_ERR_NONFINITE;
+    if (h & kFlagNotConverged) return POLYPIC_ERR_NOT_CONVERGED;
+    if (h & kFlagTimeout) return POLYPIC_ERR_TIMEOUT;
+    return POLYPIC_OK;
+}
+
+const char *polypic_status_string(polypic_status s) {
+    switch (s) {
+        case POLYPIC_OK: return "ok";
+        case POLYPIC_ERR_INVALID_ARG: return "invalid argument";
+        case POLYPIC_ERR_UNSUPPORTED: return "unsupported configuration";
+        case POLYPIC_ERR_OUT_OF_DOMAIN: return "particle outside the valid region";
+        case POLYPIC_ERR_NONFINITE: return "non-finite velocity";
+        case POLYPIC_ERR_NOT_CONVERGED: return "pressure solve did not converge";
+        case POLYPIC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case POLYPIC_ERR_CUDA: return "CUDA runtime error";
+        case POLYPIC_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// g2p.cu -- grid-to-particle transfer and mode fit (Eqs 6-8, Section 3.3),
+// with the advection fused in.
+//
+//   c_pra = sum_i w s_r v~_ia / d_r,  d_r = sum_i w s_r^2   (decoupled LSQ)
+//   v_p = c_p0,  x_p <- clamp(x_p + dt v_p, 1.5 dx, (n - 1.5) dx)
+//
+// One CTA per 8x8x4-cell tile.  The tile's velocity footprint on each face
+// grid (at most 11 x 10 x 7 nodes) is staged in shared memory with coalesced
+// loads; every thread then fits one particle at a time from the staged tile.
+// The fit is the transpose of P2G's sum factorisation with per-axis weights
+//   G0_k = W_k,  G1_k = W_k z_k / mu2 = 4 F1_k,  G2_k = W_k g_k / d_2 = (1,-2,1)/2
+// (z in cells): the quadratic fit is half the second difference for every t,
+// so no denominator is formed; the guard zeroes G2 on a guarded axis.  The
+// result is the dimensionless c dx^L; FP32 output divides by dx^L, the 16-bit
+// formats divide by the per-particle scale s_p = max |c dx^L| and round to
+// nearest even.  Outputs are written in sorted slot order (coalesced).
+#include "g2p.cuh"
+
+namespace polypic {
+
+constexpr int kG2PThreads = 256;
+// staged footprint per face grid: dims (11,10,6) (10,11,6) (10,10,7)
+template <int A> struct Tile {
+    static constexpr int X = A == 0 ? 11 : 10, Y = A == 1 ? 11 : 10, Z = A == 2 ? 7 : 6;
+    static constexpr int N = X * Y * Z;
+};
+constexpr int kTileOff1 = Tile<0>::N, kTileOff2 = Tile<0>::N + Tile<1>::N;
+constexpr int kTileFloats = Tile<0>::N + Tile<1>::N + Tile<2>::N;
+
+template <int D>
+__device__ __forceinline__ void fit_factors(const Stencil1D &s, bool guard, float (&G)[D][3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[0][k] = s.W[k];
+    if constexpr (D > 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G[1][k] = 4.0f * s.F1[k];
+    }
+    if constexpr (D > 2) {
+        const float h = guard ? 0.0f : 0.5f;
+        G[2][0] = h;
+        G[2][1] = -2.0f * h;
+        G[2][2] = h;
+    }
+}
+
+// Fit of component A for one particle; Chat receives the dimensionless
+// coefficients c dx^L in canonical order (only the first R entries are set).
+template <int R, int A>
+__device__ __forceinline__ void g2p_component(const float *s_tile, int lx, int ly, int lz,
+                                              const Stencil1D &sx, bool gx, const Stencil1D &sy,
+                                              bool gy, const Stencil1D &sz, bool gz,
+                                              float (&Chat)[R]) {
+    constexpr int D = axis_degrees(R);
+    float Gx[D][3], Gy[D][3], Gz[D][3];
+    fit_factors<D>(sx, gx, Gx);
+    fit_factors<D>(sy, gy, Gy);
+    fit_factors<D>(sz, gz, Gz);
+    const float *t = s_tile + (A == 0 ? 0 : A == 1 ? kTileOff1 : kTileOff2);
+    // contract x
+    float U1[D][3][3];
+#pragma unroll
+    for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+            const float *row = t + ((lz + kz) * Tile<A>::Y + (ly + ky)) * Tile<A>::X + lx;
+            const float v0 = row[0], v1 = row[1], v2 = row[2];
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                U1[a][ky][kz] = fmaf(Gx[a][0], v0, fmaf(Gx[a][1], v1, Gx[a][2] * v2));
+        }
+    // contract y
+    float U2[D][D][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+#pragma unroll
+            for (int kz = 0; kz < 3; ++kz)
+                U2[a][b][kz] = fmaf(Gy[b][0], U1[a][0][kz],
+                                    fmaf(Gy[b][1], U1[a][1][kz], Gy[b][2] * U1[a][2][kz]));
+    // contract z
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                if (has_mode(R, a, b, c))
+                    Chat[mode_index(a, b, c)] = fmaf(Gz[c][0], U2[a][b][0],
+                                                     fmaf(Gz[c][1], U2[a][b][1], Gz[c][2] * U2[a][b][2]));
+}
+
+template <int R, int FMT>
+__global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
+    __shared__ float s_tile[kTileFloats];
+    const GridGeom &g = A.g;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t jb = A.cell_start[tile * 256], je = A.cell_start[tile * 256 + 256];
+    if (jb == je) return;  // CTA-uniform
+    const int tx = (int)(tile % (uint32_t)g.tiles[0]);
+    const int ty = (int)((tile / (uint32_t)g.tiles[0]) % (uint32_t)g.tiles[1]);
+    const int tz = (int)(tile / ((uint32_t)g.tiles[0] * (uint32_t)g.tiles[1]));
+    const int ox = 8 * tx - 1, oy = 8 * ty - 1, oz = 4 * tz - 1;
+
+    // stage the three velocity footprints (nodes outside a grid read as 0)
+    auto stage = [&](int a, int X, int Y, int Z, int off) {
+        const int dX = g.n[0] + (a == 0), dY = g.n[1] + (a == 1), dZ = g.n[2] + (a == 2);
+        const float *src = A.vel[a];
+        for (int i = threadIdx.x; i < X * Y * Z; i += kG2PThreads) {
+            const int lx = i % X, ly = (i / X) % Y, lz = i / (X * Y);
+            const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+            float v = 0.0f;
+            if (gx >= 0 && gx < dX && gy >= 0 && gy < dY && gz >= 0 && gz < dZ)
+                v = src[((int64_t)gz * dY + gy) * dX + gx];
+            s_tile[off + i] = v;
+        }
+    };
+    stage(0, Tile<0>::X, Tile<0>::Y, Tile<0>::Z, 0);
+    stage(1, Tile<1>::X, Tile<1>::Y, Tile<1>::Z, kTileOff1);
+    stage(2, Tile<2>::X, Tile<2>::Y, Tile<2>::Z, kTileOff2);
+    __syncthreads();
+
+    using T = typename Codec<FMT>::T;
+    T *ocoeff = reinterpret_cast<T *>(A.ocoeff);
+    const int64_t cnt = A.count;
+    for (uint32_t j = jb + threadIdx.x; j < je; j += kG2PThreads) {
+        const uint32_t p = A.perm[j];
+        const float px = A.x[p], py = A.y[p], pz = A.z[p];
+        const float m = A.mass[p];
+        const float mabs = A.mass_abs ? A.mass_abs[p] : 0.0f;
+        const float v0 = cell_coord(px, g.inv_dx), v1 = cell_coord(py, g.inv_dx),
+                    v2 = cell_coord(pz, g.inv_dx);
+        bool ok = coord_valid(v0, g.n[0]) && coord_valid(v1, g.n[1]) && coord_valid(v2, g.n[2]);
+        const int ci = cell_index(v0, g.n[0]) - 8 * tx, cj = cell_index(v1, g.n[1]) - 8 * ty,
+                  ck = cell_index(v2, g.n[2]) - 4 * tz;
+        ok = ok && ci >= 0 && ci < 8 && cj >= 0 && cj < 8 && ck >= 0 && ck < 4;
+
+        float Chat[3][R];
+        if (ok) {
+            const Axis ac0 = axis_decide(v0, false), af0 = axis_decide(v0, true);
+            const Axis ac1 = axis_decide(v1, false), af1 = axis_decide(v1, true);
+            const Axis ac2 = axis_decide(v2, false), af2 = axis_decide(v2, true);
+            const Stencil1D sc0 = stencil_1d(ac0.t), sf0 = stencil_1d(af0.t);
+            const Stencil1D sc1 = stencil_1d(ac1.t), sf1 = stencil_1d(af1.t);
+            const Stencil1D sc2 = stencil_1d(ac2.t), sf2 = stencil_1d(af2.t);
+            g2p_component<R, 0>(s_tile, af0.base - ox, ac1.base - oy, ac2.base - oz, sf0,
+                                af0.guard, sc1, ac1.guard, sc2, ac2.guard, Chat[0]);
+            g2p_component<R, 1>(s_tile, ac0.base - ox, af1.base - oy, ac2.base - oz, sc0,
+                                ac0.guard, sf1, af1.guard, sc2, ac2.guard, Chat[1]);
+            g2p_component<R, 2>(s_tile, ac0.base - ox, ac1.base - oy, af2.base - oz, sc0,
+                                ac0.guard, sc1, ac1.guard, sf2, af2.guard, Chat[2]);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int r = 0; r < R; ++r) Chat[a][r] = 0.0f;
+        }
+        if (!ok) atomicOr(A.status, kFlagOutOfDomain);
+        const bool finite = isfinite(Chat[0][0]) && isfinite(Chat[1][0]) && isfinite(Chat[2][0]);
+        if (!finite) atomicOr(A.status, kFlagNonFinite);
+
+        if constexpr (FMT == POLYPIC_COEFF_F32) {
+            constexpr int D = axis_degrees(R);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int da = 0; da < D; ++da)
+#pragma unroll
+                    for (int db = 0; db < D; ++db)
+#pragma unroll
+                        for (int dc = 0; dc < D; ++dc)
+                            if (has_mode(R, da, db, dc)) {
+                                const int r = mode_index(da, db, dc);
+                                ocoeff[((int64_t)a * R + r) * cnt + j] =
+                                    Chat[a][r] * A.inv_dxpow[da + db + dc];
+                            }
+        } else {
+            float s = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int r = 0; r < R; ++r) s = fmaxf(s, fabsf(Chat[a][r]));
+            const float inv = s > 0.0f ? 1.0f / s : 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    ocoeff[((int64_t)a * R + r) * cnt + j] = Codec<FMT>::encode(Chat[a][r] * inv);
+            A.oscale[j] = s;
+        }
+        // advection with the fitted velocity (unquantised)
+        const float vx = ok ? Chat[0][0] : 0.0f, vy = ok ? Chat[1][0] : 0.0f,
+                    vz = ok ? Chat[2][0] : 0.0f;
+        A.ox[j] = ok ? fminf(fmaxf(fmaf(A.dt, vx, px), g.lo[0]), g.hi[0]) : px;
+        A.oy[j] = ok ? fminf(fmaxf(fmaf(A.dt, vy, py), g.lo[1]), g.hi[1]) : py;
+        A.oz[j] = ok ? fminf(fmaxf(fmaf(A.dt, vz, pz), g.lo[2]), g.hi[2]) : pz;
+        A.omass[j] = m;
+        if (A.omass_abs) A.omass_abs[j] = mabs;
+    }
+}
+
+cudaError_t g2p(const G2PArgs &A, int64_t num_tiles, int R, int fmt, cudaStream_t s) {
+    const int grid = (int)num_tiles;
+#define POLYPIC_G2P_CASE(RR, FF)                                          \
+    if (R == RR && fmt == FF) {                                          \
+        k_g2p_tiles<RR, FF><<<grid, kG2PThreads, 0, s>>>(A);             \
+        return cudaGetLastError();                                       \
+    }
+    POLYPIC_G2P_CASE(1, POLYPIC_COEFF_F32)
+    POLYPIC_G2P_CASE(4, POLYPIC_COEFF_F32)
+    POLYPIC_G2P_CASE(8, POLYPIC_COEFF_F32)
+    POLYPIC_G2P_CASE(27, POLYPIC_COEFF_F32)
+    POLYPIC_G2P_CASE(1, POLYPIC_COEFF_BF16)
+    POLYPIC_G2P_CASE(4, POLYPIC_COEFF_BF16)
+    POLYPIC_G2P_CASE(8, POLYPIC_COEFF_BF16)
+    POLYPIC_G2P_CASE(27, POLYPIC_COEFF_BF16)
+    POLYPIC_G2P_CASE(1, POLYPIC_COEFF_F16)
+    POLYPIC_G2P_CASE(4, POLYPIC_COEFF_F16)
+    POLYPIC_G2P_CASE(8, POLYPIC_COEFF_F16)
+    POLYPIC_G2P_CASE(27, POLYPIC_COEFF_F16)
+#undef POLYPIC_G2P_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace polypic

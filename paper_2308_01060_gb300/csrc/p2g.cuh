@@ -1,0 +1,38 @@
+// p2g.cuh -- host-side entry points of the P2G transfer (p2g.cu).
+#pragma once
+#include "polypic_internal.cuh"
+
+namespace polypic {
+
+// Node region of one 4x4x2-cell block on face grid a: nodes
+// [4bx - 1, 4bx - 1 + reg_x) x [4by - 1, ...) x [2bz - 1, 2bz - 1 + reg_z).
+__host__ __device__ constexpr int reg_x(int a) { return a == 0 ? 7 : 6; }
+__host__ __device__ constexpr int reg_y(int a) { return a == 1 ? 7 : 6; }
+__host__ __device__ constexpr int reg_z(int a) { return a == 2 ? 5 : 4; }
+__host__ __device__ constexpr int reg_size(int a) { return reg_x(a) * reg_y(a) * reg_z(a); }
+// Scratch layout of one block: [a][mass | momentum][reg_size(a)].
+__host__ __device__ constexpr int reg_off(int a, int which) {
+    return (a >= 1 ? 2 * reg_size(0) : 0) + (a >= 2 ? 2 * reg_size(1) : 0) +
+           which * reg_size(a);
+}
+constexpr int kRegionFloats = 2 * (reg_size(0) + reg_size(1) + reg_size(2));
+
+struct P2GArgs {
+    GridGeom g;
+    int64_t count;
+    const float *x, *y, *z, *mass, *mass_abs;
+    const void *coeff;
+    const float *scale;        // 16-bit formats: per-particle s_p
+    const uint32_t *perm, *cell_start;
+    float *scratch;            // p2g_scratch_bytes()
+    uint32_t *status;
+    uint32_t nblocks;          // num_keys / 32
+    float dxpow[7];            // dx^L, L = 0..6 (FP32 coefficients -> dimensionless)
+};
+
+size_t p2g_scratch_bytes(int64_t num_keys);
+
+// Writes all faces of gm[3] (mass) and gp[3] (momentum).
+cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], int R, int fmt, cudaStream_t s);
+
+}  // namespace polypic
