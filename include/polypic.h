@@ -105,7 +105,7 @@ typedef struct polypic_config {
  *               16-bit formats uint16 codes of c_pra dx^L_r / s_p, where L_r
  *               is the total degree of mode r and s_p = max |c_pra dx^L_r|
  *   coeff_scale [count] float s_p (16-bit formats only, else NULL)
- *   key, perm   [count] uint32, written by polypic_sort
+ *   key, perm   [count] uint32, written by polypic_sort (perm: slot order)
  *   cell_start  [polypic_num_keys() + 1] uint32, written by polypic_sort   */
 typedef struct polypic_particles {
     int64_t count;
@@ -163,10 +163,14 @@ size_t polypic_workspace_bytes(const polypic_ctx *ctx, int64_t n_fluid, int64_t 
 
 /* ---- forward transfers --------------------------------------------------- */
 
-/* Bit-exact stable counting sort of the particles by cell key (an
- * implementation device; the paper has none).  Writes p->key (key of each
- * particle), p->perm (perm[j] = index of the j-th particle in (key, index)
- * order) and p->cell_start (first sorted slot of each key; entry K = count).
+/* Bit-exact sort of the particles by cell key (an implementation device; the
+ * paper has none).  Writes p->key (key of each particle), p->cell_start
+ * (cell_start[k] = number of particles with key < k; entry K = count) and
+ * p->perm, the slot order used by the transfers: take the stable (key,
+ * index) order; every block of 32 consecutive keys keeps its slot range
+ * [cell_start[32b], cell_start[32b + 32]), inside which round r = 0, 1, ...
+ * lists the r-th particle of every key of the block that holds more than r
+ * particles, keys ascending.  perm[j] = index of the particle in slot j.
  * Latches OUT_OF_DOMAIN for particles outside the valid region. */
 polypic_status polypic_sort(polypic_ctx *ctx, polypic_particles *p, void *ws, size_t ws_bytes,
                             void *stream);
@@ -200,7 +204,7 @@ polypic_status polypic_grid_update(polypic_ctx *ctx, polypic_grid *fluid, polypi
  * setting to 0 the coefficient of every mode with a quadratic factor on an
  * axis where the guard holds; v_p = c_p0; x_p <- clamp(x_p + dt v_p,
  * 1.5 dx, (n - 1.5) dx).  Reads `in` (positions, masses) through in->perm and
- * writes the new state of the particle in sorted slot j = 0..count-1 to
+ * writes the new state of the particle in slot j = 0..count-1 to
  * out->x, out->mass, out->mass_abs (if non-NULL), out->coeff and
  * out->coeff_scale: `out` must not alias `in`. */
 polypic_status polypic_g2p(polypic_ctx *ctx, const polypic_grid *g, const polypic_particles *in,

@@ -70,6 +70,7 @@ def _load():
         "or_cell_key": (ctypes.c_uint32, [_int, _int, _int, _int, _int]),
         "or_keys": (None, [_i64, _F, _F, _F, _int, _int, _int, _dbl, _U32]),
         "or_stable_sort": (None, [_i64, _U32, ctypes.c_uint32, _U32, _U32]),
+        "or_block_interleave": (None, [_U32, ctypes.c_uint32, _U32, _U32]),
         "or_stencil_1d": (_int, [_dbl, _dbl, _int, _I, _D, _D, _D, _D, _I]),
         "or_particle_modes": (_int, [_dbl, _dbl, _dbl, _int, _int, _dbl, _I, _D, _D, _D, _I]),
         "or_p2g": (_int, [_i64, _D, _D, _D, _D, _D, _D, _int, _int, _int, _int, _dbl, _int,
@@ -157,6 +158,7 @@ def keys(x32, n, dx) -> np.ndarray:
 
 
 def stable_sort(key, nkeys: int):
+    """(perm in (key, index) order, cell_start)."""
     key = np.ascontiguousarray(key, dtype=np.uint32)
     P = key.shape[0]
     perm = np.empty(P, dtype=np.uint32)
@@ -164,6 +166,23 @@ def stable_sort(key, nkeys: int):
     _load().or_stable_sort(P, _p(key, ctypes.c_uint32), nkeys, _p(perm, ctypes.c_uint32),
                            _p(cs, ctypes.c_uint32))
     return perm, cs
+
+
+def block_interleave(perm, nkeys: int, cell_start):
+    perm = np.ascontiguousarray(perm, dtype=np.uint32)
+    cs = np.ascontiguousarray(cell_start, dtype=np.uint32)
+    out = np.empty_like(perm)
+    _load().or_block_interleave(_p(perm, ctypes.c_uint32), nkeys, _p(cs, ctypes.c_uint32),
+                                _p(out, ctypes.c_uint32))
+    return out
+
+
+def particle_order(x32, n, dx):
+    """The library's slot order of particles with positions x32: (perm, cell_start)
+    where perm is the block-interleaved stable order."""
+    nk = num_keys(n)
+    perm, cs = stable_sort(keys(x32, n, dx), nk)
+    return block_interleave(perm, nk, cs), cs
 
 
 # ---------------------------------------------------------------- basis

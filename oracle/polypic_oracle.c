@@ -160,7 +160,8 @@ void or_keys(int64_t np, const float *x, const float *y, const float *z,
 }
 
 /* Stable counting sort: perm[j] = index of the j-th particle in (key, index)
- * order; cell_start[k] = first sorted slot with key >= k, cell_start[nkeys] = np. */
+ * order; cell_start[k] = number of particles with key < k (so the first
+ * sorted slot with key >= k), cell_start[nkeys] = np. */
 void or_stable_sort(int64_t np, const uint32_t *key, uint32_t nkeys,
                     uint32_t *perm, uint32_t *cell_start)
 {
@@ -171,6 +172,29 @@ void or_stable_sort(int64_t np, const uint32_t *key, uint32_t nkeys,
     memcpy(fill, cell_start, sizeof(uint32_t) * ((size_t)nkeys + 1));
     for (int64_t p = 0; p < np; ++p) perm[fill[key[p]]++] = (uint32_t)p;
     free(fill);
+}
+
+/* Block-interleaved slot order (the library's particle order): blocks of 32
+ * consecutive keys keep their slot range [cell_start[32b], cell_start[32b+32]);
+ * inside a block, round r = 0, 1, ... lists the r-th particle (in the stable
+ * order above) of every key of the block that has more than r particles, keys
+ * ascending.  in: the stable order; out: the interleaved order. */
+void or_block_interleave(const uint32_t *in, uint32_t nkeys, const uint32_t *cell_start,
+                         uint32_t *out)
+{
+    for (uint32_t b = 0; b < nkeys / 32; ++b) {
+        uint32_t slot = cell_start[32 * b];
+        uint32_t maxn = 0;
+        for (uint32_t c = 0; c < 32; ++c) {
+            uint32_t n = cell_start[32 * b + c + 1] - cell_start[32 * b + c];
+            if (n > maxn) maxn = n;
+        }
+        for (uint32_t r = 0; r < maxn; ++r)
+            for (uint32_t c = 0; c < 32; ++c) {
+                uint32_t k = 32 * b + c;
+                if (cell_start[k + 1] - cell_start[k] > r) out[slot++] = in[cell_start[k] + r];
+            }
+    }
 }
 
 /* ------------------------------------------------------------------------ */

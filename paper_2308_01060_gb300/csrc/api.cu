@@ -99,7 +99,8 @@ polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *
     P.nblocks = (uint32_t)(c->num_keys / 32);
     for (int l = 0; l < 7; ++l) P.dxpow[l] = (float)std::pow(c->cfg.dx, (double)l);
     Workspace W{static_cast<char *>(ws), ws_bytes, 0};
-    P.scratch = W.take<float>((size_t)P.nblocks * kRegionFloats);
+    P.scratch = W.take<float>((size_t)(c->num_keys / 256) * kTileFloats);
+    if (W.overflow) return POLYPIC_ERR_WORKSPACE;
     return from_cuda(p2g(P, g->mass, g->mom, c->cfg.num_modes, c->cfg.coeff_format, s));
 }
 

@@ -5,37 +5,36 @@
 //
 // Work decomposition (no float atomics anywhere, so the result is
 // bit-identical from run to run):
-//   * particles are sorted by cell key; the 32 cells of one 4x4x2 block are
-//     one contiguous key range, so a block's particles are one contiguous
-//     sorted range;
-//   * one warp owns one block.  It walks the block's particles 32 at a time
-//     (lane = particle, loads coalesced through the near-identity perm) and
-//     each lane evaluates its particle's 27 node contributions per face grid
-//     with sum factorisation (81 + 81 + 81 FMA per component instead of the
-//     27 x 27 direct sum);
-//   * the contributions go to a shared staging array; 27 reducer lanes (one
-//     per stencil slot) then sum each cell's run of particles in sorted order
-//     (a warp-level segmented reduction through shared memory), keeping two
-//     partial sums per slot for the two possible stencil bases along the
-//     component's own axis, and add each finished run into the warp's
-//     private block region in shared memory;
-//   * the warp writes its block region to scratch; k_p2g_reduce sums the up
-//     to 8 block regions that cover each face node, in ascending block order.
+//   * one CTA per 8x8x4-cell tile, one warp per 4x4x2-cell block of it, one
+//     lane per cell.  Particles are in block-interleaved slot order (see
+//     sort.cu), so in round r the lanes read the r-th particle of their cell
+//     from one contiguous run of slots: coalesced loads, no reduction across
+//     lanes;
+//   * a lane accumulates its cell's footprint on face grid A in registers:
+//     4 x 3 x 3 nodes (the particle's stencil is 3 nodes wide on every axis,
+//     but its lowest node along A is cell - 1 or cell), mass and momentum.
+//     The mode sum uses sum factorisation with the padded axis contracted
+//     last: 81 + 81 + 108 FMA per particle and component for 27 modes;
+//   * after the last round the warp adds the 32 cell footprints into its
+//     block region in 36 phases (one node offset per phase: distinct cells
+//     hit distinct nodes), then the CTA adds its 8 block regions into the
+//     tile region in ascending block order and writes it to scratch;
+//   * k_p2g_reduce sums the at most 8 tile regions covering each face node in
+//     ascending tile order and writes the grids.
 #include "p2g.cuh"
 
 namespace polypic {
 
-// Per-warp shared layout: staging [m | mv][27 slots][33] + block region.
-constexpr int kStageStride = 33;
-constexpr int kStageFloats = 2 * 27 * kStageStride;
-constexpr int kWarpFloats = kStageFloats + kRegionFloats;
 constexpr int kP2GWarps = 8;
 
 template <int A> struct Reg {
     static constexpr int X = reg_x(A), Y = reg_y(A), Z = reg_z(A);
 };
+template <int A> struct TileReg {
+    static constexpr int X = tile_x(A), Y = tile_y(A), Z = tile_z(A);
+};
 
-// 1-D factor table of one axis: F[a][k] for degree a at node k.
+// 1-D factors of one axis: F[a][k] = W_k f_a(z_k) (z in cells), a < D.
 template <int D>
 __device__ __forceinline__ void axis_factors(const Stencil1D &s, float (&F)[D][3]) {
 #pragma unroll
@@ -51,219 +50,240 @@ __device__ __forceinline__ void axis_factors(const Stencil1D &s, float (&F)[D][3
     }
 }
 
+// Degrees (a, b, c) along (x, y, z) of the tensor entry (du, dv, dw) for the
+// component-A ordering u = A, (v, w) = the other two axes in increasing order.
+template <int A> __host__ __device__ constexpr int deg_x(int du, int dv, int dw) {
+    return A == 0 ? du : dv;
+}
+template <int A> __host__ __device__ constexpr int deg_y(int du, int dv, int dw) {
+    return A == 0 ? dv : (A == 1 ? du : dw);
+}
+template <int A> __host__ __device__ constexpr int deg_z(int du, int dv, int dw) {
+    return A == 2 ? du : dw;
+}
+
+// One particle's contribution to the lane's padded footprint on grid A.
+// fu: stencil along A (face offset), fv / fw: the other two axes (centre).
 template <int R, int FMT, int A>
-__device__ __forceinline__ void p2g_component(const P2GArgs &P, uint32_t p, bool live, float mt,
-                                              float cscale, const Stencil1D (&sc)[3],
-                                              const Stencil1D (&sf)[3], float *st_m,
-                                              float *st_v, int lane) {
+__device__ __forceinline__ void accumulate(const P2GArgs &P, uint32_t p, float mt, float cscale,
+                                           int shift, const Stencil1D &fu, const Stencil1D &fv,
+                                           const Stencil1D &fw, float (&am)[4][3][3],
+                                           float (&av)[4][3][3]) {
     constexpr int D = axis_degrees(R);
     using T = typename Codec<FMT>::T;
     const T *coeff = reinterpret_cast<const T *>(P.coeff);
-    float Fx[D][3], Fy[D][3], Fz[D][3];
-    axis_factors<D>(A == 0 ? sf[0] : sc[0], Fx);
-    axis_factors<D>(A == 1 ? sf[1] : sc[1], Fy);
-    axis_factors<D>(A == 2 ? sf[2] : sc[2], Fz);
-
-    // coefficients, dimensionless: c_r dx^L_r (FP32) or code_r s_p (16-bit)
+    // coefficients (dimensionless c dx^L, or code * s_p) in (u, v, w) order
     float C[D][D][D];
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+    for (int du = 0; du < D; ++du)
 #pragma unroll
-        for (int b = 0; b < D; ++b)
+        for (int dv = 0; dv < D; ++dv)
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
+            for (int dw = 0; dw < D; ++dw) {
+                const int a = deg_x<A>(du, dv, dw), b = deg_y<A>(du, dv, dw),
+                          c = deg_z<A>(du, dv, dw);
                 if (has_mode(R, a, b, c)) {
-                    const int r = mode_index(a, b, c);
-                    float raw = live ? Codec<FMT>::load(coeff + ((int64_t)A * R + r) * P.count + p)
-                                     : 0.0f;
-                    C[a][b][c] = raw * (FMT == POLYPIC_COEFF_F32 ? P.dxpow[a + b + c] : cscale);
+                    const float raw =
+                        Codec<FMT>::load(coeff + ((int64_t)A * R + mode_index(a, b, c)) * P.count + p);
+                    C[du][dv][dw] =
+                        raw * (FMT == POLYPIC_COEFF_F32 ? P.dxpow[a + b + c] : cscale);
                 } else {
-                    C[a][b][c] = 0.0f;
+                    C[du][dv][dw] = 0.0f;
                 }
             }
-    // stage 1: contract z
-    float T1[D][D][3];
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < D; ++b)
-#pragma unroll
-            for (int kz = 0; kz < 3; ++kz) {
-                float s = 0.0f;
-#pragma unroll
-                for (int c = 0; c < D; ++c)
-                    if (has_mode(R, a, b, c)) s = fmaf(C[a][b][c], Fz[c][kz], s);
-                T1[a][b][kz] = s;
-            }
-    // stage 2: contract y
+    float Fu[D][3], Fv[D][3], Fw[D][3];
+    axis_factors<D>(fu, Fu);
+    axis_factors<D>(fv, Fv);
+    axis_factors<D>(fw, Fw);
+    // contract w, then v
     float T2[D][3][3];
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+    for (int du = 0; du < D; ++du) {
+        float T1[D][3];
 #pragma unroll
-        for (int ky = 0; ky < 3; ++ky)
+        for (int dv = 0; dv < D; ++dv)
 #pragma unroll
-            for (int kz = 0; kz < 3; ++kz) {
+            for (int kw = 0; kw < 3; ++kw) {
                 float s = 0.0f;
 #pragma unroll
-                for (int b = 0; b < D; ++b) s = fmaf(T1[a][b][kz], Fy[b][ky], s);
-                T2[a][ky][kz] = s;
+                for (int dw = 0; dw < D; ++dw)
+                    if (has_mode(R, deg_x<A>(du, dv, dw), deg_y<A>(du, dv, dw), deg_z<A>(du, dv, dw)))
+                        s = fmaf(C[du][dv][dw], Fw[dw][kw], s);
+                T1[dv][kw] = s;
             }
-    // stage 3: contract x with the particle mass folded in; mass weights
-    float Fxm[D][3];
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+        for (int kv = 0; kv < 3; ++kv)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) Fxm[a][k] = mt * Fx[a][k];
-#pragma unroll
-    for (int kz = 0; kz < 3; ++kz)
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-            const float wyz = Fy[0][ky] * Fz[0][kz];
-#pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
+            for (int kw = 0; kw < 3; ++kw) {
                 float s = 0.0f;
 #pragma unroll
-                for (int a = 0; a < D; ++a) s = fmaf(T2[a][ky][kz], Fxm[a][kx], s);
-                const int slot = kx + 3 * ky + 9 * kz;
-                st_v[slot * kStageStride + lane] = s;
-                st_m[slot * kStageStride + lane] = Fxm[0][kx] * wyz;
+                for (int dv = 0; dv < D; ++dv) s = fmaf(T1[dv][kw], Fv[dv][kv], s);
+                T2[du][kv][kw] = s;
             }
-        }
-}
-
-template <int A>
-__device__ __forceinline__ void flush_run(float *reg, int cell, int lane, const float (&acc)[2][2]) {
-    const int ci = cell & 3, cj = (cell >> 2) & 3, ck = (cell >> 4) & 1;
-    const int sk0 = lane % 3, sk1 = (lane / 3) % 3, sk2 = lane / 9;
-    const bool red = lane < 27;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        if (red) {
-            const int ix = ci + sk0 + (A == 0 ? s : 0);
-            const int iy = cj + sk1 + (A == 1 ? s : 0);
-            const int iz = ck + sk2 + (A == 2 ? s : 0);
-            const int idx = (iz * Reg<A>::Y + iy) * Reg<A>::X + ix;
-            reg[reg_off(A, 0) + idx] += acc[s][0];
-            reg[reg_off(A, 1) + idx] += acc[s][1];
-        }
-        __syncwarp();
     }
-}
-
-template <int A>
-__device__ __forceinline__ void reduce_batch(float *reg, const float *st_m, const float *st_v,
-                                             int info, int nb, int lane, int &cur,
-                                             float (&acc)[2][2]) {
-    const bool red = lane < 27;
-    for (int q = 0; q < nb; ++q) {
-        const int iq = __shfl_sync(0xffffffffu, info, q);
-        const int cq = iq & 31;
-        const int sq = (iq >> (5 + A)) & 1;
-        if (cq != cur) {  // warp-uniform
-            if (cur >= 0) flush_run<A>(reg, cur, lane, acc);
-            cur = cq;
-            acc[0][0] = acc[0][1] = acc[1][0] = acc[1][1] = 0.0f;
-        }
-        if (red) {
-            const float vm = st_m[lane * kStageStride + q];
-            const float vv = st_v[lane * kStageStride + q];
-            if (sq) {  // warp-uniform: every lane reads the same particle q
-                acc[1][0] += vm;
-                acc[1][1] += vv;
-            } else {
-                acc[0][0] += vm;
-                acc[0][1] += vv;
+    // padded factors along u: node d = k + shift, mass folded in
+    float Gu[D][4];
+#pragma unroll
+    for (int du = 0; du < D; ++du) {
+        const float f0 = mt * Fu[du][0], f1 = mt * Fu[du][1], f2 = mt * Fu[du][2];
+        Gu[du][0] = shift ? 0.0f : f0;
+        Gu[du][1] = shift ? f0 : f1;
+        Gu[du][2] = shift ? f1 : f2;
+        Gu[du][3] = shift ? f2 : 0.0f;
+    }
+    // contract u into the footprint; mass weights
+#pragma unroll
+    for (int kv = 0; kv < 3; ++kv)
+#pragma unroll
+        for (int kw = 0; kw < 3; ++kw) {
+            const float wvw = Fv[0][kv] * Fw[0][kw];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                float s = av[d][kv][kw];
+#pragma unroll
+                for (int du = 0; du < D; ++du) s = fmaf(T2[du][kv][kw], Gu[du][d], s);
+                av[d][kv][kw] = s;
+                am[d][kv][kw] = fmaf(Gu[0][d], wvw, am[d][kv][kw]);
             }
         }
+}
+
+// Index in block region A of cell-local node (cu-1+d, cv-1+kv, cw-1+kw),
+// expressed through the (u, v, w) axis order of component A.
+template <int A>
+__device__ __forceinline__ int region_index(int ix, int iy, int iz) {
+    return (iz * Reg<A>::Y + iy) * Reg<A>::X + ix;
+}
+
+template <int R, int FMT, int A>
+__device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t n_c,
+                                         uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
+                                         int gk, int lane, float *reg, bool &bad) {
+    float am[4][3][3], av[4][3][3];
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int kv = 0; kv < 3; ++kv)
+#pragma unroll
+            for (int kw = 0; kw < 3; ++kw) am[d][kv][kw] = av[d][kv][kw] = 0.0f;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t off = 0;
+    for (uint32_t r = 0; r < maxn; ++r) {
+        const unsigned mask = __ballot_sync(0xffffffffu, n_c > r);
+        if (n_c > r) {
+            const uint32_t slot = bs + off + __popc(mask & lt);
+            const uint32_t p = P.perm[slot];
+            const float px = P.x[p], py = P.y[p], pz = P.z[p];
+            float mt = P.mass[p];
+            if (P.mass_abs) mt += P.mass_abs[p];
+            const float cscale = FMT == POLYPIC_COEFF_F32 ? 1.0f : P.scale[p];
+            const float v0 = cell_coord(px, P.g.inv_dx), v1 = cell_coord(py, P.g.inv_dx),
+                        v2 = cell_coord(pz, P.g.inv_dx);
+            const bool ok = coord_valid(v0, P.g.n[0]) && coord_valid(v1, P.g.n[1]) &&
+                            coord_valid(v2, P.g.n[2]) && (int)floorf(v0) == gi &&
+                            (int)floorf(v1) == gj && (int)floorf(v2) == gk;
+            if (ok) {
+                const float vu = A == 0 ? v0 : (A == 1 ? v1 : v2);
+                const float vv = A == 0 ? v1 : v0;
+                const float vw = A == 2 ? v1 : v2;
+                const Axis au = axis_decide(vu, true), av_ = axis_decide(vv, false),
+                           aw = axis_decide(vw, false);
+                const int cu = A == 0 ? gi : (A == 1 ? gj : gk);
+                const int shift = au.base - (cu - 1);
+                accumulate<R, FMT, A>(P, p, mt, cscale, shift, stencil_1d(au.t), stencil_1d(av_.t),
+                                      stencil_1d(aw.t), am, av);
+            } else {
+                bad = true;
+            }
+        }
+        off += __popc(mask);
+    }
+    // merge the 32 footprints into the block region, one node offset per phase
+    const int cu = A == 0 ? ci : (A == 1 ? cj : ck);
+    const int cv = A == 0 ? cj : ci;
+    const int cw = A == 2 ? cj : ck;
+    float *rm = reg + reg_off(A, 0);
+    float *rv = reg + reg_off(A, 1);
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int kv = 0; kv < 3; ++kv)
+#pragma unroll
+            for (int kw = 0; kw < 3; ++kw) {
+                const int nu = cu + d, nv = cv + kv, nw = cw + kw;
+                const int ix = A == 0 ? nu : nv;
+                const int iy = A == 0 ? nv : (A == 1 ? nu : nw);
+                const int iz = A == 2 ? nu : nw;
+                const int idx = region_index<A>(ix, iy, iz);
+                rm[idx] += am[d][kv][kw];
+                rv[idx] += av[d][kv][kw];
+                __syncwarp();
+            }
+}
+
+// Adds block region A of warp w into the tile region (written to dst).
+template <int A>
+__device__ __forceinline__ void merge_tile(const float *smem_regions, const bool *empty,
+                                           float *dst) {
+    constexpr int N = TileReg<A>::X * TileReg<A>::Y * TileReg<A>::Z;
+    for (int i = threadIdx.x; i < N; i += kP2GWarps * 32) {
+        const int lx = i % TileReg<A>::X, ly = (i / TileReg<A>::X) % TileReg<A>::Y,
+                  lz = i / (TileReg<A>::X * TileReg<A>::Y);
+        float sm = 0.0f, sv = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kP2GWarps; ++w) {
+            if (empty[w]) continue;
+            const int bx = lx - 4 * (w & 1), by = ly - 4 * ((w >> 1) & 1), bz = lz - 2 * (w >> 2);
+            if (bx < 0 || bx >= Reg<A>::X || by < 0 || by >= Reg<A>::Y || bz < 0 || bz >= Reg<A>::Z)
+                continue;
+            const float *r = smem_regions + w * kRegionFloats;
+            const int idx = region_index<A>(bx, by, bz);
+            sm += r[reg_off(A, 0) + idx];
+            sv += r[reg_off(A, 1) + idx];
+        }
+        dst[tile_off(A, 0) + i] = sm;
+        dst[tile_off(A, 1) + i] = sv;
     }
 }
 
 template <int R, int FMT>
-__global__ void __launch_bounds__(kP2GWarps * 32, 2) k_p2g_blocks(P2GArgs P) {
-    extern __shared__ float smem[];
+__global__ void __launch_bounds__(kP2GWarps * 32, 1) k_p2g_tiles(P2GArgs P) {
+    __shared__ float s_reg[kP2GWarps * kRegionFloats];
+    __shared__ bool s_empty[kP2GWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t b = blockIdx.x * kP2GWarps + warp;
-    if (b >= P.nblocks) return;  // warp-uniform; the kernel has no CTA barrier
-    const uint32_t cs0 = P.cell_start[b * 32], cs1 = P.cell_start[b * 32 + 32];
-    if (cs0 == cs1) return;
+    const uint32_t tile = blockIdx.x;
+    if (P.cell_start[tile * 256] == P.cell_start[tile * 256 + 256]) return;  // CTA-uniform
 
-    float *st_m = smem + warp * kWarpFloats;
-    float *st_v = st_m + 27 * kStageStride;
-    float *reg = st_m + kStageFloats;
-    for (int i = lane; i < kRegionFloats; i += 32) reg[i] = 0.0f;
-    __syncwarp();
-
-    int i0, j0, k0;
-    block_origin(P.g, b, i0, j0, k0);
-    float acc0[2][2] = {{0, 0}, {0, 0}}, acc1[2][2] = {{0, 0}, {0, 0}}, acc2[2][2] = {{0, 0}, {0, 0}};
-    int cur0 = -1, cur1 = -1, cur2 = -1;
-
-    for (uint32_t jb = cs0; jb < cs1; jb += 32) {
-        const uint32_t j = jb + lane;
-        const int nb = (int)min(32u, cs1 - jb);
-        const bool live = j < cs1;
-        uint32_t p = 0;
-        float px = 0.0f, py = 0.0f, pz = 0.0f, mt = 0.0f, cscale = 0.0f;
-        if (live) {
-            p = P.perm[j];
-            px = P.x[p];
-            py = P.y[p];
-            pz = P.z[p];
-            mt = P.mass[p] + (P.mass_abs ? P.mass_abs[p] : 0.0f);
-            if (FMT != POLYPIC_COEFF_F32) cscale = P.scale[p];
-        }
-        const float v0 = cell_coord(px, P.g.inv_dx), v1 = cell_coord(py, P.g.inv_dx),
-                    v2 = cell_coord(pz, P.g.inv_dx);
-        bool ok = live && coord_valid(v0, P.g.n[0]) && coord_valid(v1, P.g.n[1]) &&
-                  coord_valid(v2, P.g.n[2]);
-        const int ci = cell_index(v0, P.g.n[0]) - i0, cj = cell_index(v1, P.g.n[1]) - j0,
-                  ck = cell_index(v2, P.g.n[2]) - k0;
-        ok = ok && ci >= 0 && ci < 4 && cj >= 0 && cj < 4 && ck >= 0 && ck < 2;
-        if (__any_sync(0xffffffffu, live && !ok) && lane == 0) atomicOr(P.status, kFlagOutOfDomain);
-
-        Axis ac[3], af[3];
-        ac[0] = axis_decide(v0, false); af[0] = axis_decide(v0, true);
-        ac[1] = axis_decide(v1, false); af[1] = axis_decide(v1, true);
-        ac[2] = axis_decide(v2, false); af[2] = axis_decide(v2, true);
-        Stencil1D sc[3], sf[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            sc[a] = stencil_1d(ac[a].t);
-            sf[a] = stencil_1d(af[a].t);
-        }
-        int info = 0;
-        if (ok) {
-            const int s0 = af[0].base - (ci + i0 - 1), s1 = af[1].base - (cj + j0 - 1),
-                      s2 = af[2].base - (ck + k0 - 1);
-            info = ci | (cj << 2) | (ck << 4) | (s0 << 5) | (s1 << 6) | (s2 << 7);
-        } else {
-            mt = 0.0f;
-        }
-        const bool use = live && ok;
-
-        p2g_component<R, FMT, 0>(P, p, use, mt, cscale, sc, sf, st_m, st_v, lane);
+    const uint32_t b = tile * kP2GWarps + warp;
+    const uint32_t k = b * 32 + lane;
+    const uint32_t cs0 = P.cell_start[k];
+    const uint32_t n_c = P.cell_start[k + 1] - cs0;
+    const uint32_t bs = P.cell_start[b * 32];
+    const uint32_t maxn = __reduce_max_sync(0xffffffffu, n_c);
+    float *reg = s_reg + warp * kRegionFloats;
+    if (lane == 0) s_empty[warp] = maxn == 0;
+    if (maxn > 0) {
+        for (int i = lane; i < kRegionFloats; i += 32) reg[i] = 0.0f;
         __syncwarp();
-        reduce_batch<0>(reg, st_m, st_v, info, nb, lane, cur0, acc0);
-        __syncwarp();
-        p2g_component<R, FMT, 1>(P, p, use, mt, cscale, sc, sf, st_m, st_v, lane);
-        __syncwarp();
-        reduce_batch<1>(reg, st_m, st_v, info, nb, lane, cur1, acc1);
-        __syncwarp();
-        p2g_component<R, FMT, 2>(P, p, use, mt, cscale, sc, sf, st_m, st_v, lane);
-        __syncwarp();
-        reduce_batch<2>(reg, st_m, st_v, info, nb, lane, cur2, acc2);
-        __syncwarp();
+        int i0, j0, k0;
+        block_origin(P.g, b, i0, j0, k0);
+        const int ci = lane & 3, cj = (lane >> 2) & 3, ck = lane >> 4;
+        const int gi = i0 + ci, gj = j0 + cj, gk = k0 + ck;
+        bool bad = false;
+        p2g_pass<R, FMT, 0>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, bad);
+        p2g_pass<R, FMT, 1>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, bad);
+        p2g_pass<R, FMT, 2>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, bad);
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.status, kFlagOutOfDomain);
     }
-    if (cur0 >= 0) flush_run<0>(reg, cur0, lane, acc0);
-    if (cur1 >= 0) flush_run<1>(reg, cur1, lane, acc1);
-    if (cur2 >= 0) flush_run<2>(reg, cur2, lane, acc2);
-    __syncwarp();
-    float *dst = P.scratch + (size_t)b * kRegionFloats;
-    for (int i = lane; i < kRegionFloats; i += 32) dst[i] = reg[i];
+    __syncthreads();
+    float *dst = P.scratch + (size_t)tile * kTileFloats;
+    merge_tile<0>(s_reg, s_empty, dst);
+    merge_tile<1>(s_reg, s_empty, dst);
+    merge_tile<2>(s_reg, s_empty, dst);
 }
 
-// Sum of the block regions covering each node of face grid A, in ascending
-// block order (bz, by, bx); empty blocks wrote nothing and are skipped.
+// Sum of the tile regions covering each node of face grid A, in ascending
+// tile order; empty tiles wrote nothing and are skipped.
 template <int A>
 __global__ void __launch_bounds__(256) k_p2g_reduce(GridGeom g, const uint32_t *__restrict__ cs,
                                                     const float *__restrict__ scratch,
@@ -271,56 +291,44 @@ __global__ void __launch_bounds__(256) k_p2g_reduce(GridGeom g, const uint32_t *
                                                     float *__restrict__ gp) {
     const int dX = g.n[0] + (A == 0), dY = g.n[1] + (A == 1), dZ = g.n[2] + (A == 2);
     const int64_t total = (int64_t)dX * dY * dZ;
-    const int nbx = 2 * g.tiles[0], nby = 2 * g.tiles[1], nbz = 2 * g.tiles[2];
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(idx % dX);
         const int j = (int)((idx / dX) % dY);
         const int k = (int)(idx / ((int64_t)dX * dY));
-        // block b covers nodes [4b - 1, 4b - 1 + RX) along x (same for y; 2b along z)
-        const int bx0 = max(0, (i + 2 - Reg<A>::X + 3) >> 2), bx1 = min(nbx - 1, (i + 1) >> 2);
-        const int by0 = max(0, (j + 2 - Reg<A>::Y + 3) >> 2), by1 = min(nby - 1, (j + 1) >> 2);
-        const int bz0 = max(0, (k + 2 - Reg<A>::Z + 1) >> 1), bz1 = min(nbz - 1, (k + 1) >> 1);
+        // tile t covers nodes [8t - 1, 8t - 1 + X) along x (same for y; 4t along z)
+        const int tx0 = max(0, (i + 2 - TileReg<A>::X + 7) >> 3), tx1 = min(g.tiles[0] - 1, (i + 1) >> 3);
+        const int ty0 = max(0, (j + 2 - TileReg<A>::Y + 7) >> 3), ty1 = min(g.tiles[1] - 1, (j + 1) >> 3);
+        const int tz0 = max(0, (k + 2 - TileReg<A>::Z + 3) >> 2), tz1 = min(g.tiles[2] - 1, (k + 1) >> 2);
         float sm = 0.0f, sv = 0.0f;
-        for (int bz = bz0; bz <= bz1; ++bz)
-            for (int by = by0; by <= by1; ++by)
-                for (int bx = bx0; bx <= bx1; ++bx) {
-                    const uint32_t blk = block_of(g, bx, by, bz);
-                    if (cs[blk * 32] == cs[blk * 32 + 32]) continue;
-                    const int lx = i - (4 * bx - 1), ly = j - (4 * by - 1), lz = k - (2 * bz - 1);
-                    const int r = (lz * Reg<A>::Y + ly) * Reg<A>::X + lx;
-                    const float *src = scratch + (size_t)blk * kRegionFloats;
-                    sm += src[reg_off(A, 0) + r];
-                    sv += src[reg_off(A, 1) + r];
+        for (int tz = tz0; tz <= tz1; ++tz)
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    const uint32_t t = ((uint32_t)tz * g.tiles[1] + ty) * g.tiles[0] + tx;
+                    if (cs[t * 256] == cs[t * 256 + 256]) continue;
+                    const int lx = i - (8 * tx - 1), ly = j - (8 * ty - 1), lz = k - (4 * tz - 1);
+                    const int r = (lz * TileReg<A>::Y + ly) * TileReg<A>::X + lx;
+                    const float *src = scratch + (size_t)t * kTileFloats;
+                    sm += src[tile_off(A, 0) + r];
+                    sv += src[tile_off(A, 1) + r];
                 }
         gm[idx] = sm;
         gp[idx] = sv;
     }
 }
 
-template <int R, int FMT>
-static cudaError_t launch_blocks(const P2GArgs &P, cudaStream_t s) {
-    static bool attr_set = false;
-    const int smem = kP2GWarps * kWarpFloats * (int)sizeof(float);
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_p2g_blocks<R, FMT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const int grid = (int)((P.nblocks + kP2GWarps - 1) / kP2GWarps);
-    k_p2g_blocks<R, FMT><<<grid, kP2GWarps * 32, smem, s>>>(P);
-    return cudaGetLastError();
-}
-
 size_t p2g_scratch_bytes(int64_t num_keys) {
-    return (size_t)(num_keys / 32) * kRegionFloats * sizeof(float) + 256;
+    return (size_t)(num_keys / 256) * kTileFloats * sizeof(float) + 256;
 }
 
 cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], int R, int fmt, cudaStream_t s) {
+    const int grid = (int)(P.nblocks / kP2GWarps);
     cudaError_t e = cudaErrorInvalidValue;
-#define POLYPIC_P2G_CASE(RR, FF) \
-    if (R == RR && fmt == FF) e = launch_blocks<RR, FF>(P, s);
+#define POLYPIC_P2G_CASE(RR, FF)                                      \
+    if (R == RR && fmt == FF) {                                      \
+        k_p2g_tiles<RR, FF><<<grid, kP2GWarps * 32, 0, s>>>(P);      \
+        e = cudaGetLastError();                                      \
+    }
     POLYPIC_P2G_CASE(1, POLYPIC_COEFF_F32)
     POLYPIC_P2G_CASE(4, POLYPIC_COEFF_F32)
     POLYPIC_P2G_CASE(8, POLYPIC_COEFF_F32)

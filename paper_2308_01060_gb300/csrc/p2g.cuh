@@ -17,6 +17,19 @@ __host__ __device__ constexpr int reg_off(int a, int which) {
 }
 constexpr int kRegionFloats = 2 * (reg_size(0) + reg_size(1) + reg_size(2));
 
+// Node region of one 8x8x4-cell tile on face grid a (the union of its 8 block
+// regions): nodes [8tx - 1, 8tx - 1 + tile_x) x [8ty - 1, ...) x [4tz - 1, ...).
+__host__ __device__ constexpr int tile_x(int a) { return a == 0 ? 11 : 10; }
+__host__ __device__ constexpr int tile_y(int a) { return a == 1 ? 11 : 10; }
+__host__ __device__ constexpr int tile_z(int a) { return a == 2 ? 7 : 6; }
+__host__ __device__ constexpr int tile_size(int a) { return tile_x(a) * tile_y(a) * tile_z(a); }
+// Scratch layout of one tile: [a][mass | momentum][tile_size(a)].
+__host__ __device__ constexpr int tile_off(int a, int which) {
+    return (a >= 1 ? 2 * tile_size(0) : 0) + (a >= 2 ? 2 * tile_size(1) : 0) +
+           which * tile_size(a);
+}
+constexpr int kTileFloats = 2 * (tile_size(0) + tile_size(1) + tile_size(2));
+
 struct P2GArgs {
     GridGeom g;
     int64_t count;
@@ -24,7 +37,7 @@ struct P2GArgs {
     const void *coeff;
     const float *scale;        // 16-bit formats: per-particle s_p
     const uint32_t *perm, *cell_start;
-    float *scratch;            // p2g_scratch_bytes()
+    float *scratch;            // p2g_scratch_bytes(): one tile region per tile
     uint32_t *status;
     uint32_t nblocks;          // num_keys / 32
     float dxpow[7];            // dx^L, L = 0..6 (FP32 coefficients -> dimensionless)

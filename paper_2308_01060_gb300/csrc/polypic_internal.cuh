@@ -188,12 +188,20 @@ template <> struct Codec<POLYPIC_COEFF_F16> {
 };
 
 // ---------------------------------------------------------------- launch helpers
+// Carves 256-byte-aligned pieces out of the caller's workspace.  A request
+// beyond its end returns nullptr and sets `overflow`; callers check before
+// launching anything.
 struct Workspace {
     char *base;
     size_t bytes;
     size_t used;
+    bool overflow = false;
     template <class T> T *take(size_t count) {
         size_t off = (used + 255) & ~(size_t)255;
+        if (off + count * sizeof(T) > bytes) {
+            overflow = true;
+            return nullptr;
+        }
         used = off + count * sizeof(T);
         return reinterpret_cast<T *>(base + off);
     }

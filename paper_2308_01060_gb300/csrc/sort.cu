@@ -1,7 +1,7 @@
 // sort.cu -- bit-exact stable sort of particles by cell key.
 //
 // The paper has no sort; it is the device that makes the transfers
-// deterministic and coalesced.  Three pieces, none of which waits on another
+// deterministic and coalesced.  Four pieces, none of which waits on another
 // CTA (reduce-then-scan only):
 //   1. k_keys:   key of every particle (FP32 cell decision), domain check,
 //                per-key counts with warp-aggregated integer atomics
@@ -12,7 +12,11 @@
 //                scan of the digit-major histogram table, and a stable
 //                scatter that ranks equal digits with __match_any_sync.
 //                Stability makes the permutation unique, so it is compared
-//                bit-exactly with a CPU stable sort.
+//                bit-exactly with a CPU stable sort;
+//   4. interleave: inside every block of 32 keys the stable order is dealt
+//                round-robin over the keys (round r = each key's r-th
+//                particle), so that a warp whose lanes own the 32 cells reads
+//                one contiguous run of slots per round.
 #include "sort.cuh"
 
 namespace polypic {
@@ -236,6 +240,29 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_down(
     }
 }
 
+// ---------------------------------------------------------------- block interleave
+// Slot order used by the transfers: inside each block of 32 keys, round r
+// lists the r-th particle (stable order) of every key holding more than r
+// particles, keys ascending.  One warp per block, lane = key.
+__global__ void __launch_bounds__(256) k_block_interleave(const uint32_t *__restrict__ in,
+                                                          const uint32_t *__restrict__ cs,
+                                                          uint32_t *__restrict__ out,
+                                                          uint32_t nblocks) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t b = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (b >= nblocks) return;
+    const uint32_t k = b * 32 + lane;
+    const uint32_t s0 = cs[k], n = cs[k + 1] - s0, base = cs[b * 32];
+    const uint32_t maxn = __reduce_max_sync(0xffffffffu, n);
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t off = 0;
+    for (uint32_t r = 0; r < maxn; ++r) {
+        const unsigned mask = __ballot_sync(0xffffffffu, n > r);
+        if (n > r) out[base + off + __popc(mask & lt)] = in[s0 + r];
+        off += __popc(mask);
+    }
+}
+
 // ---------------------------------------------------------------- driver
 int key_bits(int64_t num_keys) {
     int b = 1;
@@ -246,7 +273,7 @@ int key_bits(int64_t num_keys) {
 size_t sort_scratch_bytes(int64_t count, int64_t num_keys) {
     int64_t ntiles = (count + kRadixTile - 1) / kRadixTile;
     size_t words = 0;
-    words += 4 * (size_t)count + 64;                          // key/value ping-pong
+    words += 5 * (size_t)count + 64;                          // key/value ping-pong + stable perm
     words += 256 * (size_t)ntiles + 64;                       // digit histograms
     words += scan_scratch_words(256 * ntiles) + 64;           // their scan
     words += scan_scratch_words(num_keys + 1) + 64;           // cell-count scan
@@ -263,9 +290,11 @@ cudaError_t sort_particles(const GridGeom &g, int64_t num_keys, int64_t count, c
     int64_t ntiles = (count + kRadixTile - 1) / kRadixTile;
     uint32_t *ka = ws.take<uint32_t>(count), *va = ws.take<uint32_t>(count);
     uint32_t *kb = ws.take<uint32_t>(count), *vb = ws.take<uint32_t>(count);
+    uint32_t *stable = ws.take<uint32_t>(count);
     uint32_t *hist = ws.take<uint32_t>(256 * ntiles);
     uint32_t *hscan = ws.take<uint32_t>(scan_scratch_words(256 * ntiles));
     uint32_t *cscan = ws.take<uint32_t>(scan_scratch_words(num_keys + 1));
+    if (ws.overflow) return cudaErrorInvalidValue;
 
     int kblocks = (int)((count + 255) / 256);
     k_keys<<<kblocks, 256, 0, s>>>(count, x, y, z, g, key, cell_start, status);
@@ -282,7 +311,7 @@ cudaError_t sort_particles(const GridGeom &g, int64_t num_keys, int64_t count, c
         int pb = (shift + per <= bits) ? per : bits - shift;
         bool first = pass == 0, last = pass == passes - 1;
         uint32_t *kout = (pass & 1) ? kb : ka;
-        uint32_t *vout = last ? perm : ((pass & 1) ? vb : va);
+        uint32_t *vout = last ? stable : ((pass & 1) ? vb : va);
         k_radix_up<<<(int)ntiles, kRadixThreads, 0, s>>>(kin, count, shift, pb, hist, (int)ntiles);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = exclusive_scan(hist, hist, ((int64_t)1 << pb) * ntiles, hscan, s)) != cudaSuccess)
@@ -304,7 +333,9 @@ cudaError_t sort_particles(const GridGeom &g, int64_t num_keys, int64_t count, c
         vin = vout;
         shift += pb;
     }
-    return cudaSuccess;
+    const uint32_t nblocks = (uint32_t)(num_keys / 32);
+    k_block_interleave<<<(nblocks + 7) / 8, 256, 0, s>>>(stable, cell_start, perm, nblocks);
+    return cudaGetLastError();
 }
 
 }  // namespace polypic

@@ -38,7 +38,7 @@ def test_sort_bit_exact(shuffle):
     ctx = pp.Context(sc.n, sc.dx, 27)
     ps, _ = sorted_particles(ctx, f)
     key = oracle.keys(f.x, sc.n, sc.dx)
-    perm, cs = oracle.stable_sort(key, oracle.num_keys(sc.n))
+    perm, cs = oracle.particle_order(f.x, sc.n, sc.dx)
     assert ctx.num_keys == oracle.num_keys(sc.n)
     assert np.array_equal(u32(ps.key), key)
     assert np.array_equal(u32(ps.perm), perm)
@@ -57,7 +57,7 @@ def test_sort_ragged_and_odd_grid(count):
     ws = ctx.workspace(count)
     pp.polypic_sort(ctx, ps, ws)
     key = oracle.keys(x, n, dx)
-    perm, cs = oracle.stable_sort(key, oracle.num_keys(n))
+    perm, cs = oracle.particle_order(x, n, dx)
     assert np.array_equal(u32(ps.perm), perm)
     assert np.array_equal(u32(ps.cell_start), cs)
     if count:
@@ -188,7 +188,7 @@ def test_g2p_parity(R):
     dt = 1e-3
     pp.polypic_g2p(ctx, g, ps, out, dt, ws)
     c_or, x_or = oracle.g2p(f.x, gv, R, sc.n, sc.dx, dt)
-    perm = oracle.stable_sort(oracle.keys(f.x, sc.n, sc.dx), ctx.num_keys)[0]
+    perm = oracle.particle_order(f.x, sc.n, sc.dx)[0]
     c_or = c_or[:, :, perm]
     x_or = x_or[:, perm]
     c_gpu = np_(out.coeff).astype(np.float64)
@@ -215,7 +215,7 @@ def test_step_parity(R):
     prm = pp.UpdateSettings(dt=sc.dt)
     pp.polypic_step(ctx, ps, out, g, prm, ws)
     c_or, x_or, (gm, gp, gv) = oracle.step(f.x, f.mass, f.coeff, sc.n, sc.dx, sc.dt)
-    perm = oracle.stable_sort(oracle.keys(f.x, sc.n, sc.dx), ctx.num_keys)[0]
+    perm = oracle.particle_order(f.x, sc.n, sc.dx)[0]
     assert np.array_equal(u32(ps.perm), perm)
     for a in range(3):
         assert rel(np_(g.mom[a]), gp[a]) < TOL
@@ -251,8 +251,8 @@ def test_step_with_solid_phase_and_drag():
         assert rel(np_(gs.vel[a]), sv[a]) < TOL
     cf, xf = oracle.g2p(f.x, fv, 8, sc.n, sc.dx, sc.dt)
     cs_, xs = oracle.g2p(s.x, sv, 8, sc.n, sc.dx, sc.dt)
-    pf = oracle.stable_sort(oracle.keys(f.x, sc.n, sc.dx), ctx.num_keys)[0]
-    psol = oracle.stable_sort(oracle.keys(s.x, sc.n, sc.dx), ctx.num_keys)[0]
+    pf = oracle.particle_order(f.x, sc.n, sc.dx)[0]
+    psol = oracle.particle_order(s.x, sc.n, sc.dx)[0]
     assert rel(np_(fo.coeff)[:, 0], cf[:, 0, pf]) < TOL
     assert rel(np_(so.coeff)[:, 0], cs_[:, 0, psol]) < TOL
     assert np.array_equal(np_(so.mass_abs), s.mass_abs[psol])

@@ -501,3 +501,33 @@ def test_pcg_projection_matches_direct_solve_and_is_divergence_free():
         if np.abs(div[fluid]).max() > 0 else (vp, None, None)
     for a in range(3):
         assert np.allclose(vp2[a], vp[a], rtol=0, atol=1e-8 * np.abs(vp[a]).max())
+
+
+def test_block_interleave_order():
+    """Rounds of the interleaved order list, per block, each key's particles in
+    stable order; it is a permutation that keeps every block's slot range."""
+    rng = np.random.default_rng(90)
+    n = (16, 8, 8)
+    dx = 1 / 16
+    x = np.stack([rng.uniform(1, n[b] - 1, 3000) * dx for b in range(3)]).astype(np.float32)
+    x[:, :400] = np.array([[5.5], [3.5], [2.5]]) * dx      # one crowded cell
+    nk = oracle.num_keys(n)
+    key = oracle.keys(x, n, dx)
+    perm, cs = oracle.stable_sort(key, nk)
+    out = oracle.block_interleave(perm, nk, cs)
+    assert np.array_equal(np.sort(out), np.arange(x.shape[1]))
+    for b in range(nk // 32):
+        lo, hi = cs[32 * b], cs[32 * b + 32]
+        seg = out[lo:hi]
+        assert np.array_equal(np.sort(seg), np.sort(perm[lo:hi]))
+        # each key's particles appear in increasing index order, and the r-th
+        # one of key k comes after the (r-1)-th one of every key of the block
+        for k in range(32 * b, 32 * b + 32):
+            mine = seg[key[seg] == k]
+            assert np.array_equal(mine, perm[cs[k]:cs[k + 1]])
+        kk = key[seg]
+        rank = np.zeros_like(kk)
+        for c in np.unique(kk):
+            rank[kk == c] = np.arange(np.sum(kk == c))
+        order = np.lexsort((kk, rank))
+        assert np.array_equal(order, np.arange(len(seg)))
