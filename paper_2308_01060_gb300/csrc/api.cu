@@ -82,7 +82,7 @@ polypic_status do_sort(polypic_ctx *c, polypic_particles *p, void *ws, size_t ws
 }
 
 polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *g, void *ws,
-                      size_t ws_bytes, cudaStream_t s) {
+                      size_t ws_bytes, cudaStream_t s, const polypic_update_params *fused = nullptr) {
     P2GArgs P{};
     P.g = c->geom;
     P.count = p->count;
@@ -100,8 +100,11 @@ polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *
     for (int l = 0; l < 7; ++l) P.dxpow[l] = (float)std::pow(c->cfg.dx, (double)l);
     Workspace W{static_cast<char *>(ws), ws_bytes, 0};
     P.scratch = W.take<float>((size_t)(c->num_keys / 256) * kTileFloats);
+    P.tile_live = W.take<uint8_t>((size_t)(c->num_keys / 256));
     if (W.overflow) return POLYPIC_ERR_WORKSPACE;
-    return from_cuda(p2g(P, g->mass, g->mom, c->cfg.num_modes, c->cfg.coeff_format, s));
+    return from_cuda(p2g(P, g->mass, g->mom, fused ? g->vel : nullptr, fused ? fused->dt : 0.0f,
+                         fused ? fused->gravity : nullptr, c->cfg.num_modes, c->cfg.coeff_format,
+                         s));
 }
 
 polypic_status do_g2p(polypic_ctx *c, const polypic_grid *g, const polypic_particles *in,
@@ -332,14 +335,17 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
     const int64_t nmax = max64(fluid_in->count, solid ? solid_in->count : 0);
     if ((s = check_ws(ctx, nmax, ws, ws_bytes)) != POLYPIC_OK) return s;
     cudaStream_t st = as_stream(stream);
+    // a single phase without projection gets the grid update fused into P2G's reduce
+    const bool fuse = !solid && !params->project;
     if ((s = do_sort(ctx, fluid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
-    if ((s = do_p2g(ctx, fluid_in, gf, ws, ws_bytes, st)) != POLYPIC_OK) return s;
+    if ((s = do_p2g(ctx, fluid_in, gf, ws, ws_bytes, st, fuse ? params : nullptr)) != POLYPIC_OK)
+        return s;
     if (solid) {
         if ((s = do_sort(ctx, solid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
         if ((s = do_p2g(ctx, solid_in, gs, ws, ws_bytes, st)) != POLYPIC_OK) return s;
     }
-    if ((s = do_grid_update(ctx, gf, solid ? gs : nullptr, fluid_in, params, ws, ws_bytes, st)) !=
-        POLYPIC_OK)
+    if (!fuse && (s = do_grid_update(ctx, gf, solid ? gs : nullptr, fluid_in, params, ws, ws_bytes,
+                                     st)) != POLYPIC_OK)
         return s;
     if ((s = do_g2p(ctx, gf, fluid_in, fluid_out, params->dt, st)) != POLYPIC_OK) return s;
     if (solid && (s = do_g2p(ctx, gs, solid_in, solid_out, params->dt, st)) != POLYPIC_OK) return s;

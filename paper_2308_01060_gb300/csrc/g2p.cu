@@ -11,9 +11,9 @@
 //   G0_k = W_k,  G1_k = W_k z_k / mu2 = 4 F1_k,  G2_k = W_k g_k / d_2 = (1,-2,1)/2
 // (z in cells): the quadratic fit is half the second difference for every t,
 // so no denominator is formed; the guard zeroes G2 on a guarded axis.  The
-// result is the dimensionless c dx^L; FP32 output divides by dx^L, the 16-bit
-// formats divide by the per-particle scale s_p = max |c dx^L| and round to
-// nearest even.  Outputs are written in sorted slot order (coalesced).
+// FP32 output folds 1/dx and 1/dx^2 into the degree-1 and degree-2 factors and
+// so comes out in physical units; the 16-bit formats fit c dx^L, divide by the
+// per-particle scale s_p = max |c dx^L| and round to nearest even.  Outputs are written in sorted slot order (coalesced).
 #include "g2p.cuh"
 
 namespace polypic {
@@ -27,16 +27,19 @@ template <int A> struct Tile {
 constexpr int kTileOff1 = Tile<0>::N, kTileOff2 = Tile<0>::N + Tile<1>::N;
 constexpr int kTileFloats = Tile<0>::N + Tile<1>::N + Tile<2>::N;
 
+// inv1 = 1/dx, inv2 = 1/dx^2 give physical coefficients; 1 and 1 give c dx^L.
 template <int D>
-__device__ __forceinline__ void fit_factors(const Stencil1D &s, bool guard, float (&G)[D][3]) {
+__device__ __forceinline__ void fit_factors(const Stencil1D &s, bool guard, float inv1,
+                                            float inv2, float (&G)[D][3]) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) G[0][k] = s.W[k];
     if constexpr (D > 1) {
+        const float f = 4.0f * inv1;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) G[1][k] = 4.0f * s.F1[k];
+        for (int k = 0; k < 3; ++k) G[1][k] = f * s.F1[k];
     }
     if constexpr (D > 2) {
-        const float h = guard ? 0.0f : 0.5f;
+        const float h = guard ? 0.0f : 0.5f * inv2;
         G[2][0] = h;
         G[2][1] = -2.0f * h;
         G[2][2] = h;
@@ -48,13 +51,13 @@ __device__ __forceinline__ void fit_factors(const Stencil1D &s, bool guard, floa
 template <int R, int A>
 __device__ __forceinline__ void g2p_component(const float *s_tile, int lx, int ly, int lz,
                                               const Stencil1D &sx, bool gx, const Stencil1D &sy,
-                                              bool gy, const Stencil1D &sz, bool gz,
-                                              float (&Chat)[R]) {
+                                              bool gy, const Stencil1D &sz, bool gz, float inv1,
+                                              float inv2, float (&Chat)[R]) {
     constexpr int D = axis_degrees(R);
     float Gx[D][3], Gy[D][3], Gz[D][3];
-    fit_factors<D>(sx, gx, Gx);
-    fit_factors<D>(sy, gy, Gy);
-    fit_factors<D>(sz, gz, Gz);
+    fit_factors<D>(sx, gx, inv1, inv2, Gx);
+    fit_factors<D>(sy, gy, inv1, inv2, Gy);
+    fit_factors<D>(sz, gz, inv1, inv2, Gz);
     const float *t = s_tile + (A == 0 ? 0 : A == 1 ? kTileOff1 : kTileOff2);
     // contract x
     float U1[D][3][3];
@@ -102,6 +105,17 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
     const int tz = (int)(tile / ((uint32_t)g.tiles[0] * (uint32_t)g.tiles[1]));
     const int ox = 8 * tx - 1, oy = 8 * ty - 1, oz = 4 * tz - 1;
 
+    // first particle's loads go out before the tile staging and its barrier
+    uint32_t j = jb + threadIdx.x;
+    uint32_t p = 0;
+    float px = 0.0f, py = 0.0f, pz = 0.0f, m = 0.0f, mabs = 0.0f;
+    if (j < je) {
+        p = A.perm[j];
+        px = A.x[p]; py = A.y[p]; pz = A.z[p]; m = A.mass[p];
+        if (A.mass_abs) mabs = A.mass_abs[p];
+    }
+    uint32_t pn = (j + kG2PThreads < je) ? A.perm[j + kG2PThreads] : 0u;
+
     // stage the three velocity footprints (nodes outside a grid read as 0)
     auto stage = [&](int a, int X, int Y, int Z, int off) {
         const int dX = g.n[0] + (a == 0), dY = g.n[1] + (a == 1), dZ = g.n[2] + (a == 2);
@@ -123,11 +137,19 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
     using T = typename Codec<FMT>::T;
     T *ocoeff = reinterpret_cast<T *>(A.ocoeff);
     const int64_t cnt = A.count;
-    for (uint32_t j = jb + threadIdx.x; j < je; j += kG2PThreads) {
-        const uint32_t p = A.perm[j];
-        const float px = A.x[p], py = A.y[p], pz = A.z[p];
-        const float m = A.mass[p];
-        const float mabs = A.mass_abs ? A.mass_abs[p] : 0.0f;
+    // FP32 output is physical (c = c dx^L / dx^L); the 16-bit codes take c dx^L
+    const float inv1 = FMT == POLYPIC_COEFF_F32 ? A.inv_dxpow[1] : 1.0f;
+    const float inv2 = FMT == POLYPIC_COEFF_F32 ? A.inv_dxpow[2] : 1.0f;
+    for (; j < je; j += kG2PThreads) {
+        // software pipeline: the next particle's data, and the index after it
+        const uint32_t jn = j + kG2PThreads;
+        float nx = 0.0f, ny = 0.0f, nz = 0.0f, nm = 0.0f, nmabs = 0.0f;
+        uint32_t pnn = 0;
+        if (jn < je) {
+            nx = A.x[pn]; ny = A.y[pn]; nz = A.z[pn]; nm = A.mass[pn];
+            if (A.mass_abs) nmabs = A.mass_abs[pn];
+            if (jn + kG2PThreads < je) pnn = A.perm[jn + kG2PThreads];
+        }
         const float v0 = cell_coord(px, g.inv_dx), v1 = cell_coord(py, g.inv_dx),
                     v2 = cell_coord(pz, g.inv_dx);
         bool ok = coord_valid(v0, g.n[0]) && coord_valid(v1, g.n[1]) && coord_valid(v2, g.n[2]);
@@ -144,11 +166,11 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
             const Stencil1D sc1 = stencil_1d(ac1.t), sf1 = stencil_1d(af1.t);
             const Stencil1D sc2 = stencil_1d(ac2.t), sf2 = stencil_1d(af2.t);
             g2p_component<R, 0>(s_tile, af0.base - ox, ac1.base - oy, ac2.base - oz, sf0,
-                                af0.guard, sc1, ac1.guard, sc2, ac2.guard, Chat[0]);
+                                af0.guard, sc1, ac1.guard, sc2, ac2.guard, inv1, inv2, Chat[0]);
             g2p_component<R, 1>(s_tile, ac0.base - ox, af1.base - oy, ac2.base - oz, sc0,
-                                ac0.guard, sf1, af1.guard, sc2, ac2.guard, Chat[1]);
+                                ac0.guard, sf1, af1.guard, sc2, ac2.guard, inv1, inv2, Chat[1]);
             g2p_component<R, 2>(s_tile, ac0.base - ox, ac1.base - oy, af2.base - oz, sc0,
-                                ac0.guard, sc1, ac1.guard, sf2, af2.guard, Chat[2]);
+                                ac0.guard, sc1, ac1.guard, sf2, af2.guard, inv1, inv2, Chat[2]);
         } else {
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -159,21 +181,12 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
         const bool finite = isfinite(Chat[0][0]) && isfinite(Chat[1][0]) && isfinite(Chat[2][0]);
         if (!finite) atomicOr(A.status, kFlagNonFinite);
 
+        T *out = ocoeff + j;  // row (a, r) starts (a R + r) * cnt elements in
         if constexpr (FMT == POLYPIC_COEFF_F32) {
-            constexpr int D = axis_degrees(R);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int da = 0; da < D; ++da)
-#pragma unroll
-                    for (int db = 0; db < D; ++db)
-#pragma unroll
-                        for (int dc = 0; dc < D; ++dc)
-                            if (has_mode(R, da, db, dc)) {
-                                const int r = mode_index(da, db, dc);
-                                ocoeff[((int64_t)a * R + r) * cnt + j] =
-                                    Chat[a][r] * A.inv_dxpow[da + db + dc];
-                            }
+                for (int r = 0; r < R; ++r, out += cnt) *out = Chat[a][r];
         } else {
             float s = 0.0f;
 #pragma unroll
@@ -184,8 +197,7 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    ocoeff[((int64_t)a * R + r) * cnt + j] = Codec<FMT>::encode(Chat[a][r] * inv);
+                for (int r = 0; r < R; ++r, out += cnt) *out = Codec<FMT>::encode(Chat[a][r] * inv);
             A.oscale[j] = s;
         }
         // advection with the fitted velocity (unquantised)
@@ -196,6 +208,7 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
         A.oz[j] = ok ? fminf(fmaxf(fmaf(A.dt, vz, pz), g.lo[2]), g.hi[2]) : pz;
         A.omass[j] = m;
         if (A.omass_abs) A.omass_abs[j] = mabs;
+        px = nx; py = ny; pz = nz; m = nm; mabs = nmabs; pn = pnn;
     }
 }
 

@@ -62,16 +62,76 @@ template <int A> __host__ __device__ constexpr int deg_z(int du, int dv, int dw)
     return A == 2 ? du : dw;
 }
 
+// ---------------------------------------------------------------- staging
+// Each lane prefetches its next particles with cp.async (4-byte copies) into
+// a private two-stage buffer laid out [stage][value][lane] (conflict-free):
+// x, y, z, m, m_abs, s_p, the particle index, then one 32-bit word per mode
+// (the coefficient, or for 16-bit formats the aligned word holding its code).
+template <int R> struct Stage {
+    static constexpr int kX = 0, kY = 1, kZ = 2, kM = 3, kMabs = 4, kScale = 5, kIdx = 6, kC = 7;
+    static constexpr int NV = kC + R;
+    static constexpr int kFloatsPerWarp = 2 * NV * 32;
+};
+
+__device__ __forceinline__ void cp_async4(float *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int R, int FMT, int A>
+__device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, float *st, int lane) {
+    using S = Stage<R>;
+    cp_async4(st + S::kX * 32 + lane, P.x + p);
+    cp_async4(st + S::kY * 32 + lane, P.y + p);
+    cp_async4(st + S::kZ * 32 + lane, P.z + p);
+    cp_async4(st + S::kM * 32 + lane, P.mass + p);
+    if (P.mass_abs) cp_async4(st + S::kMabs * 32 + lane, P.mass_abs + p);
+    reinterpret_cast<uint32_t *>(st)[S::kIdx * 32 + lane] = p;
+    if constexpr (FMT == POLYPIC_COEFF_F32) {
+        // row r of component A starts (A R + r) * count floats in
+        const float *c = reinterpret_cast<const float *>(P.coeff) + (int64_t)A * R * P.count + p;
+#pragma unroll
+        for (int r = 0; r < R; ++r, c += P.count) cp_async4(st + (S::kC + r) * 32 + lane, c);
+    } else {
+        cp_async4(st + S::kScale * 32 + lane, P.scale + p);
+        // byte offset of code (A R + r, p); its aligned 4-byte word holds it
+        const char *base = reinterpret_cast<const char *>(P.coeff);
+        int64_t b = 2 * ((int64_t)A * R * P.count + p);
+        const int64_t rstride = 2 * P.count;
+#pragma unroll
+        for (int r = 0; r < R; ++r, b += rstride) {
+            const int64_t w = b & ~(int64_t)3;
+            // only the array's last code can sit alone in a word at its end
+            if (A == 2 && r == R - 1 && w + 4 > (int64_t)6 * R * P.count) {
+                reinterpret_cast<uint32_t *>(st)[(S::kC + r) * 32 + lane] =
+                    *reinterpret_cast<const uint16_t *>(base + b);
+            } else {
+                cp_async4(st + (S::kC + r) * 32 + lane, base + w);
+            }
+        }
+    }
+}
+
 // One particle's contribution to the lane's padded footprint on grid A.
 // fu: stencil along A (face offset), fv / fw: the other two axes (centre).
 template <int R, int FMT, int A>
-__device__ __forceinline__ void accumulate(const P2GArgs &P, uint32_t p, float mt, float cscale,
+__device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, int lane, float mt,
                                            int shift, const Stencil1D &fu, const Stencil1D &fv,
                                            const Stencil1D &fw, float (&am)[4][3][3],
                                            float (&av)[4][3][3]) {
+    using S = Stage<R>;
     constexpr int D = axis_degrees(R);
-    using T = typename Codec<FMT>::T;
-    const T *coeff = reinterpret_cast<const T *>(P.coeff);
+    const float cscale = FMT == POLYPIC_COEFF_F32 ? 1.0f : st[S::kScale * 32 + lane];
+    // 16-bit codes: element e = (A R + r) count + p sits in the high half of
+    // its aligned word when e is odd; (A R + r) is a compile-time constant.
+    const uint32_t podd = reinterpret_cast<const uint32_t *>(st)[S::kIdx * 32 + lane] & 1u;
+    const uint32_t par_even_row = podd, par_odd_row = podd ^ (uint32_t)(P.count & 1);
     // coefficients (dimensionless c dx^L, or code * s_p) in (u, v, w) order
     float C[D][D][D];
 #pragma unroll
@@ -83,10 +143,16 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, uint32_t p, float m
                 const int a = deg_x<A>(du, dv, dw), b = deg_y<A>(du, dv, dw),
                           c = deg_z<A>(du, dv, dw);
                 if (has_mode(R, a, b, c)) {
-                    const float raw =
-                        Codec<FMT>::load(coeff + ((int64_t)A * R + mode_index(a, b, c)) * P.count + p);
-                    C[du][dv][dw] =
-                        raw * (FMT == POLYPIC_COEFF_F32 ? P.dxpow[a + b + c] : cscale);
+                    const int r = mode_index(a, b, c);
+                    if constexpr (FMT == POLYPIC_COEFF_F32) {
+                        C[du][dv][dw] = st[(S::kC + r) * 32 + lane];
+                    } else {
+                        const uint32_t word =
+                            reinterpret_cast<const uint32_t *>(st)[(S::kC + r) * 32 + lane];
+                        const uint32_t odd = ((A * R + r) & 1) ? par_odd_row : par_even_row;
+                        const uint16_t code = (uint16_t)(word >> (odd << 4));
+                        C[du][dv][dw] = Codec<FMT>::decode(code);
+                    }
                 } else {
                     C[du][dv][dw] = 0.0f;
                 }
@@ -95,6 +161,17 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, uint32_t p, float m
     axis_factors<D>(fu, Fu);
     axis_factors<D>(fv, Fv);
     axis_factors<D>(fw, Fw);
+    // FP32 coefficients are physical: dx^a goes into the degree-a factor rows
+    if constexpr (FMT == POLYPIC_COEFF_F32 && D > 1) {
+#pragma unroll
+        for (int a = 1; a < D; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Fu[a][k] *= P.dxpow[a];
+                Fv[a][k] *= P.dxpow[a];
+                Fw[a][k] *= P.dxpow[a];
+            }
+    }
     // contract w, then v
     float T2[D][3][3];
 #pragma unroll
@@ -121,15 +198,25 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, uint32_t p, float m
                 T2[du][kv][kw] = s;
             }
     }
-    // padded factors along u: node d = k + shift, mass folded in
-    float Gu[D][4];
+    // padded factors along u: node d = k + shift; mass (and the 16-bit scale
+    // s_p for the momentum) folded in
+    const float mom_scale = FMT == POLYPIC_COEFF_F32 ? mt : mt * cscale;
+    float Gu[D][4], Wm[4];
 #pragma unroll
     for (int du = 0; du < D; ++du) {
-        const float f0 = mt * Fu[du][0], f1 = mt * Fu[du][1], f2 = mt * Fu[du][2];
+        const float f0 = mom_scale * Fu[du][0], f1 = mom_scale * Fu[du][1],
+                    f2 = mom_scale * Fu[du][2];
         Gu[du][0] = shift ? 0.0f : f0;
         Gu[du][1] = shift ? f0 : f1;
         Gu[du][2] = shift ? f1 : f2;
         Gu[du][3] = shift ? f2 : 0.0f;
+    }
+    {
+        const float w0 = mt * Fu[0][0], w1 = mt * Fu[0][1], w2 = mt * Fu[0][2];
+        Wm[0] = shift ? 0.0f : w0;
+        Wm[1] = shift ? w0 : w1;
+        Wm[2] = shift ? w1 : w2;
+        Wm[3] = shift ? w2 : 0.0f;
     }
     // contract u into the footprint; mass weights
 #pragma unroll
@@ -143,22 +230,30 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, uint32_t p, float m
 #pragma unroll
                 for (int du = 0; du < D; ++du) s = fmaf(T2[du][kv][kw], Gu[du][d], s);
                 av[d][kv][kw] = s;
-                am[d][kv][kw] = fmaf(Gu[0][d], wvw, am[d][kv][kw]);
+                am[d][kv][kw] = fmaf(Wm[d], wvw, am[d][kv][kw]);
             }
         }
 }
 
-// Index in block region A of cell-local node (cu-1+d, cv-1+kv, cw-1+kw),
-// expressed through the (u, v, w) axis order of component A.
+// Index in block region A of node (ix, iy, iz) relative to the region origin.
 template <int A>
 __device__ __forceinline__ int region_index(int ix, int iy, int iz) {
     return (iz * Reg<A>::Y + iy) * Reg<A>::X + ix;
 }
 
+// Slot of the lane's particle in round q (every lane must call it).
+__device__ __forceinline__ uint32_t round_slot(uint32_t bs, uint32_t n_c, uint32_t q,
+                                               unsigned lt) {
+    const uint32_t before = __reduce_add_sync(0xffffffffu, min(n_c, q));
+    const unsigned mask = __ballot_sync(0xffffffffu, n_c > q);
+    return bs + before + __popc(mask & lt);
+}
+
 template <int R, int FMT, int A>
 __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t n_c,
                                          uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
-                                         int gk, int lane, float *reg, bool &bad) {
+                                         int gk, int lane, float *reg, float *stage, bool &bad) {
+    using S = Stage<R>;
     float am[4][3][3], av[4][3][3];
 #pragma unroll
     for (int d = 0; d < 4; ++d)
@@ -167,16 +262,28 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t
 #pragma unroll
             for (int kw = 0; kw < 3; ++kw) am[d][kv][kw] = av[d][kv][kw] = 0.0f;
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t off = 0;
+    float *st0 = stage, *st1 = stage + S::NV * 32;
+    // prologue: rounds 0 and 1 in flight, the index of round 2 loading
+    {
+        const uint32_t s0 = round_slot(bs, n_c, 0, lt), s1 = round_slot(bs, n_c, 1, lt);
+        if (n_c > 0) stage_particle<R, FMT, A>(P, P.perm[s0], st0, lane);
+        cp_async_commit();
+        if (n_c > 1) stage_particle<R, FMT, A>(P, P.perm[s1], st1, lane);
+        cp_async_commit();
+    }
+    uint32_t pn = 0;
+    {
+        const uint32_t s2 = round_slot(bs, n_c, 2, lt);
+        if (n_c > 2) pn = P.perm[s2];
+    }
     for (uint32_t r = 0; r < maxn; ++r) {
-        const unsigned mask = __ballot_sync(0xffffffffu, n_c > r);
+        float *st = (r & 1) ? st1 : st0;
+        cp_async_wait<1>();
         if (n_c > r) {
-            const uint32_t slot = bs + off + __popc(mask & lt);
-            const uint32_t p = P.perm[slot];
-            const float px = P.x[p], py = P.y[p], pz = P.z[p];
-            float mt = P.mass[p];
-            if (P.mass_abs) mt += P.mass_abs[p];
-            const float cscale = FMT == POLYPIC_COEFF_F32 ? 1.0f : P.scale[p];
+            const float px = st[S::kX * 32 + lane], py = st[S::kY * 32 + lane],
+                        pz = st[S::kZ * 32 + lane];
+            float mt = st[S::kM * 32 + lane];
+            if (P.mass_abs) mt += st[S::kMabs * 32 + lane];
             const float v0 = cell_coord(px, P.g.inv_dx), v1 = cell_coord(py, P.g.inv_dx),
                         v2 = cell_coord(pz, P.g.inv_dx);
             const bool ok = coord_valid(v0, P.g.n[0]) && coord_valid(v1, P.g.n[1]) &&
@@ -190,14 +297,19 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t
                            aw = axis_decide(vw, false);
                 const int cu = A == 0 ? gi : (A == 1 ? gj : gk);
                 const int shift = au.base - (cu - 1);
-                accumulate<R, FMT, A>(P, p, mt, cscale, shift, stencil_1d(au.t), stencil_1d(av_.t),
+                accumulate<R, FMT, A>(P, st, lane, mt, shift, stencil_1d(au.t), stencil_1d(av_.t),
                                       stencil_1d(aw.t), am, av);
             } else {
                 bad = true;
             }
         }
-        off += __popc(mask);
+        // refill this stage with round r + 2, start loading the index of round r + 3
+        if (n_c > r + 2) stage_particle<R, FMT, A>(P, pn, st, lane);
+        cp_async_commit();
+        const uint32_t s3 = round_slot(bs, n_c, r + 3, lt);
+        pn = n_c > r + 3 ? P.perm[s3] : 0u;
     }
+    cp_async_wait<0>();
     // merge the 32 footprints into the block region, one node offset per phase
     const int cu = A == 0 ? ci : (A == 1 ? cj : ck);
     const int cv = A == 0 ? cj : ci;
@@ -248,11 +360,15 @@ __device__ __forceinline__ void merge_tile(const float *smem_regions, const bool
 
 template <int R, int FMT>
 __global__ void __launch_bounds__(kP2GWarps * 32, 1) k_p2g_tiles(P2GArgs P) {
-    __shared__ float s_reg[kP2GWarps * kRegionFloats];
+    extern __shared__ float smem[];
     __shared__ bool s_empty[kP2GWarps];
+    float *s_reg = smem;                                     // [8][kRegionFloats]
+    float *s_stage = smem + kP2GWarps * kRegionFloats;        // [8][Stage::kFloatsPerWarp]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t tile = blockIdx.x;
-    if (P.cell_start[tile * 256] == P.cell_start[tile * 256 + 256]) return;  // CTA-uniform
+    const bool tile_empty = P.cell_start[tile * 256] == P.cell_start[tile * 256 + 256];
+    if (threadIdx.x == 0) P.tile_live[tile] = tile_empty ? 0 : 1;
+    if (tile_empty) return;  // CTA-uniform
 
     const uint32_t b = tile * kP2GWarps + warp;
     const uint32_t k = b * 32 + lane;
@@ -261,6 +377,7 @@ __global__ void __launch_bounds__(kP2GWarps * 32, 1) k_p2g_tiles(P2GArgs P) {
     const uint32_t bs = P.cell_start[b * 32];
     const uint32_t maxn = __reduce_max_sync(0xffffffffu, n_c);
     float *reg = s_reg + warp * kRegionFloats;
+    float *stage = s_stage + warp * Stage<R>::kFloatsPerWarp;
     if (lane == 0) s_empty[warp] = maxn == 0;
     if (maxn > 0) {
         for (int i = lane; i < kRegionFloats; i += 32) reg[i] = 0.0f;
@@ -270,9 +387,9 @@ __global__ void __launch_bounds__(kP2GWarps * 32, 1) k_p2g_tiles(P2GArgs P) {
         const int ci = lane & 3, cj = (lane >> 2) & 3, ck = lane >> 4;
         const int gi = i0 + ci, gj = j0 + cj, gk = k0 + ck;
         bool bad = false;
-        p2g_pass<R, FMT, 0>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, bad);
-        p2g_pass<R, FMT, 1>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, bad);
-        p2g_pass<R, FMT, 2>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, bad);
+        p2g_pass<R, FMT, 0>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+        p2g_pass<R, FMT, 1>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+        p2g_pass<R, FMT, 2>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.status, kFlagOutOfDomain);
     }
     __syncthreads();
@@ -282,53 +399,76 @@ __global__ void __launch_bounds__(kP2GWarps * 32, 1) k_p2g_tiles(P2GArgs P) {
     merge_tile<2>(s_reg, s_empty, dst);
 }
 
+template <int R, int FMT>
+static cudaError_t launch_tiles(const P2GArgs &P, int grid, cudaStream_t s) {
+    const int smem = (kP2GWarps * kRegionFloats + kP2GWarps * Stage<R>::kFloatsPerWarp) * 4;
+    static int configured_device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_p2g_tiles<R, FMT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured_device = dev;
+    }
+    k_p2g_tiles<R, FMT><<<grid, kP2GWarps * 32, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
 // Sum of the tile regions covering each node of face grid A, in ascending
-// tile order; empty tiles wrote nothing and are skipped.
+// tile order; tiles without particles wrote nothing and are skipped.  With
+// `fuse` set it also applies the single-phase grid update (v = mv/m, + dt g,
+// walls) and writes the velocity.  Launch: x over the x nodes, y over j, z
+// over k (grid-stride on y and z).
 template <int A>
-__global__ void __launch_bounds__(256) k_p2g_reduce(GridGeom g, const uint32_t *__restrict__ cs,
+__global__ void __launch_bounds__(128) k_p2g_reduce(GridGeom g, const uint8_t *__restrict__ live,
                                                     const float *__restrict__ scratch,
-                                                    float *__restrict__ gm,
-                                                    float *__restrict__ gp) {
+                                                    float *__restrict__ gm, float *__restrict__ gp,
+                                                    float *__restrict__ gv, float dt, float ga) {
     const int dX = g.n[0] + (A == 0), dY = g.n[1] + (A == 1), dZ = g.n[2] + (A == 2);
-    const int64_t total = (int64_t)dX * dY * dZ;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(idx % dX);
-        const int j = (int)((idx / dX) % dY);
-        const int k = (int)(idx / ((int64_t)dX * dY));
-        // tile t covers nodes [8t - 1, 8t - 1 + X) along x (same for y; 4t along z)
-        const int tx0 = max(0, (i + 2 - TileReg<A>::X + 7) >> 3), tx1 = min(g.tiles[0] - 1, (i + 1) >> 3);
-        const int ty0 = max(0, (j + 2 - TileReg<A>::Y + 7) >> 3), ty1 = min(g.tiles[1] - 1, (j + 1) >> 3);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dX) return;
+    const int tx0 = max(0, (i + 2 - TileReg<A>::X + 7) >> 3), tx1 = min(g.tiles[0] - 1, (i + 1) >> 3);
+    for (int k = blockIdx.z; k < dZ; k += gridDim.z) {
         const int tz0 = max(0, (k + 2 - TileReg<A>::Z + 3) >> 2), tz1 = min(g.tiles[2] - 1, (k + 1) >> 2);
-        float sm = 0.0f, sv = 0.0f;
-        for (int tz = tz0; tz <= tz1; ++tz)
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) {
-                    const uint32_t t = ((uint32_t)tz * g.tiles[1] + ty) * g.tiles[0] + tx;
-                    if (cs[t * 256] == cs[t * 256 + 256]) continue;
-                    const int lx = i - (8 * tx - 1), ly = j - (8 * ty - 1), lz = k - (4 * tz - 1);
-                    const int r = (lz * TileReg<A>::Y + ly) * TileReg<A>::X + lx;
-                    const float *src = scratch + (size_t)t * kTileFloats;
-                    sm += src[tile_off(A, 0) + r];
-                    sv += src[tile_off(A, 1) + r];
-                }
-        gm[idx] = sm;
-        gp[idx] = sv;
+        for (int j = blockIdx.y; j < dY; j += gridDim.y) {
+            const int ty0 = max(0, (j + 2 - TileReg<A>::Y + 7) >> 3),
+                      ty1 = min(g.tiles[1] - 1, (j + 1) >> 3);
+            float sm = 0.0f, sv = 0.0f;
+            for (int tz = tz0; tz <= tz1; ++tz)
+                for (int ty = ty0; ty <= ty1; ++ty)
+                    for (int tx = tx0; tx <= tx1; ++tx) {
+                        const uint32_t t = ((uint32_t)tz * g.tiles[1] + ty) * g.tiles[0] + tx;
+                        if (!live[t]) continue;
+                        const int lx = i - (8 * tx - 1), ly = j - (8 * ty - 1), lz = k - (4 * tz - 1);
+                        const int r = (lz * TileReg<A>::Y + ly) * TileReg<A>::X + lx;
+                        const float *src = scratch + (size_t)t * kTileFloats;
+                        sm += src[tile_off(A, 0) + r];
+                        sv += src[tile_off(A, 1) + r];
+                    }
+            const int64_t idx = ((int64_t)k * dY + j) * dX + i;
+            gm[idx] = sm;
+            gp[idx] = sv;
+            if (gv) {
+                const int ia = A == 0 ? i : (A == 1 ? j : k);
+                float v = sm > 0.0f ? sv / sm : 0.0f;
+                v = fmaf(dt, ga, v);
+                gv[idx] = (ia == 0 || ia == g.n[A]) ? 0.0f : v;
+            }
+        }
     }
 }
 
 size_t p2g_scratch_bytes(int64_t num_keys) {
-    return (size_t)(num_keys / 256) * kTileFloats * sizeof(float) + 256;
+    return (size_t)(num_keys / 256) * (kTileFloats * sizeof(float) + 1) + 512;
 }
 
-cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], int R, int fmt, cudaStream_t s) {
+cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], float dt,
+                const float gravity[3], int R, int fmt, cudaStream_t s) {
     const int grid = (int)(P.nblocks / kP2GWarps);
     cudaError_t e = cudaErrorInvalidValue;
-#define POLYPIC_P2G_CASE(RR, FF)                                      \
-    if (R == RR && fmt == FF) {                                      \
-        k_p2g_tiles<RR, FF><<<grid, kP2GWarps * 32, 0, s>>>(P);      \
-        e = cudaGetLastError();                                      \
-    }
+#define POLYPIC_P2G_CASE(RR, FF) \
+    if (R == RR && fmt == FF) e = launch_tiles<RR, FF>(P, grid, s);
     POLYPIC_P2G_CASE(1, POLYPIC_COEFF_F32)
     POLYPIC_P2G_CASE(4, POLYPIC_COEFF_F32)
     POLYPIC_P2G_CASE(8, POLYPIC_COEFF_F32)
@@ -344,14 +484,15 @@ cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], int R, int fmt, cu
 #undef POLYPIC_P2G_CASE
     if (e != cudaSuccess) return e;
     const GridGeom &g = P.g;
-    auto blocks_for = [&](int a) {
-        int64_t tot = (int64_t)(g.n[0] + (a == 0)) * (g.n[1] + (a == 1)) * (g.n[2] + (a == 2));
-        int64_t nb = (tot + 255) / 256;
-        return (int)(nb < 152 * 64 ? nb : 152 * 64);
+    auto launch = [&](auto kern, int a) {
+        const int dX = g.n[0] + (a == 0), dY = g.n[1] + (a == 1), dZ = g.n[2] + (a == 2);
+        dim3 grid((dX + 127) / 128, dY < 1024 ? dY : 1024, dZ < 64 ? dZ : 64);
+        kern<<<grid, 128, 0, s>>>(g, P.tile_live, P.scratch, gm[a], gp[a], gv ? gv[a] : nullptr, dt,
+                                 gravity ? gravity[a] : 0.0f);
     };
-    k_p2g_reduce<0><<<blocks_for(0), 256, 0, s>>>(g, P.cell_start, P.scratch, gm[0], gp[0]);
-    k_p2g_reduce<1><<<blocks_for(1), 256, 0, s>>>(g, P.cell_start, P.scratch, gm[1], gp[1]);
-    k_p2g_reduce<2><<<blocks_for(2), 256, 0, s>>>(g, P.cell_start, P.scratch, gm[2], gp[2]);
+    launch(k_p2g_reduce<0>, 0);
+    launch(k_p2g_reduce<1>, 1);
+    launch(k_p2g_reduce<2>, 2);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ struct P2GArgs {
     const float *scale;        // 16-bit formats: per-particle s_p
     const uint32_t *perm, *cell_start;
     float *scratch;            // p2g_scratch_bytes(): one tile region per tile
+    uint8_t *tile_live;        // one flag per tile, written by every CTA
     uint32_t *status;
     uint32_t nblocks;          // num_keys / 32
     float dxpow[7];            // dx^L, L = 0..6 (FP32 coefficients -> dimensionless)
@@ -45,7 +46,9 @@ struct P2GArgs {
 
 size_t p2g_scratch_bytes(int64_t num_keys);
 
-// Writes all faces of gm[3] (mass) and gp[3] (momentum).
-cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], int R, int fmt, cudaStream_t s);
+// Writes all faces of gm[3] (mass) and gp[3] (momentum); with gv non-NULL
+// also the single-phase grid update (v = mv/m + dt g, zero on wall faces).
+cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], float dt,
+                const float gravity[3], int R, int fmt, cudaStream_t s);
 
 }  // namespace polypic

@@ -179,11 +179,15 @@ template <> struct Codec<POLYPIC_COEFF_F32> {
 template <> struct Codec<POLYPIC_COEFF_BF16> {
     using T = __nv_bfloat16;
     __device__ static float load(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    __device__ static float decode(uint16_t bits) {
+        return __bfloat162float(__ushort_as_bfloat16(bits));
+    }
     __device__ static __nv_bfloat16 encode(float v) { return __float2bfloat16_rn(v); }
 };
 template <> struct Codec<POLYPIC_COEFF_F16> {
     using T = __half;
     __device__ static float load(const __half *p) { return __half2float(*p); }
+    __device__ static float decode(uint16_t bits) { return __half2float(__ushort_as_half(bits)); }
     __device__ static __half encode(float v) { return __float2half_rn(v); }
 };
 
