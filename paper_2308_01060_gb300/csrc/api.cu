@@ -30,8 +30,13 @@ size_t required_ws(const polypic_ctx *c, int64_t nf, int64_t ns) {
     size_t a = sort_scratch_bytes(n, c->num_keys);
     size_t b = p2g_scratch_bytes(c->num_keys);
     size_t d = pcg_scratch_bytes(c->geom);
+    // the G2P adjoint holds its coefficient adjoint next to the P2G scratch
+    size_t e = c->cfg.coeff_format == POLYPIC_COEFF_F32
+                   ? adjoint_scratch_bytes(n, c->cfg.num_modes) + b + 256
+                   : 0;
     size_t m = a > b ? a : b;
     m = m > d ? m : d;
+    m = m > e ? m : e;
     return m + 4096;
 }
 

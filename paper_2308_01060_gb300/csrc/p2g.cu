@@ -84,12 +84,21 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int R, int FMT, int A>
-__device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, float *st, int lane) {
+template <int R, int FMT, int A, bool ADJ>
+__device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, uint32_t slot,
+                                               float *st, int lane) {
     using S = Stage<R>;
     cp_async4(st + S::kX * 32 + lane, P.x + p);
     cp_async4(st + S::kY * 32 + lane, P.y + p);
     cp_async4(st + S::kZ * 32 + lane, P.z + p);
+    if constexpr (ADJ) {
+        // adjoint scatter: unit weight, coefficients mu (slot order) from scratch
+        st[S::kM * 32 + lane] = 1.0f;
+        const float *c = P.mu + (int64_t)A * R * P.count + slot;
+#pragma unroll
+        for (int r = 0; r < R; ++r, c += P.count) cp_async4(st + (S::kC + r) * 32 + lane, c);
+        return;
+    }
     cp_async4(st + S::kM * 32 + lane, P.mass + p);
     if (P.mass_abs) cp_async4(st + S::kMabs * 32 + lane, P.mass_abs + p);
     reinterpret_cast<uint32_t *>(st)[S::kIdx * 32 + lane] = p;
@@ -120,11 +129,30 @@ __device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, flo
 
 // One particle's contribution to the lane's padded footprint on grid A.
 // fu: stencil along A (face offset), fv / fw: the other two axes (centre).
-template <int R, int FMT, int A>
+// Fit factors of the G2P least-squares fit in physical units (the adjoint
+// scatter): G0 = W, G1 = 4 F1 / dx, G2 = (1, -2, 1) / (2 dx^2), zero when guarded.
+template <int D>
+__device__ __forceinline__ void fit_rows(const Stencil1D &s, bool guard, float inv1, float inv2,
+                                         float (&G)[D][3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[0][k] = s.W[k];
+    if constexpr (D > 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G[1][k] = 4.0f * inv1 * s.F1[k];
+    }
+    if constexpr (D > 2) {
+        const float h = guard ? 0.0f : 0.5f * inv2;
+        G[2][0] = h;
+        G[2][1] = -2.0f * h;
+        G[2][2] = h;
+    }
+}
+
+template <int R, int FMT, int A, bool ADJ>
 __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, int lane, float mt,
                                            int shift, const Stencil1D &fu, const Stencil1D &fv,
-                                           const Stencil1D &fw, float (&am)[4][3][3],
-                                           float (&av)[4][3][3]) {
+                                           const Stencil1D &fw, bool gu, bool gv, bool gw,
+                                           float (&am)[4][3][3], float (&av)[4][3][3]) {
     using S = Stage<R>;
     constexpr int D = axis_degrees(R);
     const float cscale = FMT == POLYPIC_COEFF_F32 ? 1.0f : st[S::kScale * 32 + lane];
@@ -158,11 +186,17 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
                 }
             }
     float Fu[D][3], Fv[D][3], Fw[D][3];
-    axis_factors<D>(fu, Fu);
-    axis_factors<D>(fv, Fv);
-    axis_factors<D>(fw, Fw);
+    if constexpr (ADJ) {
+        fit_rows<D>(fu, gu, P.inv_dx, P.inv_dx2, Fu);
+        fit_rows<D>(fv, gv, P.inv_dx, P.inv_dx2, Fv);
+        fit_rows<D>(fw, gw, P.inv_dx, P.inv_dx2, Fw);
+    } else {
+        axis_factors<D>(fu, Fu);
+        axis_factors<D>(fv, Fv);
+        axis_factors<D>(fw, Fw);
+    }
     // FP32 coefficients are physical: dx^a goes into the degree-a factor rows
-    if constexpr (FMT == POLYPIC_COEFF_F32 && D > 1) {
+    if constexpr (!ADJ && FMT == POLYPIC_COEFF_F32 && D > 1) {
 #pragma unroll
         for (int a = 1; a < D; ++a)
 #pragma unroll
@@ -230,7 +264,7 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
 #pragma unroll
                 for (int du = 0; du < D; ++du) s = fmaf(T2[du][kv][kw], Gu[du][d], s);
                 av[d][kv][kw] = s;
-                am[d][kv][kw] = fmaf(Wm[d], wvw, am[d][kv][kw]);
+                if constexpr (!ADJ) am[d][kv][kw] = fmaf(Wm[d], wvw, am[d][kv][kw]);
             }
         }
 }
@@ -249,7 +283,7 @@ __device__ __forceinline__ uint32_t round_slot(uint32_t bs, uint32_t n_c, uint32
     return bs + before + __popc(mask & lt);
 }
 
-template <int R, int FMT, int A>
+template <int R, int FMT, int A, bool ADJ>
 __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t n_c,
                                          uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
                                          int gk, int lane, float *reg, float *stage, bool &bad) {
@@ -266,15 +300,15 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t
     // prologue: rounds 0 and 1 in flight, the index of round 2 loading
     {
         const uint32_t s0 = round_slot(bs, n_c, 0, lt), s1 = round_slot(bs, n_c, 1, lt);
-        if (n_c > 0) stage_particle<R, FMT, A>(P, P.perm[s0], st0, lane);
+        if (n_c > 0) stage_particle<R, FMT, A, ADJ>(P, P.perm[s0], s0, st0, lane);
         cp_async_commit();
-        if (n_c > 1) stage_particle<R, FMT, A>(P, P.perm[s1], st1, lane);
+        if (n_c > 1) stage_particle<R, FMT, A, ADJ>(P, P.perm[s1], s1, st1, lane);
         cp_async_commit();
     }
-    uint32_t pn = 0;
+    uint32_t pn = 0, sn = 0;
     {
-        const uint32_t s2 = round_slot(bs, n_c, 2, lt);
-        if (n_c > 2) pn = P.perm[s2];
+        sn = round_slot(bs, n_c, 2, lt);
+        if (n_c > 2) pn = P.perm[sn];
     }
     for (uint32_t r = 0; r < maxn; ++r) {
         float *st = (r & 1) ? st1 : st0;
@@ -297,17 +331,18 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t
                            aw = axis_decide(vw, false);
                 const int cu = A == 0 ? gi : (A == 1 ? gj : gk);
                 const int shift = au.base - (cu - 1);
-                accumulate<R, FMT, A>(P, st, lane, mt, shift, stencil_1d(au.t), stencil_1d(av_.t),
-                                      stencil_1d(aw.t), am, av);
+                accumulate<R, FMT, A, ADJ>(P, st, lane, mt, shift, stencil_1d(au.t),
+                                           stencil_1d(av_.t), stencil_1d(aw.t), au.guard,
+                                           av_.guard, aw.guard, am, av);
             } else {
                 bad = true;
             }
         }
         // refill this stage with round r + 2, start loading the index of round r + 3
-        if (n_c > r + 2) stage_particle<R, FMT, A>(P, pn, st, lane);
+        if (n_c > r + 2) stage_particle<R, FMT, A, ADJ>(P, pn, sn, st, lane);
         cp_async_commit();
-        const uint32_t s3 = round_slot(bs, n_c, r + 3, lt);
-        pn = n_c > r + 3 ? P.perm[s3] : 0u;
+        sn = round_slot(bs, n_c, r + 3, lt);
+        pn = n_c > r + 3 ? P.perm[sn] : 0u;
     }
     cp_async_wait<0>();
     // merge the 32 footprints into the block region, one node offset per phase
@@ -358,7 +393,7 @@ __device__ __forceinline__ void merge_tile(const float *smem_regions, const bool
     }
 }
 
-template <int R, int FMT>
+template <int R, int FMT, bool ADJ>
 __global__ void __launch_bounds__(kP2GWarps * 32, 1) k_p2g_tiles(P2GArgs P) {
     extern __shared__ float smem[];
     __shared__ bool s_empty[kP2GWarps];
@@ -387,9 +422,9 @@ __global__ void __launch_bounds__(kP2GWarps * 32, 1) k_p2g_tiles(P2GArgs P) {
         const int ci = lane & 3, cj = (lane >> 2) & 3, ck = lane >> 4;
         const int gi = i0 + ci, gj = j0 + cj, gk = k0 + ck;
         bool bad = false;
-        p2g_pass<R, FMT, 0>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-        p2g_pass<R, FMT, 1>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-        p2g_pass<R, FMT, 2>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+        p2g_pass<R, FMT, 0, ADJ>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+        p2g_pass<R, FMT, 1, ADJ>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+        p2g_pass<R, FMT, 2, ADJ>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.status, kFlagOutOfDomain);
     }
     __syncthreads();
@@ -399,19 +434,19 @@ __global__ void __launch_bounds__(kP2GWarps * 32, 1) k_p2g_tiles(P2GArgs P) {
     merge_tile<2>(s_reg, s_empty, dst);
 }
 
-template <int R, int FMT>
+template <int R, int FMT, bool ADJ>
 static cudaError_t launch_tiles(const P2GArgs &P, int grid, cudaStream_t s) {
     const int smem = (kP2GWarps * kRegionFloats + kP2GWarps * Stage<R>::kFloatsPerWarp) * 4;
     static int configured_device = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (configured_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_p2g_tiles<R, FMT>,
+        cudaError_t e = cudaFuncSetAttribute(k_p2g_tiles<R, FMT, ADJ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured_device = dev;
     }
-    k_p2g_tiles<R, FMT><<<grid, kP2GWarps * 32, smem, s>>>(P);
+    k_p2g_tiles<R, FMT, ADJ><<<grid, kP2GWarps * 32, smem, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -424,7 +459,8 @@ template <int A>
 __global__ void __launch_bounds__(128) k_p2g_reduce(GridGeom g, const uint8_t *__restrict__ live,
                                                     const float *__restrict__ scratch,
                                                     float *__restrict__ gm, float *__restrict__ gp,
-                                                    float *__restrict__ gv, float dt, float ga) {
+                                                    float *__restrict__ gv, float dt, float ga,
+                                                    bool accumulate) {
     const int dX = g.n[0] + (A == 0), dY = g.n[1] + (A == 1), dZ = g.n[2] + (A == 2);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= dX) return;
@@ -447,8 +483,8 @@ __global__ void __launch_bounds__(128) k_p2g_reduce(GridGeom g, const uint8_t *_
                         sv += src[tile_off(A, 1) + r];
                     }
             const int64_t idx = ((int64_t)k * dY + j) * dX + i;
-            gm[idx] = sm;
-            gp[idx] = sv;
+            if (gm) gm[idx] = sm;
+            gp[idx] = accumulate ? gp[idx] + sv : sv;
             if (gv) {
                 const int ia = A == 0 ? i : (A == 1 ? j : k);
                 float v = sm > 0.0f ? sv / sm : 0.0f;
@@ -463,12 +499,40 @@ size_t p2g_scratch_bytes(int64_t num_keys) {
     return (size_t)(num_keys / 256) * (kTileFloats * sizeof(float) + 1) + 512;
 }
 
+static cudaError_t reduce_tiles(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3],
+                                float dt, const float gravity[3], bool accumulate, cudaStream_t s) {
+    const GridGeom &g = P.g;
+    auto launch = [&](auto kern, int a) {
+        const int dX = g.n[0] + (a == 0), dY = g.n[1] + (a == 1), dZ = g.n[2] + (a == 2);
+        dim3 grid((dX + 127) / 128, dY < 1024 ? dY : 1024, dZ < 64 ? dZ : 64);
+        kern<<<grid, 128, 0, s>>>(g, P.tile_live, P.scratch, gm ? gm[a] : nullptr, gp[a],
+                                 gv ? gv[a] : nullptr, dt, gravity ? gravity[a] : 0.0f,
+                                 accumulate);
+    };
+    launch(k_p2g_reduce<0>, 0);
+    launch(k_p2g_reduce<1>, 1);
+    launch(k_p2g_reduce<2>, 2);
+    return cudaGetLastError();
+}
+
+cudaError_t p2g_adjoint_scatter(const P2GArgs &P, float *lv[3], bool accumulate, int R,
+                                cudaStream_t s) {
+    const int grid = (int)(P.nblocks / kP2GWarps);
+    cudaError_t e = cudaErrorInvalidValue;
+    if (R == 1) e = launch_tiles<1, POLYPIC_COEFF_F32, true>(P, grid, s);
+    if (R == 4) e = launch_tiles<4, POLYPIC_COEFF_F32, true>(P, grid, s);
+    if (R == 8) e = launch_tiles<8, POLYPIC_COEFF_F32, true>(P, grid, s);
+    if (R == 27) e = launch_tiles<27, POLYPIC_COEFF_F32, true>(P, grid, s);
+    if (e != cudaSuccess) return e;
+    return reduce_tiles(P, nullptr, lv, nullptr, 0.0f, nullptr, accumulate, s);
+}
+
 cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], float dt,
                 const float gravity[3], int R, int fmt, cudaStream_t s) {
     const int grid = (int)(P.nblocks / kP2GWarps);
     cudaError_t e = cudaErrorInvalidValue;
 #define POLYPIC_P2G_CASE(RR, FF) \
-    if (R == RR && fmt == FF) e = launch_tiles<RR, FF>(P, grid, s);
+    if (R == RR && fmt == FF) e = launch_tiles<RR, FF, false>(P, grid, s);
     POLYPIC_P2G_CASE(1, POLYPIC_COEFF_F32)
     POLYPIC_P2G_CASE(4, POLYPIC_COEFF_F32)
     POLYPIC_P2G_CASE(8, POLYPIC_COEFF_F32)
@@ -483,17 +547,7 @@ cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], floa
     POLYPIC_P2G_CASE(27, POLYPIC_COEFF_F16)
 #undef POLYPIC_P2G_CASE
     if (e != cudaSuccess) return e;
-    const GridGeom &g = P.g;
-    auto launch = [&](auto kern, int a) {
-        const int dX = g.n[0] + (a == 0), dY = g.n[1] + (a == 1), dZ = g.n[2] + (a == 2);
-        dim3 grid((dX + 127) / 128, dY < 1024 ? dY : 1024, dZ < 64 ? dZ : 64);
-        kern<<<grid, 128, 0, s>>>(g, P.tile_live, P.scratch, gm[a], gp[a], gv ? gv[a] : nullptr, dt,
-                                 gravity ? gravity[a] : 0.0f);
-    };
-    launch(k_p2g_reduce<0>, 0);
-    launch(k_p2g_reduce<1>, 1);
-    launch(k_p2g_reduce<2>, 2);
-    return cudaGetLastError();
+    return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
 }
 
 }  // namespace polypic

@@ -42,6 +42,9 @@ struct P2GArgs {
     uint32_t *status;
     uint32_t nblocks;          // num_keys / 32
     float dxpow[7];            // dx^L, L = 0..6 (FP32 coefficients -> dimensionless)
+    // adjoint scatter only: mu [3][R][count] in slot order, 1/dx, 1/dx^2
+    const float *mu;
+    float inv_dx, inv_dx2;
 };
 
 size_t p2g_scratch_bytes(int64_t num_keys);
@@ -50,5 +53,12 @@ size_t p2g_scratch_bytes(int64_t num_keys);
 // also the single-phase grid update (v = mv/m + dt g, zero on wall faces).
 cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], float dt,
                 const float gravity[3], int R, int fmt, cudaStream_t s);
+
+// Adjoint of the G2P fit's grid dependence: lv_ia (+)= sum_p sum_r mu_pra
+// G_r(x_ia - x_p), the same deterministic scatter with the fit factors
+// G_r = w s_r / d_r and unit weight.  Reads positions through perm, mu in
+// slot order.
+cudaError_t p2g_adjoint_scatter(const P2GArgs &P, float *lv[3], bool accumulate, int R,
+                                cudaStream_t s);
 
 }  // namespace polypic
