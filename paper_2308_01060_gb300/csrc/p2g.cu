@@ -160,31 +160,6 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
     // its aligned word when e is odd; (A R + r) is a compile-time constant.
     const uint32_t podd = reinterpret_cast<const uint32_t *>(st)[S::kIdx * 32 + lane] & 1u;
     const uint32_t par_even_row = podd, par_odd_row = podd ^ (uint32_t)(P.count & 1);
-    // coefficients (dimensionless c dx^L, or code * s_p) in (u, v, w) order
-    float C[D][D][D];
-#pragma unroll
-    for (int du = 0; du < D; ++du)
-#pragma unroll
-        for (int dv = 0; dv < D; ++dv)
-#pragma unroll
-            for (int dw = 0; dw < D; ++dw) {
-                const int a = deg_x<A>(du, dv, dw), b = deg_y<A>(du, dv, dw),
-                          c = deg_z<A>(du, dv, dw);
-                if (has_mode(R, a, b, c)) {
-                    const int r = mode_index(a, b, c);
-                    if constexpr (FMT == POLYPIC_COEFF_F32) {
-                        C[du][dv][dw] = st[(S::kC + r) * 32 + lane];
-                    } else {
-                        const uint32_t word =
-                            reinterpret_cast<const uint32_t *>(st)[(S::kC + r) * 32 + lane];
-                        const uint32_t odd = ((A * R + r) & 1) ? par_odd_row : par_even_row;
-                        const uint16_t code = (uint16_t)(word >> (odd << 4));
-                        C[du][dv][dw] = Codec<FMT>::decode(code);
-                    }
-                } else {
-                    C[du][dv][dw] = 0.0f;
-                }
-            }
     float Fu[D][3], Fv[D][3], Fw[D][3];
     if constexpr (ADJ) {
         fit_rows<D>(fu, gu, P.inv_dx, P.inv_dx2, Fu);
@@ -206,10 +181,44 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
                 Fw[a][k] *= P.dxpow[a];
             }
     }
-    // contract w, then v
-    float T2[D][3][3];
+    // mass weights first (padded along u: node d = k + shift)
+    if constexpr (!ADJ) {
+        const float w0 = mt * Fu[0][0], w1 = mt * Fu[0][1], w2 = mt * Fu[0][2];
+        const float Wm[4] = {shift ? 0.0f : w0, shift ? w0 : w1, shift ? w1 : w2, shift ? w2 : 0.0f};
+#pragma unroll
+        for (int kv = 0; kv < 3; ++kv)
+#pragma unroll
+            for (int kw = 0; kw < 3; ++kw) {
+                const float wvw = Fv[0][kv] * Fw[0][kw];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) am[d][kv][kw] = fmaf(Wm[d], wvw, am[d][kv][kw]);
+            }
+    }
+    // momentum, streamed over the degree du along u: contract w, then v, then
+    // u into the padded footprint (mass and the 16-bit scale s_p folded in)
+    const float mom_scale = FMT == POLYPIC_COEFF_F32 ? mt : mt * cscale;
 #pragma unroll
     for (int du = 0; du < D; ++du) {
+        float C[D][D];
+#pragma unroll
+        for (int dv = 0; dv < D; ++dv)
+#pragma unroll
+            for (int dw = 0; dw < D; ++dw) {
+                const int a = deg_x<A>(du, dv, dw), b = deg_y<A>(du, dv, dw),
+                          c = deg_z<A>(du, dv, dw);
+                C[dv][dw] = 0.0f;
+                if (has_mode(R, a, b, c)) {
+                    const int r = mode_index(a, b, c);
+                    if constexpr (FMT == POLYPIC_COEFF_F32) {
+                        C[dv][dw] = st[(S::kC + r) * 32 + lane];
+                    } else {
+                        const uint32_t word =
+                            reinterpret_cast<const uint32_t *>(st)[(S::kC + r) * 32 + lane];
+                        const uint32_t odd = ((A * R + r) & 1) ? par_odd_row : par_even_row;
+                        C[dv][dw] = Codec<FMT>::decode((uint16_t)(word >> (odd << 4)));
+                    }
+                }
+            }
         float T1[D][3];
 #pragma unroll
         for (int dv = 0; dv < D; ++dv)
@@ -219,54 +228,23 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
 #pragma unroll
                 for (int dw = 0; dw < D; ++dw)
                     if (has_mode(R, deg_x<A>(du, dv, dw), deg_y<A>(du, dv, dw), deg_z<A>(du, dv, dw)))
-                        s = fmaf(C[du][dv][dw], Fw[dw][kw], s);
+                        s = fmaf(C[dv][dw], Fw[dw][kw], s);
                 T1[dv][kw] = s;
             }
+        const float f0 = mom_scale * Fu[du][0], f1 = mom_scale * Fu[du][1],
+                    f2 = mom_scale * Fu[du][2];
+        const float Gu[4] = {shift ? 0.0f : f0, shift ? f0 : f1, shift ? f1 : f2, shift ? f2 : 0.0f};
 #pragma unroll
         for (int kv = 0; kv < 3; ++kv)
 #pragma unroll
             for (int kw = 0; kw < 3; ++kw) {
-                float s = 0.0f;
+                float t2 = 0.0f;
 #pragma unroll
-                for (int dv = 0; dv < D; ++dv) s = fmaf(T1[dv][kw], Fv[dv][kv], s);
-                T2[du][kv][kw] = s;
+                for (int dv = 0; dv < D; ++dv) t2 = fmaf(T1[dv][kw], Fv[dv][kv], t2);
+#pragma unroll
+                for (int d = 0; d < 4; ++d) av[d][kv][kw] = fmaf(t2, Gu[d], av[d][kv][kw]);
             }
     }
-    // padded factors along u: node d = k + shift; mass (and the 16-bit scale
-    // s_p for the momentum) folded in
-    const float mom_scale = FMT == POLYPIC_COEFF_F32 ? mt : mt * cscale;
-    float Gu[D][4], Wm[4];
-#pragma unroll
-    for (int du = 0; du < D; ++du) {
-        const float f0 = mom_scale * Fu[du][0], f1 = mom_scale * Fu[du][1],
-                    f2 = mom_scale * Fu[du][2];
-        Gu[du][0] = shift ? 0.0f : f0;
-        Gu[du][1] = shift ? f0 : f1;
-        Gu[du][2] = shift ? f1 : f2;
-        Gu[du][3] = shift ? f2 : 0.0f;
-    }
-    {
-        const float w0 = mt * Fu[0][0], w1 = mt * Fu[0][1], w2 = mt * Fu[0][2];
-        Wm[0] = shift ? 0.0f : w0;
-        Wm[1] = shift ? w0 : w1;
-        Wm[2] = shift ? w1 : w2;
-        Wm[3] = shift ? w2 : 0.0f;
-    }
-    // contract u into the footprint; mass weights
-#pragma unroll
-    for (int kv = 0; kv < 3; ++kv)
-#pragma unroll
-        for (int kw = 0; kw < 3; ++kw) {
-            const float wvw = Fv[0][kv] * Fw[0][kw];
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                float s = av[d][kv][kw];
-#pragma unroll
-                for (int du = 0; du < D; ++du) s = fmaf(T2[du][kv][kw], Gu[du][d], s);
-                av[d][kv][kw] = s;
-                if constexpr (!ADJ) am[d][kv][kw] = fmaf(Wm[d], wvw, am[d][kv][kw]);
-            }
-        }
 }
 
 // Index in block region A of node (ix, iy, iz) relative to the region origin.
@@ -394,7 +372,9 @@ __device__ __forceinline__ void merge_tile(const float *smem_regions, const bool
 }
 
 template <int R, int FMT, bool ADJ>
-__global__ void __launch_bounds__(kP2GWarps * 32, 1) k_p2g_tiles(P2GArgs P) {
+// 27 modes keep the compiler's register allocation (one CTA per SM measured
+// faster); fewer modes fit two CTAs per SM without spills.
+__global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles(P2GArgs P) {
     extern __shared__ float smem[];
     __shared__ bool s_empty[kP2GWarps];
     float *s_reg = smem;                                     // [8][kRegionFloats]

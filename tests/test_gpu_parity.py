@@ -281,3 +281,47 @@ def test_16bit_coefficients_round_trip(fmt, tol):
     assert max(errs) < tol, errs
     for a in range(3):
         assert rel(np_(g2.mass[a]), gm[a]) < TOL
+
+
+# ------------------------------------------------------------------ projection
+
+def test_pcg_projection_matches_oracle():
+    """Jacobi-PCG with FP64 reductions on the cells holding fluid particles:
+    same projected field as the oracle's FP64 solve, divergence-free."""
+    sc = scenes.dam_break_scene(n=24, R=1, dt=1e-3)
+    f = sc.fluid
+    ctx = pp.Context(sc.n, sc.dx, 1)
+    ps, ws = sorted_particles(ctx, scenes.ParticleSet(x=f.x, mass=f.mass, coeff=None, num_modes=1))
+    gv = random_grid_velocity(sc.n, sc.dx, seed=77)
+    rng = np.random.default_rng(3)
+    gm = [(rng.uniform(0.5, 1.5, s)).astype(np.float32) for s in (oracle.face_shape(a, sc.n) for a in range(3))]
+    gp = [(gm[a] * gv[a]).astype(np.float32) for a in range(3)]
+    g = grid_from_host(ctx, mass=gm, mom=gp)
+    prm = pp.UpdateSettings(dt=sc.dt, project=True, pcg_rtol=1e-6, pcg_maxiter=2000)
+    pp.polypic_grid_update(ctx, g, prm, fluid_particles=ps, ws=ws)
+    assert pp.polypic_check_device_status(ctx) == 0
+    fv = oracle.grid_update(sc.n, sc.dt, prm.gravity, gm, gp)
+    fluid = np.zeros((sc.n[2], sc.n[1], sc.n[0]), dtype=bool)
+    cells = np.floor(f.x.astype(np.float32) * np.float32(1 / sc.dx)).astype(int)
+    fluid[cells[2], cells[1], cells[0]] = True
+    vp, _, _ = oracle.pcg_project(sc.n, sc.dx, sc.dt, 1000.0, fluid, fv, rtol=1e-10, maxiter=5000)
+    for a in range(3):
+        assert rel(np_(g.vel[a]), vp[a]) < 1e-4
+    v = [np_(g.vel[a]).astype(np.float64) for a in range(3)]
+    div = (np.diff(v[0], axis=2) + np.diff(v[1], axis=1) + np.diff(v[2], axis=0)) / sc.dx
+    div0 = (np.diff(fv[0], axis=2) + np.diff(fv[1], axis=1) + np.diff(fv[2], axis=0)) / sc.dx
+    assert np.abs(div[fluid]).max() <= 1e-4 * np.abs(div0[fluid]).max()
+
+
+def test_pcg_reports_not_converged():
+    sc = scenes.dam_break_scene(n=24, R=1, dt=1e-3)
+    f = sc.fluid
+    ctx = pp.Context(sc.n, sc.dx, 1)
+    ps, ws = sorted_particles(ctx, scenes.ParticleSet(x=f.x, mass=f.mass, coeff=None, num_modes=1))
+    gv = random_grid_velocity(sc.n, sc.dx, seed=78)
+    g = grid_from_host(ctx, mass=[np.ones_like(v) for v in gv], mom=gv)
+    prm = pp.UpdateSettings(dt=sc.dt, project=True, pcg_rtol=1e-12, pcg_maxiter=3)
+    with pytest.raises(pp.PolyPICError) as ei:
+        pp.polypic_grid_update(ctx, g, prm, fluid_particles=ps, ws=ws)
+    assert ei.value.name == "NOT_CONVERGED"
+    assert pp.polypic_check_device_status(ctx) == 5

@@ -531,3 +531,16 @@ def test_block_interleave_order():
             rank[kk == c] = np.arange(np.sum(kk == c))
         order = np.lexsort((kk, rank))
         assert np.array_equal(order, np.arange(len(seg)))
+
+
+def test_affine_map_reduces_to_constant_map_at_zero_dt():
+    """Eq 12: xi = x_p + (I + dt C)^-1 (x - x_p) is the identity shift at dt = 0."""
+    sc = scenes.parity_scene(n=12, R=8, seed=12, random_mode_init=True)
+    f = sc.fluid
+    gm0, gp0 = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx)
+    gm1, gp1 = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx, map_affine=True, dt=0.0)
+    gm2, gp2 = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx, map_affine=True, dt=1e-3)
+    for a in range(3):
+        assert np.array_equal(gm0[a], gm1[a]) and np.allclose(gp0[a], gp1[a], rtol=0, atol=0)
+        assert np.array_equal(gm0[a], gm2[a])          # the map moves modes, not weights
+        assert not np.allclose(gp0[a], gp2[a], rtol=1e-12, atol=0)
