@@ -185,6 +185,26 @@ polypic_status polypic_sort(polypic_ctx *ctx, polypic_particles *p, void *ws, si
 polypic_status polypic_p2g(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
                            void *ws, size_t ws_bytes, void *stream);
 
+/* P2G exactly as polypic_p2g, but without a caller workspace: for callers
+ * that cannot allocate device memory while they run, e.g. a host application
+ * that reserves all of the GPU's memory at start-up and forbids allocation
+ * afterwards, or code whose allocator may not be entered from where the
+ * transfer is issued.  The paper has no counterpart; this is a deployment
+ * convenience.  Its scratch is a fixed array built into the library (about
+ * 33 MB, held on every GPU that loads the library until the process exits),
+ * enough for grids of at most 2048 key tiles, i.e.
+ * ceil(n_x/8) * ceil(n_y/8) * ceil(n_z/4) <= 2048 (64^3 uses 1024); larger
+ * grids return POLYPIC_ERR_WORKSPACE before anything is launched.  The call
+ * allocates nothing itself.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the one array and
+ * it keeps the previous call's contents (every launch writes each entry it
+ * later reads, so nothing needs clearing); calls that overlap on the GPU, on
+ * any stream or context of the process, race on it and must be serialised by
+ * the caller.  Inputs and outputs are as for polypic_p2g. */
+polypic_status polypic_p2g_noalloc(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
+                                   void *stream);
+
 /* Grid update (delegated to the host simulator by the paper; this minimal
  * form): v = mv/m where m > 0 else 0 (Eq 5, Eq 20 for the solid grid);
  * v~ = v + dt g; with a solid grid and drag_k > 0, implicit two-phase drag on

@@ -284,6 +284,34 @@ polypic_status polypic_p2g(polypic_ctx *ctx, const polypic_particles *p, polypic
     return do_p2g(ctx, p, g, ws, ws_bytes, as_stream(stream));
 }
 
+polypic_status polypic_p2g_noalloc(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
+                                   void *stream) {
+    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s = check_sorted(p);
+    if (s != POLYPIC_OK) return s;
+    if ((s = check_coeff(ctx, p)) != POLYPIC_OK) return s;
+    if (!grid_ok(g, true, true, false)) return POLYPIC_ERR_INVALID_ARG;
+    if (ctx->num_keys / 256 > (int64_t)p2g_builtin_max_tiles()) return POLYPIC_ERR_WORKSPACE;
+    P2GArgs P{};
+    P.g = ctx->geom;
+    P.count = p->count;
+    P.x = p->x[0];
+    P.y = p->x[1];
+    P.z = p->x[2];
+    P.mass = p->mass;
+    P.mass_abs = p->mass_abs;
+    P.coeff = p->coeff;
+    P.scale = p->coeff_scale;
+    P.perm = p->perm;
+    P.cell_start = p->cell_start;
+    P.status = ctx->d_status;
+    P.nblocks = (uint32_t)(ctx->num_keys / 32);
+    for (int l = 0; l < 7; ++l) P.dxpow[l] = (float)std::pow(ctx->cfg.dx, (double)l);
+    if (p2g_builtin_scratch(&P.scratch, &P.tile_live) != cudaSuccess) return POLYPIC_ERR_CUDA;
+    return from_cuda(p2g(P, g->mass, g->mom, nullptr, 0.0f, nullptr, ctx->cfg.num_modes,
+                         ctx->cfg.coeff_format, as_stream(stream)));
+}
+
 polypic_status polypic_grid_update(polypic_ctx *ctx, polypic_grid *fluid, polypic_grid *solid,
                                    const polypic_particles *fluid_particles,
                                    const polypic_update_params *params, void *ws,

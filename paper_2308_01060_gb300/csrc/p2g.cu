@@ -21,6 +21,8 @@
 //     tile region in ascending block order and writes it to scratch;
 //   * k_p2g_reduce sums the at most 8 tile regions covering each face node in
 //     ascending tile order and writes the grids.
+#include <mutex>
+
 #include "p2g.cuh"
 
 namespace polypic {
@@ -473,6 +475,43 @@ __global__ void __launch_bounds__(128) k_p2g_reduce(GridGeom g, const uint8_t *_
             }
         }
     }
+}
+
+// ---------------------------------------------------------------- built-in scratch
+// For callers that cannot hand the library a workspace (see
+// polypic_p2g_noalloc): the tile regions and live flags live in fixed-size
+// device arrays that every GPU loading the library holds until the process
+// exits.  Host code must not pass these names to a kernel (on the host they
+// are stand-ins, not device addresses); p2g_builtin_scratch() looks the
+// device addresses up once per device with cudaGetSymbolAddress.
+constexpr int kBuiltinTiles = 2048;
+static __device__ __align__(256) float g_builtin_tiles[(size_t)kBuiltinTiles * kTileFloats];
+static __device__ __align__(256) uint8_t g_builtin_live[kBuiltinTiles];
+
+int p2g_builtin_max_tiles() { return kBuiltinTiles; }
+
+cudaError_t p2g_builtin_scratch(float **tiles, uint8_t **live) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static bool ready[kMaxDevices] = {};
+    static float *tile_ptr[kMaxDevices] = {};
+    static uint8_t *live_ptr[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[dev]) {
+        void *t = nullptr, *l = nullptr;
+        if ((e = cudaGetSymbolAddress(&t, g_builtin_tiles)) != cudaSuccess) return e;
+        if ((e = cudaGetSymbolAddress(&l, g_builtin_live)) != cudaSuccess) return e;
+        tile_ptr[dev] = static_cast<float *>(t);
+        live_ptr[dev] = static_cast<uint8_t *>(l);
+        ready[dev] = true;
+    }
+    *tiles = tile_ptr[dev];
+    *live = live_ptr[dev];
+    return cudaSuccess;
 }
 
 size_t p2g_scratch_bytes(int64_t num_keys) {

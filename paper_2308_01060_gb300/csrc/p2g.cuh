@@ -49,6 +49,12 @@ struct P2GArgs {
 
 size_t p2g_scratch_bytes(int64_t num_keys);
 
+// Built-in fixed-size scratch for polypic_p2g_noalloc: device addresses of the
+// tile regions and live flags on the current device (looked up on the first
+// call per device), and the number of tiles they hold.
+cudaError_t p2g_builtin_scratch(float **tiles, uint8_t **live);
+int p2g_builtin_max_tiles();
+
 // Writes all faces of gm[3] (mass) and gp[3] (momentum); with gv non-NULL
 // also the single-phase grid update (v = mv/m + dt g, zero on wall faces).
 cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], float dt,

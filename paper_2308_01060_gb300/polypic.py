@@ -69,6 +69,7 @@ _lib = None
 EXPORTS = [
     "polypic_create", "polypic_destroy", "polypic_num_keys", "polypic_cell_key",
     "polypic_grid_dims", "polypic_workspace_bytes", "polypic_sort", "polypic_p2g",
+    "polypic_p2g_noalloc",
     "polypic_grid_update", "polypic_g2p", "polypic_step", "polypic_g2p_adjoint",
     "polypic_grid_update_adjoint", "polypic_p2g_adjoint", "polypic_check_device_status",
     "polypic_status_string",
@@ -94,6 +95,7 @@ def load_library(path: str = LIB_PATH):
         "polypic_workspace_bytes": (ctypes.c_size_t, [_vp, ctypes.c_int64, ctypes.c_int64]),
         "polypic_sort": (st, [_vp, P(Particles), _vp, ctypes.c_size_t, _vp]),
         "polypic_p2g": (st, [_vp, P(Particles), P(Grid), _vp, ctypes.c_size_t, _vp]),
+        "polypic_p2g_noalloc": (st, [_vp, P(Particles), P(Grid), _vp]),
         "polypic_grid_update": (st, [_vp, P(Grid), P(Grid), P(Particles), P(UpdateParams), _vp,
                                      ctypes.c_size_t, _vp]),
         "polypic_g2p": (st, [_vp, P(Grid), P(Particles), P(Particles), ctypes.c_float, _vp,
@@ -302,6 +304,16 @@ def polypic_p2g(ctx: Context, p: ParticleState, g: GridState, ws: torch.Tensor, 
     wp, wb = _ws(ws)
     _check(load_library().polypic_p2g(ctx.handle, ctypes.byref(cs), ctypes.byref(cg), wp, wb,
                                       _stream(stream)), "polypic_p2g")
+
+
+def polypic_p2g_noalloc(ctx: Context, p: ParticleState, g: GridState, stream=None):
+    """P2G using the library's built-in scratch instead of a workspace, for
+    callers that must not allocate device memory while running (grids of at
+    most 2048 key tiles).  Calls that overlap on the GPU race on that scratch."""
+    cs = p.c_struct()
+    cg = g.c_struct()
+    _check(load_library().polypic_p2g_noalloc(ctx.handle, ctypes.byref(cs), ctypes.byref(cg),
+                                              _stream(stream)), "polypic_p2g_noalloc")
 
 
 def polypic_grid_update(ctx: Context, fluid: GridState, params: UpdateSettings,
