@@ -137,14 +137,12 @@ def algorithmic_bytes(R: int, fmt: str):
     return p2g, g2p
 
 
-def launches_per_step(num_keys: int) -> int:
-    """Kernels of ours per polypic_step (one phase, no projection): keys +
-    3-kernel count scan, 5 per radix pass (histogram, 3-kernel scan, scatter),
-    the block interleave, P2G tiles + 3 reductions with the grid update fused
-    in, G2P."""
-    bits = max(1, int(np.ceil(np.log2(num_keys))))
-    passes = (bits + 7) // 8
-    return 4 + 5 * passes + 1 + 4 + 1
+def launches_per_step() -> int:
+    """Kernels of ours per polypic_step (one phase, no projection): keys with
+    arrival ranks, the 3-kernel count scan, the scatter, the per-cell order,
+    the crowded-cell pass (exits at once when no cell holds more than 64
+    particles), P2G tiles + 3 reductions with the grid update fused in, G2P."""
+    return 1 + 3 + 1 + 1 + 1 + 4 + 1
 
 
 def make_state(pp, ctx, scene, device):
@@ -363,7 +361,7 @@ def our_arm(args):
     roofline = {
         "bound": "hbm", "achieved": round(dom_gbs, 1), "peak": hbm, "unit": "GB/s",
         "frac": round(dom_gbs / hbm, 4), "traffic": None,
-        "kernel": "polypic_p2g (k_p2g_blocks + 3 x k_p2g_reduce)" if dominant == "p2g"
+        "kernel": "polypic_p2g call (k_p2g_tiles + 3 x k_p2g_reduce)" if dominant == "p2g"
         else "polypic_g2p (k_g2p_tiles)",
         "algorithmic_bytes_per_particle": p2g_b if dominant == "p2g" else g2p_b,
         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
@@ -425,7 +423,7 @@ def our_arm(args):
             "roofline": roofline,
             "variants": variants,
             "e2e": e2e,
-            "gpu_launches": launches_per_step(main["ctx"].num_keys) * args.steps,
+            "gpu_launches": launches_per_step() * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
             "device_status": main["status"],

@@ -66,13 +66,12 @@ template <int A> __host__ __device__ constexpr int deg_z(int du, int dv, int dw)
 
 // ---------------------------------------------------------------- staging
 // Each lane prefetches its next particles with cp.async (4-byte copies) into
-// a private two-stage buffer laid out [stage][value][lane] (conflict-free):
+// a private multi-stage buffer laid out [stage][value][lane] (conflict-free):
 // x, y, z, m, m_abs, s_p, the particle index, then one 32-bit word per mode
 // (the coefficient, or for 16-bit formats the aligned word holding its code).
 template <int R> struct Stage {
     static constexpr int kX = 0, kY = 1, kZ = 2, kM = 3, kMabs = 4, kScale = 5, kIdx = 6, kC = 7;
     static constexpr int NV = kC + R;
-    static constexpr int kFloatsPerWarp = 2 * NV * 32;
 };
 
 __device__ __forceinline__ void cp_async4(float *dst, const void *src) {
@@ -263,6 +262,18 @@ __device__ __forceinline__ uint32_t round_slot(uint32_t bs, uint32_t n_c, uint32
     return bs + before + __popc(mask & lt);
 }
 
+// Rounds in flight per lane (cp.async groups).  Two measured fastest at 27
+// modes (four were 8% slower: the pipeline restarts for each component and
+// the prologue grows with the depth).
+#ifndef POLYPIC_P2G_STAGES
+#define POLYPIC_P2G_STAGES 2
+#endif
+constexpr int kStages = POLYPIC_P2G_STAGES;
+template <int R> constexpr int p2g_smem_bytes() {
+    return (kP2GWarps * kRegionFloats + kP2GWarps * kStages * Stage<R>::NV * 32) * 4;
+}
+static_assert(p2g_smem_bytes<27>() <= 227 * 1024, "P2G staging exceeds the shared memory of a CTA");
+
 template <int R, int FMT, int A, bool ADJ>
 __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t n_c,
                                          uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
@@ -276,28 +287,24 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t
 #pragma unroll
             for (int kw = 0; kw < 3; ++kw) am[d][kv][kw] = av[d][kv][kw] = 0.0f;
     const unsigned lt = (1u << lane) - 1u;
-    float *st0 = stage, *st1 = stage + S::NV * 32;
-    // prologue: rounds 0 and 1 in flight, the index of round 2 loading
-    {
-        const uint32_t s0 = round_slot(bs, n_c, 0, lt), s1 = round_slot(bs, n_c, 1, lt);
-        if (n_c > 0) stage_particle<R, FMT, A, ADJ>(P, P.perm[s0], s0, st0, lane);
-        cp_async_commit();
-        if (n_c > 1) stage_particle<R, FMT, A, ADJ>(P, P.perm[s1], s1, st1, lane);
+    // prologue: rounds 0 .. kStages-1 in flight, the index of round kStages loading
+#pragma unroll
+    for (int q = 0; q < kStages; ++q) {
+        const uint32_t sq = round_slot(bs, n_c, (uint32_t)q, lt);
+        if (n_c > (uint32_t)q)
+            stage_particle<R, FMT, A, ADJ>(P, P.perm[sq], sq, stage + q * S::NV * 32, lane);
         cp_async_commit();
     }
-    uint32_t pn = 0, sn = 0;
-    {
-        sn = round_slot(bs, n_c, 2, lt);
-        if (n_c > 2) pn = P.perm[sn];
-    }
+    uint32_t sn = round_slot(bs, n_c, kStages, lt);
+    uint32_t pn = n_c > (uint32_t)kStages ? P.perm[sn] : 0u;
     for (uint32_t r = 0; r < maxn; ++r) {
-        float *st = (r & 1) ? st1 : st0;
-        cp_async_wait<1>();
+        float *st = stage + (r % kStages) * S::NV * 32;
+        cp_async_wait<kStages - 1>();
         if (n_c > r) {
             const float px = st[S::kX * 32 + lane], py = st[S::kY * 32 + lane],
                         pz = st[S::kZ * 32 + lane];
             float mt = st[S::kM * 32 + lane];
-            if (P.mass_abs) mt += st[S::kMabs * 32 + lane];
+            if (!ADJ && P.mass_abs) mt += st[S::kMabs * 32 + lane];
             const float v0 = cell_coord(px, P.g.inv_dx), v1 = cell_coord(py, P.g.inv_dx),
                         v2 = cell_coord(pz, P.g.inv_dx);
             const bool ok = coord_valid(v0, P.g.n[0]) && coord_valid(v1, P.g.n[1]) &&
@@ -318,11 +325,11 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t
                 bad = true;
             }
         }
-        // refill this stage with round r + 2, start loading the index of round r + 3
-        if (n_c > r + 2) stage_particle<R, FMT, A, ADJ>(P, pn, sn, st, lane);
+        // refill this stage with round r + kStages; load the index of the round after
+        if (n_c > r + kStages) stage_particle<R, FMT, A, ADJ>(P, pn, sn, st, lane);
         cp_async_commit();
-        sn = round_slot(bs, n_c, r + 3, lt);
-        pn = n_c > r + 3 ? P.perm[sn] : 0u;
+        sn = round_slot(bs, n_c, r + kStages + 1, lt);
+        pn = n_c > r + kStages + 1 ? P.perm[sn] : 0u;
     }
     cp_async_wait<0>();
     // merge the 32 footprints into the block region, one node offset per phase
@@ -380,7 +387,7 @@ __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles
     extern __shared__ float smem[];
     __shared__ bool s_empty[kP2GWarps];
     float *s_reg = smem;                                     // [8][kRegionFloats]
-    float *s_stage = smem + kP2GWarps * kRegionFloats;        // [8][Stage::kFloatsPerWarp]
+    float *s_stage = smem + kP2GWarps * kRegionFloats;        // [8][kStages][NV][32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t tile = blockIdx.x;
     const bool tile_empty = P.cell_start[tile * 256] == P.cell_start[tile * 256 + 256];
@@ -394,7 +401,7 @@ __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles
     const uint32_t bs = P.cell_start[b * 32];
     const uint32_t maxn = __reduce_max_sync(0xffffffffu, n_c);
     float *reg = s_reg + warp * kRegionFloats;
-    float *stage = s_stage + warp * Stage<R>::kFloatsPerWarp;
+    float *stage = s_stage + warp * kStages * Stage<R>::NV * 32;
     if (lane == 0) s_empty[warp] = maxn == 0;
     if (maxn > 0) {
         for (int i = lane; i < kRegionFloats; i += 32) reg[i] = 0.0f;
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles
 
 template <int R, int FMT, bool ADJ>
 static cudaError_t launch_tiles(const P2GArgs &P, int grid, cudaStream_t s) {
-    const int smem = (kP2GWarps * kRegionFloats + kP2GWarps * Stage<R>::kFloatsPerWarp) * 4;
+    const int smem = p2g_smem_bytes<R>();
     static int configured_device = -1;
     int dev = 0;
     cudaGetDevice(&dev);

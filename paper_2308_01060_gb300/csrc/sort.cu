@@ -1,22 +1,23 @@
 // sort.cu -- bit-exact stable sort of particles by cell key.
 //
 // The paper has no sort; it is the device that makes the transfers
-// deterministic and coalesced.  Four pieces, none of which waits on another
-// CTA (reduce-then-scan only):
-//   1. k_keys:   key of every particle (FP32 cell decision), domain check,
-//                per-key counts with warp-aggregated integer atomics
-//                (integer addition is order independent, so counts are exact);
-//   2. scan:     exclusive prefix sum of the counts -> cell_start;
-//   3. radix:    LSD radix sort of (key, index) pairs, 8 bits or fewer per
-//                pass; each pass = per-tile digit histograms, a device-wide
-//                scan of the digit-major histogram table, and a stable
-//                scatter that ranks equal digits with __match_any_sync.
-//                Stability makes the permutation unique, so it is compared
-//                bit-exactly with a CPU stable sort;
-//   4. interleave: inside every block of 32 keys the stable order is dealt
-//                round-robin over the keys (round r = each key's r-th
-//                particle), so that a warp whose lanes own the 32 cells reads
-//                one contiguous run of slots per round.
+// deterministic and coalesced.  No kernel waits on another CTA:
+//   1. k_keys:     key of every particle (FP32 cell decision), domain check,
+//                  per-key counts with warp-aggregated integer atomics (exact:
+//                  integer addition is order independent) whose return values
+//                  give each particle an arrival rank inside its cell;
+//   2. scan:       exclusive prefix sum of the counts -> cell_start;
+//   3. k_scatter:  particle p to cell_start[key] + arrival rank, so every
+//                  cell's particles fill its range in a timing-dependent order;
+//   4. k_cell_order / k_crowded_cells: the stable order inside each cell is
+//                  ascending particle index (unique, so it is compared
+//                  bit-exactly with a CPU stable sort); it is recovered from
+//                  the arrival order by selection (small cells) or a CTA radix
+//                  sort (crowded cells) and written straight into the slot
+//                  order of the transfers: inside every block of 32 keys the
+//                  stable order is dealt round-robin over the keys (round r =
+//                  each key's r-th particle), so that a warp whose lanes own
+//                  the 32 cells reads one contiguous run of slots per round.
 #include "sort.cuh"
 
 namespace polypic {
@@ -26,9 +27,12 @@ __global__ void __launch_bounds__(256) k_keys(int64_t n, const float *__restrict
                                               const float *__restrict__ y,
                                               const float *__restrict__ z, GridGeom g,
                                               uint32_t *__restrict__ key,
+                                              uint32_t *__restrict__ rank,
                                               uint32_t *__restrict__ counts,
+                                              uint32_t *__restrict__ num_crowded,
                                               uint32_t *__restrict__ status) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) *num_crowded = 0;
     bool live = p < n;
     uint32_t k = 0;
     bool bad = false;
@@ -40,11 +44,16 @@ __global__ void __launch_bounds__(256) k_keys(int64_t n, const float *__restrict
         k = cell_key(g, cell_index(vx, g.n[0]), cell_index(vy, g.n[1]), cell_index(vz, g.n[2]));
         key[p] = k;
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kFlagOutOfDomain);
+    const int lane = threadIdx.x & 31;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kFlagOutOfDomain);
     unsigned active = __ballot_sync(0xffffffffu, live);
     if (live) {
-        unsigned peers = __match_any_sync(active, k);
-        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[k], (uint32_t)__popc(peers));
+        const unsigned peers = __match_any_sync(active, k);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader) old = atomicAdd(&counts[k], (uint32_t)__popc(peers));
+        old = __shfl_sync(active, old, leader);
+        rank[p] = old + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     }
 }
 
@@ -162,121 +171,150 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t L, uint32_
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- radix
-// Each CTA owns kRadixTile consecutive keys; warp w owns the kRadixItems*32
-// keys starting at tile + w * kRadixItems * 32, visited 32 at a time.
-__global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t *__restrict__ keys,
-                                                            int64_t n, int shift, int bits,
-                                                            uint32_t *__restrict__ hist,
-                                                            int ntiles) {
-    __shared__ uint32_t s_hist[256];
-    int radix = 1 << bits;
-    for (int i = threadIdx.x; i < 256; i += kRadixThreads) s_hist[i] = 0;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kRadixTile;
-    for (int i = threadIdx.x; i < kRadixTile; i += kRadixThreads) {
-        int64_t idx = base + i;
-        if (idx < n) atomicAdd(&s_hist[(keys[idx] >> shift) & (uint32_t)(radix - 1)], 1u);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < radix; d += kRadixThreads)
-        hist[(int64_t)d * ntiles + blockIdx.x] = s_hist[d];
+// ---------------------------------------------------------------- scatter
+// Every particle to cell_start[key] + its arrival rank: each cell's particles
+// land in its range, in an order that depends on the atomics' timing.
+__global__ void __launch_bounds__(256) k_scatter(int64_t n, const uint32_t *__restrict__ key,
+                                                 const uint32_t *__restrict__ rank,
+                                                 const uint32_t *__restrict__ cs,
+                                                 uint32_t *__restrict__ out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) out[cs[key[p]] + rank[p]] = (uint32_t)p;
 }
 
-template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(kRadixThreads) k_radix_down(
-    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n, int shift,
-    int bits, const uint32_t *__restrict__ offsets, int ntiles) {
-    constexpr int kWarps = kRadixThreads / 32;
-    __shared__ uint32_t s_warp[kWarps][256];
-    __shared__ uint32_t s_off[256];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint32_t mask = (1u << bits) - 1u;
-    for (int i = tid; i < kWarps * 256; i += kRadixThreads) (&s_warp[0][0])[i] = 0;
-    for (int d = tid; d < 256; d += kRadixThreads)
-        s_off[d] = d <= (int)mask ? offsets[(int64_t)d * ntiles + blockIdx.x] : 0u;
-    __syncthreads();
-
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)w * (kRadixItems * 32);
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t k[kRadixItems], v[kRadixItems], loc[kRadixItems];
-    int dg[kRadixItems];
-#pragma unroll
-    for (int r = 0; r < kRadixItems; ++r) {
-        int64_t idx = base + r * 32 + lane;
-        bool valid = idx < n;
-        k[r] = valid ? keys_in[idx] : 0u;
-        v[r] = valid ? (FIRST ? (uint32_t)idx : vals_in[idx]) : 0u;
-        int d = valid ? (int)((k[r] >> shift) & mask) : 256;  // 256: no digit
-        dg[r] = d;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t prior = d < 256 ? s_warp[w][d] : 0u;
-        __syncwarp();
-        if (d < 256 && lane == __ffs(peers) - 1) s_warp[w][d] = prior + (uint32_t)__popc(peers);
-        __syncwarp();
-        loc[r] = prior + (uint32_t)__popc(peers & lt);
-    }
-    __syncthreads();
-    // exclusive prefix of each digit's count over the warps (warp order = key order)
-    for (int d = tid; d <= (int)mask; d += kRadixThreads) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int ww = 0; ww < kWarps; ++ww) {
-            uint32_t c = s_warp[ww][d];
-            s_warp[ww][d] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kRadixItems; ++r) {
-        int d = dg[r];
-        if (d < 256) {
-            uint32_t pos = s_off[d] + s_warp[w][d] + loc[r];
-            if (!LAST) keys_out[pos] = k[r];
-            vals_out[pos] = v[r];
-        }
-    }
-}
-
-// ---------------------------------------------------------------- block interleave
+// ---------------------------------------------------------------- cell order
 // Slot order used by the transfers: inside each block of 32 keys, round r
-// lists the r-th particle (stable order) of every key holding more than r
-// particles, keys ascending.  One warp per block, lane = key.
-__global__ void __launch_bounds__(256) k_block_interleave(const uint32_t *__restrict__ in,
-                                                          const uint32_t *__restrict__ cs,
-                                                          uint32_t *__restrict__ out,
-                                                          uint32_t nblocks) {
+// lists the r-th particle (ascending particle index, i.e. the stable order)
+// of every key holding more than r particles, keys ascending.  One warp per
+// block, lane = key.  A lane finds its cell's r-th index by selection over
+// the cell's arrival-ordered range (the smallest index above the previous
+// one: indices are distinct), which costs n^2 loads for n particles, so cells
+// holding more than kSelectMax particles are listed for k_crowded_cells
+// instead; their slots are left to it.
+__global__ void __launch_bounds__(256) k_cell_order(const uint32_t *__restrict__ in,
+                                                    const uint32_t *__restrict__ cs,
+                                                    uint32_t *__restrict__ out, uint32_t nblocks,
+                                                    uint32_t *__restrict__ crowded,
+                                                    uint32_t *__restrict__ num_crowded) {
     const int lane = threadIdx.x & 31;
     const uint32_t b = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (b >= nblocks) return;
+    if (b >= nblocks) return;  // warp-uniform
     const uint32_t k = b * 32 + lane;
     const uint32_t s0 = cs[k], n = cs[k + 1] - s0, base = cs[b * 32];
-    const uint32_t maxn = __reduce_max_sync(0xffffffffu, n);
+    const bool select = n <= (uint32_t)kSelectMax;
+    if (!select) crowded[atomicAdd(num_crowded, 1u)] = k;
+    const uint32_t maxn = __reduce_max_sync(0xffffffffu, select ? n : 0u);
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t off = 0;
+    uint32_t off = 0, floor_idx = 0;
     for (uint32_t r = 0; r < maxn; ++r) {
         const unsigned mask = __ballot_sync(0xffffffffu, n > r);
-        if (n > r) out[base + off + __popc(mask & lt)] = in[s0 + r];
+        if (select && n > r) {
+            uint32_t best = 0xffffffffu;
+            for (uint32_t j = 0; j < n; ++j) {
+                const uint32_t e = __ldg(in + s0 + j);
+                best = (e >= floor_idx && e < best) ? e : best;
+            }
+            out[base + off + __popc(mask & lt)] = best;
+            floor_idx = best + 1u;
+        }
         off += __popc(mask);
     }
 }
 
+// Cells holding more than kSelectMax particles, one CTA per cell: a stable
+// LSD radix sort of the cell's indices (8-bit digits, ranked in chunks of 256
+// in order) between its range of `a` and of `b`, then the interleaved write.
+// Linear in the cell's population, so a crowded cell costs what its particles
+// cost.  Launched with a fixed grid; CTAs beyond the list exit at once.
+__global__ void __launch_bounds__(256) k_crowded_cells(const uint32_t *__restrict__ crowded,
+                                                       const uint32_t *__restrict__ num_crowded,
+                                                       uint32_t *a, uint32_t *b,
+                                                       const uint32_t *__restrict__ cs,
+                                                       uint32_t *__restrict__ out, int value_bits) {
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_wc[8][256];
+    __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_n[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t total_cells = *num_crowded;
+    for (uint32_t ci = blockIdx.x; ci < total_cells; ci += gridDim.x) {
+        const uint32_t k = crowded[ci];
+        const uint32_t s0 = cs[k], n = cs[k + 1] - s0;
+        uint32_t *src = a + s0, *dst = b + s0;
+        for (int shift = 0; shift < value_bits; shift += 8) {
+            // digit histogram -> exclusive digit starts
+            s_base[tid] = 0;
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) s_wc[ww][tid] = 0;
+            __syncthreads();
+            for (uint32_t i = tid; i < n; i += 256) atomicAdd(&s_base[(src[i] >> shift) & 255u], 1u);
+            __syncthreads();
+            uint32_t total;
+            const uint32_t start = block_exclusive_scan(s_base[tid], s_warp, &total);
+            s_base[tid] = start;
+            __syncthreads();
+            // stable scatter, 256 indices per chunk in order
+            for (uint32_t c0 = 0; c0 < n; c0 += 256) {
+                const uint32_t i = c0 + tid;
+                const bool valid = i < n;
+                const uint32_t v = valid ? src[i] : 0u;
+                const uint32_t d = valid ? (v >> shift) & 255u : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                if (valid && lane == __ffs(peers) - 1) s_wc[w][d] = (uint32_t)__popc(peers);
+                __syncthreads();
+                uint32_t run = 0;
+#pragma unroll
+                for (int ww = 0; ww < 8; ++ww) {
+                    const uint32_t c = s_wc[ww][tid];
+                    s_wc[ww][tid] = run;
+                    run += c;
+                }
+                __syncthreads();
+                if (valid) dst[s_base[d] + s_wc[w][d] + (uint32_t)__popc(peers & lt)] = v;
+                __syncthreads();
+                s_base[tid] += run;
+#pragma unroll
+                for (int ww = 0; ww < 8; ++ww) s_wc[ww][tid] = 0;
+                __syncthreads();
+            }
+            uint32_t *t = src;
+            src = dst;
+            dst = t;
+        }
+        // interleaved slots of the cell's sorted indices
+        const uint32_t blk = k >> 5, c = k & 31u;
+        if (tid < 32) s_n[tid] = cs[blk * 32 + tid + 1] - cs[blk * 32 + tid];
+        __syncthreads();
+        const uint32_t base = cs[blk * 32];
+        for (uint32_t q = tid; q < n; q += 256) {
+            uint32_t before = 0, pos = 0;
+#pragma unroll 8
+            for (uint32_t cc = 0; cc < 32; ++cc) {
+                const uint32_t nc = s_n[cc];
+                before += min(nc, q);
+                pos += (cc < c && nc > q) ? 1u : 0u;
+            }
+            out[base + before + pos] = src[q];
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- driver
-int key_bits(int64_t num_keys) {
-    int b = 1;
-    while (((int64_t)1 << b) < num_keys) ++b;
+static int value_bits(int64_t count) {
+    int b = 8;
+    while (b < 32 && ((int64_t)1 << b) < count) b += 8;
     return b;
 }
 
+static int64_t crowded_capacity(int64_t count) { return count / (kSelectMax + 1) + 1; }
+
 size_t sort_scratch_bytes(int64_t count, int64_t num_keys) {
-    int64_t ntiles = (count + kRadixTile - 1) / kRadixTile;
     size_t words = 0;
-    words += 5 * (size_t)count + 64;                          // key/value ping-pong + stable perm
-    words += 256 * (size_t)ntiles + 64;                       // digit histograms
-    words += scan_scratch_words(256 * ntiles) + 64;           // their scan
-    words += scan_scratch_words(num_keys + 1) + 64;           // cell-count scan
+    words += 3 * (size_t)count + 3 * 64;                       // rank, arrival order, radix buffer
+    words += (size_t)crowded_capacity(count) + 1 + 2 * 64;     // crowded-cell list and its length
+    words += scan_scratch_words(num_keys + 1) + 64;            // cell-count scan
     return words * sizeof(uint32_t) + 8 * 256;
 }
 
@@ -287,54 +325,25 @@ cudaError_t sort_particles(const GridGeom &g, int64_t num_keys, int64_t count, c
     cudaError_t e = cudaMemsetAsync(cell_start, 0, sizeof(uint32_t) * (num_keys + 1), s);
     if (e != cudaSuccess) return e;
     if (count == 0) return cudaSuccess;
-    int64_t ntiles = (count + kRadixTile - 1) / kRadixTile;
-    uint32_t *ka = ws.take<uint32_t>(count), *va = ws.take<uint32_t>(count);
-    uint32_t *kb = ws.take<uint32_t>(count), *vb = ws.take<uint32_t>(count);
-    uint32_t *stable = ws.take<uint32_t>(count);
-    uint32_t *hist = ws.take<uint32_t>(256 * ntiles);
-    uint32_t *hscan = ws.take<uint32_t>(scan_scratch_words(256 * ntiles));
+    uint32_t *rank = ws.take<uint32_t>(count);
+    uint32_t *arrival = ws.take<uint32_t>(count);
+    uint32_t *radix = ws.take<uint32_t>(count);
+    uint32_t *crowded = ws.take<uint32_t>(crowded_capacity(count));
+    uint32_t *num_crowded = ws.take<uint32_t>(1);
     uint32_t *cscan = ws.take<uint32_t>(scan_scratch_words(num_keys + 1));
     if (ws.overflow) return cudaErrorInvalidValue;
 
-    int kblocks = (int)((count + 255) / 256);
-    k_keys<<<kblocks, 256, 0, s>>>(count, x, y, z, g, key, cell_start, status);
+    const int pblocks = (int)((count + 255) / 256);
+    k_keys<<<pblocks, 256, 0, s>>>(count, x, y, z, g, key, rank, cell_start, num_crowded, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = exclusive_scan(cell_start, cell_start, num_keys + 1, cscan, s)) != cudaSuccess) return e;
-
-    int bits = key_bits(num_keys);
-    int passes = (bits + 7) / 8;
-    int per = (bits + passes - 1) / passes;
-    const uint32_t *kin = key;
-    const uint32_t *vin = nullptr;
-    int shift = 0;
-    for (int pass = 0; pass < passes; ++pass) {
-        int pb = (shift + per <= bits) ? per : bits - shift;
-        bool first = pass == 0, last = pass == passes - 1;
-        uint32_t *kout = (pass & 1) ? kb : ka;
-        uint32_t *vout = last ? stable : ((pass & 1) ? vb : va);
-        k_radix_up<<<(int)ntiles, kRadixThreads, 0, s>>>(kin, count, shift, pb, hist, (int)ntiles);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = exclusive_scan(hist, hist, ((int64_t)1 << pb) * ntiles, hscan, s)) != cudaSuccess)
-            return e;
-        if (first && last)
-            k_radix_down<true, true><<<(int)ntiles, kRadixThreads, 0, s>>>(
-                kin, vin, kout, vout, count, shift, pb, hist, (int)ntiles);
-        else if (first)
-            k_radix_down<true, false><<<(int)ntiles, kRadixThreads, 0, s>>>(
-                kin, vin, kout, vout, count, shift, pb, hist, (int)ntiles);
-        else if (last)
-            k_radix_down<false, true><<<(int)ntiles, kRadixThreads, 0, s>>>(
-                kin, vin, kout, vout, count, shift, pb, hist, (int)ntiles);
-        else
-            k_radix_down<false, false><<<(int)ntiles, kRadixThreads, 0, s>>>(
-                kin, vin, kout, vout, count, shift, pb, hist, (int)ntiles);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        kin = kout;
-        vin = vout;
-        shift += pb;
-    }
+    k_scatter<<<pblocks, 256, 0, s>>>(count, key, rank, cell_start, arrival);
     const uint32_t nblocks = (uint32_t)(num_keys / 32);
-    k_block_interleave<<<(nblocks + 7) / 8, 256, 0, s>>>(stable, cell_start, perm, nblocks);
+    k_cell_order<<<(nblocks + 7) / 8, 256, 0, s>>>(arrival, cell_start, perm, nblocks, crowded,
+                                                   num_crowded);
+    const int64_t cap = crowded_capacity(count);
+    k_crowded_cells<<<(int)(cap < 304 ? cap : 304), 256, 0, s>>>(
+        crowded, num_crowded, arrival, radix, cell_start, perm, value_bits(count));
     return cudaGetLastError();
 }
 

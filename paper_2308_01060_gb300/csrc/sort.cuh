@@ -6,9 +6,9 @@ namespace polypic {
 
 constexpr int kScanThreads = 256;
 constexpr int kScanTile = 4096;
-constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 16;
-constexpr int kRadixTile = kRadixThreads * kRadixItems;
+// Cells holding at most this many particles are ordered by per-lane
+// selection (quadratic in the population); larger ones by a CTA radix sort.
+constexpr int kSelectMax = 64;
 
 size_t scan_scratch_words(int64_t L);
 

@@ -64,6 +64,30 @@ def test_sort_ragged_and_odd_grid(count):
         assert np.array_equal(u32(ps.key), key)
 
 
+@pytest.mark.parametrize("crowd", [[64, 65, 300, 5000], [70000, 1, 65]])
+def test_sort_crowded_cells_bit_exact(crowd):
+    """Cells above and at the per-lane selection limit (64 particles) next to
+    sparse ones, in shuffled input order; 70000 particles need three 8-bit
+    digit passes over the particle index, fewer than 65536 need two."""
+    n = (16, 16, 8)
+    dx = 1 / 16
+    rng = np.random.default_rng(len(crowd))
+    cells = [(3, 4, 2), (4, 4, 2), (5, 9, 3), (12, 2, 6)]
+    parts = [(np.array(c)[:, None] + rng.uniform(0, 1, (3, m))) * dx for c, m in zip(cells, crowd)]
+    parts.append(rng.uniform(1.0, 7.0, (3, 3000)) * dx * np.array([[2.0], [2.0], [1.0]]))
+    x = np.concatenate(parts, axis=1)
+    x = np.ascontiguousarray(x[:, rng.permutation(x.shape[1])]).astype(np.float32)
+    ctx = pp.Context(n, dx, 1)
+    ps = pp.upload_particles(ctx, x, np.ones(x.shape[1], np.float32))
+    ws = ctx.workspace(x.shape[1])
+    for _ in range(2):                      # the second call reuses the workspace
+        pp.polypic_sort(ctx, ps, ws)
+        perm, cs = oracle.particle_order(x, n, dx)
+        assert np.array_equal(u32(ps.cell_start), cs)
+        assert np.array_equal(u32(ps.perm), perm)
+    assert pp.polypic_check_device_status(ctx) == 0
+
+
 def test_sort_flags_out_of_domain():
     n = (16, 16, 16)
     dx = 1 / 16
