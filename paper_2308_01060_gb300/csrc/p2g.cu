@@ -274,8 +274,38 @@ template <int R> constexpr int p2g_smem_bytes() {
 }
 static_assert(p2g_smem_bytes<27>() <= 227 * 1024, "P2G staging exceeds the shared memory of a CTA");
 
+// The rounds of the three component passes form one stream (pass 0 rounds
+// 0 .. maxn-1, then pass 1, then pass 2) that flows through the stage ring
+// without draining: while a pass finishes and merges, the first rounds of the
+// next one are already in flight.  `ia` / `ir` name the next round to issue,
+// `sn` / `pn` its slot and particle index (loaded one round ahead).
+struct Pipe {
+    int ia;
+    uint32_t ir, sn, pn;
+    int ring;  // stage holding the next round to consume
+};
+
+template <int R, int FMT, bool ADJ>
+__device__ __forceinline__ void pipe_issue(const P2GArgs &P, Pipe &q, uint32_t bs, uint32_t n_c,
+                                           uint32_t maxn, unsigned lt, float *st, int lane) {
+    if (q.ia < 3 && n_c > q.ir) {  // q.ia is warp-uniform
+        if (q.ia == 0) stage_particle<R, FMT, 0, ADJ>(P, q.pn, q.sn, st, lane);
+        else if (q.ia == 1) stage_particle<R, FMT, 1, ADJ>(P, q.pn, q.sn, st, lane);
+        else stage_particle<R, FMT, 2, ADJ>(P, q.pn, q.sn, st, lane);
+    }
+    cp_async_commit();
+    if (q.ia < 3 && ++q.ir == maxn) {
+        q.ir = 0;
+        ++q.ia;
+    }
+    if (q.ia < 3) {
+        q.sn = round_slot(bs, n_c, q.ir, lt);
+        q.pn = n_c > q.ir ? P.perm[q.sn] : 0u;
+    }
+}
+
 template <int R, int FMT, int A, bool ADJ>
-__device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t n_c,
+__device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs, uint32_t n_c,
                                          uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
                                          int gk, int lane, float *reg, float *stage, bool &bad) {
     using S = Stage<R>;
@@ -287,18 +317,8 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t
 #pragma unroll
             for (int kw = 0; kw < 3; ++kw) am[d][kv][kw] = av[d][kv][kw] = 0.0f;
     const unsigned lt = (1u << lane) - 1u;
-    // prologue: rounds 0 .. kStages-1 in flight, the index of round kStages loading
-#pragma unroll
-    for (int q = 0; q < kStages; ++q) {
-        const uint32_t sq = round_slot(bs, n_c, (uint32_t)q, lt);
-        if (n_c > (uint32_t)q)
-            stage_particle<R, FMT, A, ADJ>(P, P.perm[sq], sq, stage + q * S::NV * 32, lane);
-        cp_async_commit();
-    }
-    uint32_t sn = round_slot(bs, n_c, kStages, lt);
-    uint32_t pn = n_c > (uint32_t)kStages ? P.perm[sn] : 0u;
     for (uint32_t r = 0; r < maxn; ++r) {
-        float *st = stage + (r % kStages) * S::NV * 32;
+        float *st = stage + q.ring * S::NV * 32;
         cp_async_wait<kStages - 1>();
         if (n_c > r) {
             const float px = st[S::kX * 32 + lane], py = st[S::kY * 32 + lane],
@@ -325,13 +345,10 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t
                 bad = true;
             }
         }
-        // refill this stage with round r + kStages; load the index of the round after
-        if (n_c > r + kStages) stage_particle<R, FMT, A, ADJ>(P, pn, sn, st, lane);
-        cp_async_commit();
-        sn = round_slot(bs, n_c, r + kStages + 1, lt);
-        pn = n_c > r + kStages + 1 ? P.perm[sn] : 0u;
+        // refill the stage just consumed with the next round of the stream
+        pipe_issue<R, FMT, ADJ>(P, q, bs, n_c, maxn, lt, st, lane);
+        q.ring = q.ring + 1 == kStages ? 0 : q.ring + 1;
     }
-    cp_async_wait<0>();
     // merge the 32 footprints into the block region, one node offset per phase
     const int cu = A == 0 ? ci : (A == 1 ? cj : ck);
     const int cv = A == 0 ? cj : ci;
@@ -353,6 +370,27 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, uint32_t bs, uint32_t
                 rv[idx] += av[d][kv][kw];
                 __syncwarp();
             }
+}
+
+// All three passes of one block: the prologue fills the ring once.
+template <int R, int FMT, bool ADJ>
+__device__ __forceinline__ void p2g_block(const P2GArgs &P, uint32_t bs, uint32_t n_c,
+                                          uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
+                                          int gk, int lane, float *reg, float *stage, bool &bad) {
+    const unsigned lt = (1u << lane) - 1u;
+    Pipe q;
+    q.ia = 0;
+    q.ir = 0;
+    q.ring = 0;
+    q.sn = round_slot(bs, n_c, 0, lt);
+    q.pn = n_c > 0 ? P.perm[q.sn] : 0u;
+#pragma unroll
+    for (int k = 0; k < kStages; ++k)
+        pipe_issue<R, FMT, ADJ>(P, q, bs, n_c, maxn, lt, stage + k * Stage<R>::NV * 32, lane);
+    p2g_pass<R, FMT, 0, ADJ>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+    p2g_pass<R, FMT, 1, ADJ>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+    p2g_pass<R, FMT, 2, ADJ>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+    cp_async_wait<0>();
 }
 
 // Adds block region A of warp w into the tile region (written to dst).
@@ -411,9 +449,7 @@ __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles
         const int ci = lane & 3, cj = (lane >> 2) & 3, ck = lane >> 4;
         const int gi = i0 + ci, gj = j0 + cj, gk = k0 + ck;
         bool bad = false;
-        p2g_pass<R, FMT, 0, ADJ>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-        p2g_pass<R, FMT, 1, ADJ>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-        p2g_pass<R, FMT, 2, ADJ>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+        p2g_block<R, FMT, ADJ>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.status, kFlagOutOfDomain);
     }
     __syncthreads();

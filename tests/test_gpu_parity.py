@@ -225,6 +225,48 @@ def test_g2p_parity(R):
     assert pp.polypic_check_device_status(ctx) == 0
 
 
+def _offset_particles(ctx, count, shift):
+    """Output arrays whose first element sits `shift` elements past an
+    allocation start, so that rows begin at every 16-byte phase."""
+    def buf(shape, dtype):
+        n = int(np.prod(shape))
+        return torch.zeros(n + shift, dtype=dtype, device="cuda")[shift:].view(shape)
+
+    ref = ctx.new_particles(count)
+    return pp.ParticleState(
+        x=buf((3, count), torch.float32), mass=buf((count,), torch.float32),
+        coeff=buf(tuple(ref.coeff.shape), ref.coeff.dtype), key=ref.key, perm=ref.perm,
+        cell_start=ref.cell_start,
+        scale=None if ref.scale is None else buf((count,), torch.float32))
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+@pytest.mark.parametrize("shift", [1, 3])
+def test_g2p_output_alignment_does_not_change_results(fmt, shift):
+    """G2P into output arrays at arbitrary 16-byte phases (odd particle count,
+    arrays offset by `shift` elements) writes the aligned call's values bit
+    for bit."""
+    sc = _scene(R=27, seed=12)
+    f = sc.fluid
+    keep = f.n - 1 if f.n % 2 == 0 else f.n                 # odd particle count
+    sub = scenes.ParticleSet(x=np.ascontiguousarray(f.x[:, :keep]), mass=f.mass[:keep],
+                             coeff=None, num_modes=27)
+    ctx = pp.Context(sc.n, sc.dx, 27, coeff_format=fmt)
+    ps, ws = sorted_particles(ctx, sub)
+    g = grid_from_host(ctx, vel=random_grid_velocity(sc.n, sc.dx, seed=31))
+    ref = ctx.new_particles(ps.count)
+    pp.polypic_g2p(ctx, g, ps, ref, 1e-3, ws)
+    out = _offset_particles(ctx, ps.count, shift)
+    pp.polypic_g2p(ctx, g, ps, out, 1e-3, ws)
+    assert torch.equal(out.x, ref.x)
+    assert torch.equal(out.mass, ref.mass)
+    assert torch.equal(out.coeff.view(torch.int16) if fmt != "f32" else out.coeff,
+                       ref.coeff.view(torch.int16) if fmt != "f32" else ref.coeff)
+    if fmt != "f32":
+        assert torch.equal(out.scale, ref.scale)
+    assert pp.polypic_check_device_status(ctx) == 0
+
+
 # ------------------------------------------------------------------ full step
 
 @pytest.mark.parametrize("R", [4, 27])
