@@ -126,6 +126,14 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- workload
 
+# DRAM bytes (read + write) per particle of one k_p2g_tiles<27, FP32> launch,
+# from a full ncu capture on the 96^3 dam break (1,557,376 particles: 537.3 MB
+# read, 13.6 MB written); P2G traffic grows in proportion to the particles, so
+# it scales to the 128^3 launch.  It must go back to None whenever the kernel
+# changes after that capture.
+P2G_TILES_DRAM_BYTES_PER_PARTICLE = (537.332224e6 + 13.564928e6) / 1557376
+
+
 def algorithmic_bytes(R: int, fmt: str):
     """Per particle-step bytes of the P2G and G2P calls.  P2G reads x, m and
     c; G2P reads x and writes x and c; the grid term (P2G writes of m and mv,
@@ -360,7 +368,10 @@ def our_arm(args):
     dom_gbs = p2g_gbs if dominant == "p2g" else g2p_gbs
     roofline = {
         "bound": "hbm", "achieved": round(dom_gbs, 1), "peak": hbm, "unit": "GB/s",
-        "frac": round(dom_gbs / hbm, 4), "traffic": None,
+        "frac": round(dom_gbs / hbm, 4),
+        "traffic": (round(P * P2G_TILES_DRAM_BYTES_PER_PARTICLE / 1e9, 4)
+                    if dominant == "p2g" and P2G_TILES_DRAM_BYTES_PER_PARTICLE else None),
+        "traffic_unit": "GB per launch (k_p2g_tiles only, scaled from the 96^3 capture)",
         "kernel": "polypic_p2g call (k_p2g_tiles + 3 x k_p2g_reduce)" if dominant == "p2g"
         else "polypic_g2p (k_g2p_tiles)",
         "algorithmic_bytes_per_particle": p2g_b if dominant == "p2g" else g2p_b,
