@@ -71,6 +71,7 @@ def _load():
         "or_keys": (None, [_i64, _F, _F, _F, _int, _int, _int, _dbl, _U32]),
         "or_stable_sort": (None, [_i64, _U32, ctypes.c_uint32, _U32, _U32]),
         "or_block_interleave": (None, [_U32, ctypes.c_uint32, _U32, _U32]),
+        "or_tile_group_order": (None, [_U32, ctypes.c_uint32, _U32, _U32]),
         "or_stencil_1d": (_int, [_dbl, _dbl, _int, _I, _D, _D, _D, _D, _I]),
         "or_particle_modes": (_int, [_dbl, _dbl, _dbl, _int, _int, _dbl, _I, _D, _D, _D, _I]),
         "or_p2g": (_int, [_i64, _D, _D, _D, _D, _D, _D, _int, _int, _int, _int, _dbl, _int,
@@ -175,6 +176,25 @@ def block_interleave(perm, nkeys: int, cell_start):
     _load().or_block_interleave(_p(perm, ctypes.c_uint32), nkeys, _p(cs, ctypes.c_uint32),
                                 _p(out, ctypes.c_uint32))
     return out
+
+
+def tile_group_order(perm, nkeys: int, cell_start):
+    """Grouped slot order of ordered phases from the stable order
+    (count-ranked groups of 32 cells per 256-key tile, each dealt round by
+    round)."""
+    perm = np.ascontiguousarray(perm, dtype=np.uint32)
+    cs = np.ascontiguousarray(cell_start, dtype=np.uint32)
+    out = np.empty_like(perm)
+    _load().or_tile_group_order(_p(perm, ctypes.c_uint32), nkeys, _p(cs, ctypes.c_uint32),
+                                _p(out, ctypes.c_uint32))
+    return out
+
+
+def ordered_particle_order(x32, n, dx):
+    """Slot order of an ordered phase with positions x32: (perm, cell_start)."""
+    nk = num_keys(n)
+    perm, cs = stable_sort(keys(x32, n, dx), nk)
+    return tile_group_order(perm, nk, cs), cs
 
 
 def particle_order(x32, n, dx):

@@ -197,6 +197,44 @@ void or_block_interleave(const uint32_t *in, uint32_t nkeys, const uint32_t *cel
     }
 }
 
+/* Grouped slot order of ordered particle phases.  Keys come in tiles of 256
+ * consecutive keys; a tile's particles keep their slot range
+ * [cell_start[256 t], cell_start[256 t + 256]).  Inside a tile the cells are
+ * ranked by particle count n: by min(n, 31) descending, ties by key
+ * ascending, and rank 32 g + l is lane l of group g.  Groups follow each other
+ * (g = 0..7); inside group g, round r = 0, 1, ... lists the r-th particle (in
+ * the stable order) of every lane whose cell holds more than r particles,
+ * lanes ascending.  in: the stable order; out: the slot order. */
+void or_tile_group_order(const uint32_t *in, uint32_t nkeys, const uint32_t *cell_start,
+                         uint32_t *out)
+{
+    for (uint32_t t = 0; t < nkeys / 256; ++t) {
+        uint32_t k0 = 256 * t, slot = cell_start[k0];
+        uint32_t ranked[256];
+        int r = 0;
+        for (int bucket = 31; bucket >= 0; --bucket)
+            for (uint32_t c = 0; c < 256; ++c) {
+                uint32_t n = cell_start[k0 + c + 1] - cell_start[k0 + c];
+                uint32_t q = n < 31 ? n : 31;
+                if (q == (uint32_t)bucket) ranked[r++] = c;
+            }
+        for (int g = 0; g < 8; ++g) {
+            uint32_t maxn = 0;
+            for (int l = 0; l < 32; ++l) {
+                uint32_t k = k0 + ranked[32 * g + l];
+                uint32_t n = cell_start[k + 1] - cell_start[k];
+                if (n > maxn) maxn = n;
+            }
+            for (uint32_t round = 0; round < maxn; ++round)
+                for (int l = 0; l < 32; ++l) {
+                    uint32_t k = k0 + ranked[32 * g + l];
+                    if (cell_start[k + 1] - cell_start[k] > round)
+                        out[slot++] = in[cell_start[k] + round];
+                }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* One-axis stencil of a particle on one face grid.
  *

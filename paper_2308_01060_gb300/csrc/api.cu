@@ -83,7 +83,8 @@ polypic_status do_sort(polypic_ctx *c, polypic_particles *p, void *ws, size_t ws
     if (p->count > 0 && !p->key) return POLYPIC_ERR_INVALID_ARG;
     Workspace W{static_cast<char *>(ws), ws_bytes, 0};
     return from_cuda(sort_particles(c->geom, c->num_keys, p->count, p->x[0], p->x[1], p->x[2],
-                                    p->key, p->perm, p->cell_start, c->d_status, W, s));
+                                    p->key, p->perm, p->cell_start, c->d_status, Layout::kBlocks,
+                                    W, s));
 }
 
 polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *g, void *ws,

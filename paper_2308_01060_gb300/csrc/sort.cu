@@ -19,6 +19,7 @@
 //                  each key's r-th particle), so that a warp whose lanes own
 //                  the 32 cells reads one contiguous run of slots per round.
 #include "sort.cuh"
+#include "tile_order.cuh"
 
 namespace polypic {
 
@@ -183,24 +184,20 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t n, const uint32_t *__re
 }
 
 // ---------------------------------------------------------------- cell order
-// Slot order used by the transfers: inside each block of 32 keys, round r
-// lists the r-th particle (ascending particle index, i.e. the stable order)
-// of every key holding more than r particles, keys ascending.  One warp per
-// block, lane = key.  A lane finds its cell's r-th index by selection over
-// the cell's arrival-ordered range (the smallest index above the previous
-// one: indices are distinct), which costs n^2 loads for n particles, so cells
-// holding more than kSelectMax particles are listed for k_crowded_cells
-// instead; their slots are left to it.
-__global__ void __launch_bounds__(256) k_cell_order(const uint32_t *__restrict__ in,
-                                                    const uint32_t *__restrict__ cs,
-                                                    uint32_t *__restrict__ out, uint32_t nblocks,
-                                                    uint32_t *__restrict__ crowded,
-                                                    uint32_t *__restrict__ num_crowded) {
+// Every layout deals a set of 32 cells ("lanes") round-robin: round r lists
+// the r-th particle (ascending input index, i.e. the stable order) of every
+// lane whose cell holds more than r, lanes ascending, from slot `base` on.
+// One warp per lane set.  A lane finds its cell's r-th index by selection over
+// the cell's arrival-ordered range [s0, s0 + n) (the smallest index above the
+// previous one: indices are distinct), which costs n^2 loads, so cells holding
+// more than kSelectMax particles are listed for k_crowded_cells instead and
+// their slots are left to it.
+__device__ __forceinline__ void deal_rounds(const uint32_t *__restrict__ in, uint32_t k,
+                                            uint32_t s0, uint32_t n, uint32_t base,
+                                            uint32_t *__restrict__ out,
+                                            uint32_t *__restrict__ crowded,
+                                            uint32_t *__restrict__ num_crowded) {
     const int lane = threadIdx.x & 31;
-    const uint32_t b = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (b >= nblocks) return;  // warp-uniform
-    const uint32_t k = b * 32 + lane;
-    const uint32_t s0 = cs[k], n = cs[k + 1] - s0, base = cs[b * 32];
     const bool select = n <= (uint32_t)kSelectMax;
     if (!select) crowded[atomicAdd(num_crowded, 1u)] = k;
     const uint32_t maxn = __reduce_max_sync(0xffffffffu, select ? n : 0u);
@@ -221,20 +218,52 @@ __global__ void __launch_bounds__(256) k_cell_order(const uint32_t *__restrict__
     }
 }
 
+// Block-interleaved layout: lane set = the 32 keys of a block (keys ascending).
+__global__ void __launch_bounds__(256) k_cell_order(const uint32_t *__restrict__ in,
+                                                    const uint32_t *__restrict__ cs,
+                                                    uint32_t *__restrict__ out, uint32_t nblocks,
+                                                    uint32_t *__restrict__ crowded,
+                                                    uint32_t *__restrict__ num_crowded) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t b = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (b >= nblocks) return;  // warp-uniform
+    const uint32_t k = b * 32 + lane;
+    const uint32_t s0 = cs[k];
+    deal_rounds(in, k, s0, cs[k + 1] - s0, cs[b * 32], out, crowded, num_crowded);
+}
+
+// Grouped layout: one CTA per tile, warp g deals group g of the ranked cells.
+__global__ void __launch_bounds__(256) k_cell_order_groups(const uint32_t *__restrict__ in,
+                                                           const uint32_t *__restrict__ cs,
+                                                           uint32_t *__restrict__ out,
+                                                           uint32_t *__restrict__ crowded,
+                                                           uint32_t *__restrict__ num_crowded) {
+    __shared__ TileOrder o;
+    const uint32_t tile = blockIdx.x;
+    if (cs[tile * kTileCells] == cs[tile * kTileCells + kTileCells]) return;  // CTA-uniform
+    rank_tile<256>(cs, tile, o);
+    const uint32_t rk = threadIdx.x;  // rank = 32 g + lane
+    const uint32_t k = tile * kTileCells + o.cell[rk];
+    deal_rounds(in, k, cs[k], o.n[rk], o.gstart[threadIdx.x >> 5], out, crowded, num_crowded);
+}
+
 // Cells holding more than kSelectMax particles, one CTA per cell: a stable
 // LSD radix sort of the cell's indices (8-bit digits, ranked in chunks of 256
-// in order) between its range of `a` and of `b`, then the interleaved write.
+// in order) between its range of `a` and of `b`, then the dealt slots.
 // Linear in the cell's population, so a crowded cell costs what its particles
 // cost.  Launched with a fixed grid; CTAs beyond the list exit at once.
+template <Layout L>
 __global__ void __launch_bounds__(256) k_crowded_cells(const uint32_t *__restrict__ crowded,
                                                        const uint32_t *__restrict__ num_crowded,
                                                        uint32_t *a, uint32_t *b,
                                                        const uint32_t *__restrict__ cs,
                                                        uint32_t *__restrict__ out, int value_bits) {
+    __shared__ TileOrder o;
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_wc[8][256];
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_n[32];
+    __shared__ uint32_t s_lane, s_setbase, s_rank;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t total_cells = *num_crowded;
@@ -282,18 +311,35 @@ __global__ void __launch_bounds__(256) k_crowded_cells(const uint32_t *__restric
             src = dst;
             dst = t;
         }
-        // interleaved slots of the cell's sorted indices
-        const uint32_t blk = k >> 5, c = k & 31u;
-        if (tid < 32) s_n[tid] = cs[blk * 32 + tid + 1] - cs[blk * 32 + tid];
+        // the cell's lane set: its 32 counts, its lane and the set's first slot
+        if constexpr (L == Layout::kBlocks) {
+            const uint32_t blk = k >> 5;
+            if (tid < 32) s_n[tid] = cs[blk * 32 + tid + 1] - cs[blk * 32 + tid];
+            if (tid == 0) {
+                s_lane = k & 31u;
+                s_setbase = cs[blk * 32];
+            }
+        } else {
+            const uint32_t tile = k / kTileCells;
+            rank_tile<256>(cs, tile, o);
+            if (o.cell[tid] == k - tile * kTileCells) s_rank = (uint32_t)tid;
+            __syncthreads();
+            const uint32_t grp = s_rank >> 5;
+            if (tid < 32) s_n[tid] = o.n[32 * grp + (uint32_t)tid];
+            if (tid == 0) {
+                s_lane = s_rank & 31u;
+                s_setbase = o.gstart[grp];
+            }
+        }
         __syncthreads();
-        const uint32_t base = cs[blk * 32];
+        const uint32_t l = s_lane, base = s_setbase;
         for (uint32_t q = tid; q < n; q += 256) {
             uint32_t before = 0, pos = 0;
 #pragma unroll 8
-            for (uint32_t cc = 0; cc < 32; ++cc) {
-                const uint32_t nc = s_n[cc];
-                before += min(nc, q);
-                pos += (cc < c && nc > q) ? 1u : 0u;
+            for (uint32_t ll = 0; ll < 32; ++ll) {
+                const uint32_t nl = s_n[ll];
+                before += min(nl, q);
+                pos += (ll < l && nl > q) ? 1u : 0u;
             }
             out[base + before + pos] = src[q];
         }
@@ -312,39 +358,61 @@ static int64_t crowded_capacity(int64_t count) { return count / (kSelectMax + 1)
 
 size_t sort_scratch_bytes(int64_t count, int64_t num_keys) {
     size_t words = 0;
-    words += 3 * (size_t)count + 3 * 64;                       // rank, arrival order, radix buffer
+    words += 4 * (size_t)count + 4 * 64;                       // key, rank, arrival, radix
     words += (size_t)crowded_capacity(count) + 1 + 2 * 64;     // crowded-cell list and its length
     words += scan_scratch_words(num_keys + 1) + 64;            // cell-count scan
     return words * sizeof(uint32_t) + 8 * 256;
 }
 
+bool take_sort_scratch(Workspace &ws, int64_t count, int64_t num_keys, SortScratch &S) {
+    S.key = ws.take<uint32_t>(count);
+    S.rank = ws.take<uint32_t>(count);
+    S.arrival = ws.take<uint32_t>(count);
+    S.radix = ws.take<uint32_t>(count);
+    S.crowded = ws.take<uint32_t>(crowded_capacity(count));
+    S.num_crowded = ws.take<uint32_t>(1);
+    S.cscan = ws.take<uint32_t>(scan_scratch_words(num_keys + 1));
+    return !ws.overflow;
+}
+
+cudaError_t finish_order(int64_t num_keys, int64_t count, const uint32_t *key,
+                         uint32_t *cell_start, uint32_t *perm, Layout layout,
+                         const SortScratch &S, cudaStream_t s) {
+    cudaError_t e = exclusive_scan(cell_start, cell_start, num_keys + 1, S.cscan, s);
+    if (e != cudaSuccess) return e;
+    const int pblocks = (int)((count + 255) / 256);
+    k_scatter<<<pblocks, 256, 0, s>>>(count, key, S.rank, cell_start, S.arrival);
+    const int64_t cap = crowded_capacity(count);
+    const int cgrid = (int)(cap < 304 ? cap : 304);
+    if (layout == Layout::kBlocks) {
+        const uint32_t nblocks = (uint32_t)(num_keys / 32);
+        k_cell_order<<<(nblocks + 7) / 8, 256, 0, s>>>(S.arrival, cell_start, perm, nblocks,
+                                                       S.crowded, S.num_crowded);
+        k_crowded_cells<Layout::kBlocks><<<cgrid, 256, 0, s>>>(
+            S.crowded, S.num_crowded, S.arrival, S.radix, cell_start, perm, value_bits(count));
+    } else {
+        k_cell_order_groups<<<(unsigned)(num_keys / kTileCells), 256, 0, s>>>(
+            S.arrival, cell_start, perm, S.crowded, S.num_crowded);
+        k_crowded_cells<Layout::kGroups><<<cgrid, 256, 0, s>>>(
+            S.crowded, S.num_crowded, S.arrival, S.radix, cell_start, perm, value_bits(count));
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t sort_particles(const GridGeom &g, int64_t num_keys, int64_t count, const float *x,
                            const float *y, const float *z, uint32_t *key, uint32_t *perm,
-                           uint32_t *cell_start, uint32_t *status, Workspace &ws,
+                           uint32_t *cell_start, uint32_t *status, Layout layout, Workspace &ws,
                            cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(cell_start, 0, sizeof(uint32_t) * (num_keys + 1), s);
     if (e != cudaSuccess) return e;
     if (count == 0) return cudaSuccess;
-    uint32_t *rank = ws.take<uint32_t>(count);
-    uint32_t *arrival = ws.take<uint32_t>(count);
-    uint32_t *radix = ws.take<uint32_t>(count);
-    uint32_t *crowded = ws.take<uint32_t>(crowded_capacity(count));
-    uint32_t *num_crowded = ws.take<uint32_t>(1);
-    uint32_t *cscan = ws.take<uint32_t>(scan_scratch_words(num_keys + 1));
-    if (ws.overflow) return cudaErrorInvalidValue;
-
-    const int pblocks = (int)((count + 255) / 256);
-    k_keys<<<pblocks, 256, 0, s>>>(count, x, y, z, g, key, rank, cell_start, num_crowded, status);
+    SortScratch S;
+    if (!take_sort_scratch(ws, count, num_keys, S)) return cudaErrorInvalidValue;
+    if (!key) key = S.key;
+    k_keys<<<(int)((count + 255) / 256), 256, 0, s>>>(count, x, y, z, g, key, S.rank, cell_start,
+                                                      S.num_crowded, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = exclusive_scan(cell_start, cell_start, num_keys + 1, cscan, s)) != cudaSuccess) return e;
-    k_scatter<<<pblocks, 256, 0, s>>>(count, key, rank, cell_start, arrival);
-    const uint32_t nblocks = (uint32_t)(num_keys / 32);
-    k_cell_order<<<(nblocks + 7) / 8, 256, 0, s>>>(arrival, cell_start, perm, nblocks, crowded,
-                                                   num_crowded);
-    const int64_t cap = crowded_capacity(count);
-    k_crowded_cells<<<(int)(cap < 304 ? cap : 304), 256, 0, s>>>(
-        crowded, num_crowded, arrival, radix, cell_start, perm, value_bits(count));
-    return cudaGetLastError();
+    return finish_order(num_keys, count, key, cell_start, perm, layout, S, s);
 }
 
 }  // namespace polypic

@@ -533,6 +533,54 @@ def test_block_interleave_order():
         assert np.array_equal(order, np.arange(len(seg)))
 
 
+def test_tile_group_order():
+    """The grouped slot order of ordered phases, checked through properties
+    that define it: a permutation keeping every 256-key tile's slot range;
+    each cell's particles in stable order; cells first appearing in
+    (min(n, 31) descending, key ascending) order; ranks 32 g .. 32 g + 31
+    filling consecutive slots; and inside a group, (round, lane) strictly
+    increasing."""
+    rng = np.random.default_rng(91)
+    n = (16, 8, 8)
+    dx = 1 / 16
+    x = np.stack([rng.uniform(1, n[b] - 1, 3000) * dx for b in range(3)]).astype(np.float32)
+    x[:, :400] = np.array([[5.5], [3.5], [2.5]]) * dx      # crowded cells: both in
+    x[:, 400:440] = np.array([[2.5], [2.5], [2.5]]) * dx   # the top bucket, key order decides
+    x[:, 440:460] = np.array([[1.5], [1.5], [1.5]]) * dx   # 16..30 particles: ranked by count,
+    x[:, 460:485] = np.array([[6.5], [1.5], [1.5]]) * dx   # not by key (the higher key is fuller)
+    nk = oracle.num_keys(n)
+    key = oracle.keys(x, n, dx)
+    perm, cs = oracle.stable_sort(key, nk)
+    out = oracle.tile_group_order(perm, nk, cs)
+    assert np.array_equal(np.sort(out), np.arange(x.shape[1]))
+    pos_in_cell = np.empty(x.shape[1], np.int64)
+    for k in range(nk):
+        pos_in_cell[perm[cs[k]:cs[k + 1]]] = np.arange(cs[k + 1] - cs[k])
+    groups = 0
+    for t in range(nk // 256):
+        lo, hi = cs[256 * t], cs[256 * t + 256]
+        seg = out[lo:hi]
+        assert np.array_equal(np.sort(seg), np.sort(perm[lo:hi]))
+        kk = key[seg].astype(np.int64)
+        for k in np.unique(kk):                      # stable order inside each cell
+            assert np.array_equal(seg[kk == k], perm[cs[k]:cs[k + 1]])
+        _, first = np.unique(kk, return_index=True)
+        ranked = kk[np.sort(first)]                  # cells by first appearance
+        cnt = np.minimum(cs[ranked + 1] - cs[ranked], 31)
+        for a_, b_, ca, cb in zip(ranked[:-1], ranked[1:], cnt[:-1], cnt[1:]):
+            assert ca > cb or (ca == cb and a_ < b_)
+        rank = {int(k): i for i, k in enumerate(ranked)}
+        grp = np.array([rank[int(k)] // 32 for k in kk])
+        lane = np.array([rank[int(k)] % 32 for k in kk])
+        assert np.all(np.diff(grp) >= 0)             # groups fill consecutive slots
+        rnd = pos_in_cell[seg]
+        for g in np.unique(grp):
+            m = grp == g
+            assert np.all(np.diff(rnd[m] * 32 + lane[m]) > 0)   # round by round, lane by lane
+        groups += len(np.unique(grp))
+    assert groups >= 8                               # several tiles hold more than one group
+
+
 def test_affine_map_reduces_to_constant_map_at_zero_dt():
     """Eq 12: xi = x_p + (I + dt C)^-1 (x - x_p) is the identity shift at dt = 0."""
     sc = scenes.parity_scene(n=12, R=8, seed=12, random_mode_init=True)
