@@ -13,89 +13,16 @@
 // so no denominator is formed; the guard zeroes G2 on a guarded axis.  The
 // FP32 output folds 1/dx and 1/dx^2 into the degree-1 and degree-2 factors and
 // so comes out in physical units; the 16-bit formats fit c dx^L, divide by the
-// per-particle scale s_p = max |c dx^L| and round to nearest even.  Outputs are written in sorted slot order (coalesced).
+// per-particle scale s_p = max |c dx^L| and round to nearest even.  Outputs
+// are written in sorted slot order (coalesced).
 #include "g2p.cuh"
+#include "g2p_fit.cuh"
 
 namespace polypic {
 
-constexpr int kG2PThreads = 256;
-// staged footprint per face grid: dims (11,10,6) (10,11,6) (10,10,7)
-template <int A> struct Tile {
-    static constexpr int X = A == 0 ? 11 : 10, Y = A == 1 ? 11 : 10, Z = A == 2 ? 7 : 6;
-    static constexpr int N = X * Y * Z;
-};
-constexpr int kTileOff1 = Tile<0>::N, kTileOff2 = Tile<0>::N + Tile<1>::N;
-constexpr int kTileFloats = Tile<0>::N + Tile<1>::N + Tile<2>::N;
-
-// inv1 = 1/dx, inv2 = 1/dx^2 give physical coefficients; 1 and 1 give c dx^L.
-template <int D>
-__device__ __forceinline__ void fit_factors(const Stencil1D &s, bool guard, float inv1,
-                                            float inv2, float (&G)[D][3]) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) G[0][k] = s.W[k];
-    if constexpr (D > 1) {
-        const float f = 4.0f * inv1;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) G[1][k] = f * s.F1[k];
-    }
-    if constexpr (D > 2) {
-        const float h = guard ? 0.0f : 0.5f * inv2;
-        G[2][0] = h;
-        G[2][1] = -2.0f * h;
-        G[2][2] = h;
-    }
-}
-
-// Fit of component A for one particle; Chat receives the dimensionless
-// coefficients c dx^L in canonical order (only the first R entries are set).
-template <int R, int A>
-__device__ __forceinline__ void g2p_component(const float *s_tile, int lx, int ly, int lz,
-                                              const Stencil1D &sx, bool gx, const Stencil1D &sy,
-                                              bool gy, const Stencil1D &sz, bool gz, float inv1,
-                                              float inv2, float (&Chat)[R]) {
-    constexpr int D = axis_degrees(R);
-    float Gx[D][3], Gy[D][3], Gz[D][3];
-    fit_factors<D>(sx, gx, inv1, inv2, Gx);
-    fit_factors<D>(sy, gy, inv1, inv2, Gy);
-    fit_factors<D>(sz, gz, inv1, inv2, Gz);
-    const float *t = s_tile + (A == 0 ? 0 : A == 1 ? kTileOff1 : kTileOff2);
-    // contract x
-    float U1[D][3][3];
-#pragma unroll
-    for (int kz = 0; kz < 3; ++kz)
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-            const float *row = t + ((lz + kz) * Tile<A>::Y + (ly + ky)) * Tile<A>::X + lx;
-            const float v0 = row[0], v1 = row[1], v2 = row[2];
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                U1[a][ky][kz] = fmaf(Gx[a][0], v0, fmaf(Gx[a][1], v1, Gx[a][2] * v2));
-        }
-    // contract y
-    float U2[D][D][3];
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < D; ++b)
-#pragma unroll
-            for (int kz = 0; kz < 3; ++kz)
-                U2[a][b][kz] = fmaf(Gy[b][0], U1[a][0][kz],
-                                    fmaf(Gy[b][1], U1[a][1][kz], Gy[b][2] * U1[a][2][kz]));
-    // contract z
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < D; ++b)
-#pragma unroll
-            for (int c = 0; c < D; ++c)
-                if (has_mode(R, a, b, c))
-                    Chat[mode_index(a, b, c)] = fmaf(Gz[c][0], U2[a][b][0],
-                                                     fmaf(Gz[c][1], U2[a][b][1], Gz[c][2] * U2[a][b][2]));
-}
-
 template <int R, int FMT>
 __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
-    __shared__ float s_tile[kTileFloats];
+    __shared__ float s_tile[kVelTileFloats];
     const GridGeom &g = A.g;
     const uint32_t tile = blockIdx.x;
     const uint32_t jb = A.cell_start[tile * 256], je = A.cell_start[tile * 256 + 256];
@@ -117,21 +44,7 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
     uint32_t pn = (j + kG2PThreads < je) ? A.perm[j + kG2PThreads] : 0u;
 
     // stage the three velocity footprints (nodes outside a grid read as 0)
-    auto stage = [&](int a, int X, int Y, int Z, int off) {
-        const int dX = g.n[0] + (a == 0), dY = g.n[1] + (a == 1), dZ = g.n[2] + (a == 2);
-        const float *src = A.vel[a];
-        for (int i = threadIdx.x; i < X * Y * Z; i += kG2PThreads) {
-            const int lx = i % X, ly = (i / X) % Y, lz = i / (X * Y);
-            const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-            float v = 0.0f;
-            if (gx >= 0 && gx < dX && gy >= 0 && gy < dY && gz >= 0 && gz < dZ)
-                v = src[((int64_t)gz * dY + gy) * dX + gx];
-            s_tile[off + i] = v;
-        }
-    };
-    stage(0, Tile<0>::X, Tile<0>::Y, Tile<0>::Z, 0);
-    stage(1, Tile<1>::X, Tile<1>::Y, Tile<1>::Z, kTileOff1);
-    stage(2, Tile<2>::X, Tile<2>::Y, Tile<2>::Z, kTileOff2);
+    stage_velocity<0>(g, A.vel, tx, ty, tz, s_tile);
     __syncthreads();
 
     using T = typename Codec<FMT>::T;
@@ -165,12 +78,18 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
             const Stencil1D sc0 = stencil_1d(ac0.t), sf0 = stencil_1d(af0.t);
             const Stencil1D sc1 = stencil_1d(ac1.t), sf1 = stencil_1d(af1.t);
             const Stencil1D sc2 = stencil_1d(ac2.t), sf2 = stencil_1d(af2.t);
-            g2p_component<R, 0>(s_tile, af0.base - ox, ac1.base - oy, ac2.base - oz, sf0,
-                                af0.guard, sc1, ac1.guard, sc2, ac2.guard, inv1, inv2, Chat[0]);
-            g2p_component<R, 1>(s_tile, ac0.base - ox, af1.base - oy, ac2.base - oz, sc0,
-                                ac0.guard, sf1, af1.guard, sc2, ac2.guard, inv1, inv2, Chat[1]);
-            g2p_component<R, 2>(s_tile, ac0.base - ox, ac1.base - oy, af2.base - oz, sc0,
-                                ac0.guard, sc1, ac1.guard, sf2, af2.guard, inv1, inv2, Chat[2]);
+            g2p_component<R, 0, Tile<0>::X, Tile<0>::Y>(s_tile, af0.base - ox, ac1.base - oy,
+                                                        ac2.base - oz, sf0, af0.guard, sc1,
+                                                        ac1.guard, sc2, ac2.guard, inv1, inv2,
+                                                        Chat[0]);
+            g2p_component<R, 1, Tile<1>::X, Tile<1>::Y>(s_tile + kVelTileOff1, ac0.base - ox,
+                                                        af1.base - oy, ac2.base - oz, sc0,
+                                                        ac0.guard, sf1, af1.guard, sc2,
+                                                        ac2.guard, inv1, inv2, Chat[1]);
+            g2p_component<R, 2, Tile<2>::X, Tile<2>::Y>(s_tile + kVelTileOff2, ac0.base - ox,
+                                                        ac1.base - oy, af2.base - oz, sc0,
+                                                        ac0.guard, sc1, ac1.guard, sf2,
+                                                        af2.guard, inv1, inv2, Chat[2]);
         } else {
 #pragma unroll
             for (int a = 0; a < 3; ++a)
