@@ -1,0 +1,243 @@
+// p2g_kernel.cuh -- the per-particle pieces of the P2G transfer (Eqs 1-5,
+// 13, 15-19) shared by the tile kernels of p2g.cu (block-interleaved phases)
+// and p2g_ordered.cu (ordered phases): cp.async staging of a particle, the
+// sum-factorised accumulation into a lane's padded 4 x 3 x 3 footprint, and
+// the slot of a lane's particle in a round.
+#pragma once
+#include "p2g.cuh"
+
+namespace polypic {
+
+
+template <int A> struct TileReg {
+    static constexpr int X = tile_x(A), Y = tile_y(A), Z = tile_z(A);
+};
+
+// 1-D factors of one axis: F[a][k] = W_k f_a(z_k) (z in cells), a < D.
+template <int D>
+__device__ __forceinline__ void axis_factors(const Stencil1D &s, float (&F)[D][3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) F[0][k] = s.W[k];
+    if constexpr (D > 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) F[1][k] = s.F1[k];
+    }
+    if constexpr (D > 2) {
+        F[2][0] = s.phi;
+        F[2][1] = -2.0f * s.phi;
+        F[2][2] = s.phi;
+    }
+}
+
+// Degrees (a, b, c) along (x, y, z) of the tensor entry (du, dv, dw) for the
+// component-A ordering u = A, (v, w) = the other two axes in increasing order.
+template <int A> __host__ __device__ constexpr int deg_x(int du, int dv, int dw) {
+    return A == 0 ? du : dv;
+}
+template <int A> __host__ __device__ constexpr int deg_y(int du, int dv, int dw) {
+    return A == 0 ? dv : (A == 1 ? du : dw);
+}
+template <int A> __host__ __device__ constexpr int deg_z(int du, int dv, int dw) {
+    return A == 2 ? du : dw;
+}
+
+// ---------------------------------------------------------------- staging
+// Each lane prefetches its next particles with cp.async (4-byte copies) into
+// a private multi-stage buffer laid out [stage][value][lane] (conflict-free):
+// x, y, z, m, m_abs, s_p, the particle index, then one 32-bit word per mode
+// (the coefficient, or for 16-bit formats the aligned word holding its code).
+template <int R> struct Stage {
+    static constexpr int kX = 0, kY = 1, kZ = 2, kM = 3, kMabs = 4, kScale = 5, kIdx = 6, kC = 7;
+    static constexpr int NV = kC + R;
+};
+
+__device__ __forceinline__ void cp_async4(float *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int R, int FMT, int A, bool ADJ>
+__device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, uint32_t slot,
+                                               float *st, int lane) {
+    using S = Stage<R>;
+    cp_async4(st + S::kX * 32 + lane, P.x + p);
+    cp_async4(st + S::kY * 32 + lane, P.y + p);
+    cp_async4(st + S::kZ * 32 + lane, P.z + p);
+    if constexpr (ADJ) {
+        // adjoint scatter: unit weight, coefficients mu (slot order) from scratch
+        st[S::kM * 32 + lane] = 1.0f;
+        const float *c = P.mu + (int64_t)A * R * P.count + slot;
+#pragma unroll
+        for (int r = 0; r < R; ++r, c += P.count) cp_async4(st + (S::kC + r) * 32 + lane, c);
+        return;
+    }
+    cp_async4(st + S::kM * 32 + lane, P.mass + p);
+    if (P.mass_abs) cp_async4(st + S::kMabs * 32 + lane, P.mass_abs + p);
+    reinterpret_cast<uint32_t *>(st)[S::kIdx * 32 + lane] = p;
+    if constexpr (FMT == POLYPIC_COEFF_F32) {
+        // row r of component A starts (A R + r) * count floats in
+        const float *c = reinterpret_cast<const float *>(P.coeff) + (int64_t)A * R * P.count + p;
+#pragma unroll
+        for (int r = 0; r < R; ++r, c += P.count) cp_async4(st + (S::kC + r) * 32 + lane, c);
+    } else {
+        cp_async4(st + S::kScale * 32 + lane, P.scale + p);
+        // byte offset of code (A R + r, p); its aligned 4-byte word holds it
+        const char *base = reinterpret_cast<const char *>(P.coeff);
+        int64_t b = 2 * ((int64_t)A * R * P.count + p);
+        const int64_t rstride = 2 * P.count;
+#pragma unroll
+        for (int r = 0; r < R; ++r, b += rstride) {
+            const int64_t w = b & ~(int64_t)3;
+            // only the array's last code can sit alone in a word at its end
+            if (A == 2 && r == R - 1 && w + 4 > (int64_t)6 * R * P.count) {
+                reinterpret_cast<uint32_t *>(st)[(S::kC + r) * 32 + lane] =
+                    *reinterpret_cast<const uint16_t *>(base + b);
+            } else {
+                cp_async4(st + (S::kC + r) * 32 + lane, base + w);
+            }
+        }
+    }
+}
+
+// One particle's contribution to the lane's padded footprint on grid A.
+// fu: stencil along A (face offset), fv / fw: the other two axes (centre).
+// Fit factors of the G2P least-squares fit in physical units (the adjoint
+// scatter): G0 = W, G1 = 4 F1 / dx, G2 = (1, -2, 1) / (2 dx^2), zero when guarded.
+template <int D>
+__device__ __forceinline__ void fit_rows(const Stencil1D &s, bool guard, float inv1, float inv2,
+                                         float (&G)[D][3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[0][k] = s.W[k];
+    if constexpr (D > 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G[1][k] = 4.0f * inv1 * s.F1[k];
+    }
+    if constexpr (D > 2) {
+        const float h = guard ? 0.0f : 0.5f * inv2;
+        G[2][0] = h;
+        G[2][1] = -2.0f * h;
+        G[2][2] = h;
+    }
+}
+
+template <int R, int FMT, int A, bool ADJ>
+__device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, int lane, float mt,
+                                           int shift, const Stencil1D &fu, const Stencil1D &fv,
+                                           const Stencil1D &fw, bool gu, bool gv, bool gw,
+                                           float (&am)[4][3][3], float (&av)[4][3][3]) {
+    using S = Stage<R>;
+    constexpr int D = axis_degrees(R);
+    const float cscale = FMT == POLYPIC_COEFF_F32 ? 1.0f : st[S::kScale * 32 + lane];
+    // 16-bit codes: element e = (A R + r) count + p sits in the high half of
+    // its aligned word when e is odd; (A R + r) is a compile-time constant.
+    const uint32_t podd = reinterpret_cast<const uint32_t *>(st)[S::kIdx * 32 + lane] & 1u;
+    const uint32_t par_even_row = podd, par_odd_row = podd ^ (uint32_t)(P.count & 1);
+    float Fu[D][3], Fv[D][3], Fw[D][3];
+    if constexpr (ADJ) {
+        fit_rows<D>(fu, gu, P.inv_dx, P.inv_dx2, Fu);
+        fit_rows<D>(fv, gv, P.inv_dx, P.inv_dx2, Fv);
+        fit_rows<D>(fw, gw, P.inv_dx, P.inv_dx2, Fw);
+    } else {
+        axis_factors<D>(fu, Fu);
+        axis_factors<D>(fv, Fv);
+        axis_factors<D>(fw, Fw);
+    }
+    // FP32 coefficients are physical: dx^a goes into the degree-a factor rows
+    if constexpr (!ADJ && FMT == POLYPIC_COEFF_F32 && D > 1) {
+#pragma unroll
+        for (int a = 1; a < D; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Fu[a][k] *= P.dxpow[a];
+                Fv[a][k] *= P.dxpow[a];
+                Fw[a][k] *= P.dxpow[a];
+            }
+    }
+    // mass weights first (padded along u: node d = k + shift)
+    if constexpr (!ADJ) {
+        const float w0 = mt * Fu[0][0], w1 = mt * Fu[0][1], w2 = mt * Fu[0][2];
+        const float Wm[4] = {shift ? 0.0f : w0, shift ? w0 : w1, shift ? w1 : w2, shift ? w2 : 0.0f};
+#pragma unroll
+        for (int kv = 0; kv < 3; ++kv)
+#pragma unroll
+            for (int kw = 0; kw < 3; ++kw) {
+                const float wvw = Fv[0][kv] * Fw[0][kw];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) am[d][kv][kw] = fmaf(Wm[d], wvw, am[d][kv][kw]);
+            }
+    }
+    // momentum, streamed over the degree du along u: contract w, then v, then
+    // u into the padded footprint (mass and the 16-bit scale s_p folded in)
+    const float mom_scale = FMT == POLYPIC_COEFF_F32 ? mt : mt * cscale;
+#pragma unroll
+    for (int du = 0; du < D; ++du) {
+        float C[D][D];
+#pragma unroll
+        for (int dv = 0; dv < D; ++dv)
+#pragma unroll
+            for (int dw = 0; dw < D; ++dw) {
+                const int a = deg_x<A>(du, dv, dw), b = deg_y<A>(du, dv, dw),
+                          c = deg_z<A>(du, dv, dw);
+                C[dv][dw] = 0.0f;
+                if (has_mode(R, a, b, c)) {
+                    const int r = mode_index(a, b, c);
+                    if constexpr (FMT == POLYPIC_COEFF_F32) {
+                        C[dv][dw] = st[(S::kC + r) * 32 + lane];
+                    } else {
+                        const uint32_t word =
+                            reinterpret_cast<const uint32_t *>(st)[(S::kC + r) * 32 + lane];
+                        const uint32_t odd = ((A * R + r) & 1) ? par_odd_row : par_even_row;
+                        C[dv][dw] = Codec<FMT>::decode((uint16_t)(word >> (odd << 4)));
+                    }
+                }
+            }
+        float T1[D][3];
+#pragma unroll
+        for (int dv = 0; dv < D; ++dv)
+#pragma unroll
+            for (int kw = 0; kw < 3; ++kw) {
+                float s = 0.0f;
+#pragma unroll
+                for (int dw = 0; dw < D; ++dw)
+                    if (has_mode(R, deg_x<A>(du, dv, dw), deg_y<A>(du, dv, dw), deg_z<A>(du, dv, dw)))
+                        s = fmaf(C[dv][dw], Fw[dw][kw], s);
+                T1[dv][kw] = s;
+            }
+        const float f0 = mom_scale * Fu[du][0], f1 = mom_scale * Fu[du][1],
+                    f2 = mom_scale * Fu[du][2];
+        const float Gu[4] = {shift ? 0.0f : f0, shift ? f0 : f1, shift ? f1 : f2, shift ? f2 : 0.0f};
+#pragma unroll
+        for (int kv = 0; kv < 3; ++kv)
+#pragma unroll
+            for (int kw = 0; kw < 3; ++kw) {
+                float t2 = 0.0f;
+#pragma unroll
+                for (int dv = 0; dv < D; ++dv) t2 = fmaf(T1[dv][kw], Fv[dv][kv], t2);
+#pragma unroll
+                for (int d = 0; d < 4; ++d) av[d][kv][kw] = fmaf(t2, Gu[d], av[d][kv][kw]);
+            }
+    }
+}
+
+// Slot of the lane's particle in round q (every lane must call it).
+__device__ __forceinline__ uint32_t round_slot(uint32_t bs, uint32_t n_c, uint32_t q,
+                                               unsigned lt) {
+    const uint32_t before = __reduce_add_sync(0xffffffffu, min(n_c, q));
+    const unsigned mask = __ballot_sync(0xffffffffu, n_c > q);
+    return bs + before + __popc(mask & lt);
+}
+
+// Rounds in flight per lane (cp.async groups).  Two measured fastest at 27
+// modes (four were 8% slower: the pipeline restarts for each component and
+// the prologue grows with the depth).
+#ifndef POLYPIC_P2G_STAGES
+#define POLYPIC_P2G_STAGES 2
+#endif
+constexpr int kStages = POLYPIC_P2G_STAGES;
+}  // namespace polypic
