@@ -35,8 +35,8 @@ size_t required_ws(const polypic_ctx *c, int64_t nf, int64_t ns) {
     size_t e = c->cfg.coeff_format == POLYPIC_COEFF_F32
                    ? adjoint_scratch_bytes(n, c->cfg.num_modes) + b + 256
                    : 0;
-    // the ordered step: its sort, advected positions and far list
-    size_t o = a + (size_t)n * 4 * sizeof(float) + 8 * 256;
+    // the ordered step: its sort and far list
+    size_t o = a + (size_t)n * sizeof(uint32_t) + 8 * 256;
     size_t m = a > b ? a : b;
     m = m > d ? m : d;
     m = m > e ? m : e;
@@ -470,7 +470,6 @@ polypic_status polypic_step_ordered(polypic_ctx *ctx, const polypic_particles *i
     Workspace W{static_cast<char *>(ws), ws_bytes, 0};
     SortScratch S;
     if (!take_sort_scratch(W, in->count, ctx->num_keys, S)) return POLYPIC_ERR_WORKSPACE;
-    float *xn = W.take<float>((size_t)in->count * 3);
     uint32_t *far = W.take<uint32_t>((size_t)in->count);
     uint32_t *num_far = W.take<uint32_t>(1);
     if (W.overflow) return POLYPIC_ERR_WORKSPACE;
@@ -479,10 +478,7 @@ polypic_status polypic_step_ordered(polypic_ctx *ctx, const polypic_particles *i
     A.g = ctx->geom;
     A.count = in->count;
     A.dt = params->dt;
-    for (int a = 0; a < 3; ++a) {
-        A.vel[a] = g->vel[a];
-        A.xn[a] = xn + (size_t)a * in->count;
-    }
+    for (int a = 0; a < 3; ++a) A.vel[a] = g->vel[a];
     A.x = in->x[0];
     A.y = in->x[1];
     A.z = in->x[2];
@@ -500,10 +496,8 @@ polypic_status polypic_step_ordered(polypic_ctx *ctx, const polypic_particles *i
     OrderedG2PArgs G{};
     G.g = ctx->geom;
     G.count = in->count;
-    for (int a = 0; a < 3; ++a) {
-        G.vel[a] = g->vel[a];
-        G.xn[a] = A.xn[a];
-    }
+    G.dt = params->dt;
+    for (int a = 0; a < 3; ++a) G.vel[a] = g->vel[a];
     G.x = in->x[0];
     G.y = in->x[1];
     G.z = in->x[2];

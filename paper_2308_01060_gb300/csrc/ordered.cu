@@ -13,7 +13,9 @@
 //   (sort)         finish_order() turns the counts into the next order;
 //   k_g2p_ordered  tile by tile in the NEXT order: gathers each particle's
 //                  old position, fits all modes there from a footprint staged
-//                  with a one-cell halo, writes every output contiguously;
+//                  with a one-cell halo, advects again with the velocity mode
+//                  (bit-identical to k_advect's: same arithmetic, same nodes),
+//                  writes every output contiguously;
 //   k_g2p_far      the particles that moved more than a cell out of their new
 //                  tile, fitted from the grid itself;
 //   k_gather       copies a phase into a given order (to order a phase once).
@@ -89,12 +91,7 @@ __global__ void __launch_bounds__(kG2PThreads) k_advect(AdvectArgs A) {
                     w2 = cell_coord(nz, g.inv_dx);
         const uint32_t k =
             cell_key(g, cell_index(w0, g.n[0]), cell_index(w1, g.n[1]), cell_index(w2, g.n[2]));
-        if (live) {
-            A.xn[0][j] = nx;
-            A.xn[1][j] = ny;
-            A.xn[2][j] = nz;
-            A.key[j] = k;
-        }
+        if (live) A.key[j] = k;
         // count with arrival rank, warp-aggregated
         const unsigned active = __ballot_sync(0xffffffffu, live);
         if (live) {
@@ -157,10 +154,11 @@ __device__ __forceinline__ void fit_from_grid(const GridGeom &g, const float *co
     }
 }
 
-// Outputs of slot j of the next order from the fit Chat (shared by the two
-// G2P kernels of ordered phases).
+// Outputs of slot j of the next order from the fit Chat at the old
+// position (px, py, pz) (shared by the two G2P kernels of ordered phases).
 template <int R, int FMT>
-__device__ __forceinline__ void write_slot(const OrderedG2PArgs &A, uint32_t j, uint32_t p, float m,
+__device__ __forceinline__ void write_slot(const OrderedG2PArgs &A, uint32_t j, uint32_t p,
+                                           bool ok, float px, float py, float pz, float m,
                                            float mabs, const float (&Chat)[3][R]) {
     using T = typename Codec<FMT>::T;
     const int64_t cnt = A.count;
@@ -183,10 +181,11 @@ __device__ __forceinline__ void write_slot(const OrderedG2PArgs &A, uint32_t j, 
             for (int r = 0; r < R; ++r, out += cnt) *out = Codec<FMT>::encode(Chat[a][r] * inv);
         A.oscale[j] = sc;
     }
-    // the advected position (computed once, by k_advect) and its key
-    A.ox[j] = A.xn[0][p];
-    A.oy[j] = A.xn[1][p];
-    A.oz[j] = A.xn[2][p];
+    // advection with the velocity mode, as k_advect did, and its key
+    const GridGeom &g = A.g;
+    A.ox[j] = ok ? fminf(fmaxf(fmaf(A.dt, Chat[0][0], px), g.lo[0]), g.hi[0]) : px;
+    A.oy[j] = ok ? fminf(fmaxf(fmaf(A.dt, Chat[1][0], py), g.lo[1]), g.hi[1]) : py;
+    A.oz[j] = ok ? fminf(fmaxf(fmaf(A.dt, Chat[2][0], pz), g.lo[2]), g.hi[2]) : pz;
     A.okey[j] = A.key_new[p];
     A.omass[j] = m;
     if (A.omass_abs) A.omass_abs[j] = mabs;
@@ -272,7 +271,7 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_ordered(OrderedG2PArgs A) {
             const bool finite =
                 isfinite(Chat[0][0]) && isfinite(Chat[1][0]) && isfinite(Chat[2][0]);
             if (!finite) atomicOr(A.status, kFlagNonFinite);
-            write_slot<R, FMT>(A, j, p, m, mabs, Chat);
+            write_slot<R, FMT>(A, j, p, ok, px, py, pz, m, mabs, Chat);
         }
         px = nx; py = ny; pz = nz; m = nm; mabs = nmabs; p = pn; pn = pnn;
     }
@@ -288,8 +287,9 @@ __global__ void __launch_bounds__(128) k_g2p_far(OrderedG2PArgs A) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nfar;
          i += gridDim.x * blockDim.x) {
         const uint32_t j = A.far[i], p = A.perm[j];
-        const float v0 = cell_coord(A.x[p], A.g.inv_dx), v1 = cell_coord(A.y[p], A.g.inv_dx),
-                    v2 = cell_coord(A.z[p], A.g.inv_dx);
+        const float px = A.x[p], py = A.y[p], pz = A.z[p];
+        const float v0 = cell_coord(px, A.g.inv_dx), v1 = cell_coord(py, A.g.inv_dx),
+                    v2 = cell_coord(pz, A.g.inv_dx);
         const Axis ac[3] = {axis_decide(v0, false), axis_decide(v1, false),
                             axis_decide(v2, false)};
         const Axis af[3] = {axis_decide(v0, true), axis_decide(v1, true), axis_decide(v2, true)};
@@ -297,7 +297,8 @@ __global__ void __launch_bounds__(128) k_g2p_far(OrderedG2PArgs A) {
         fit_from_grid<R>(A.g, A.vel, ac, af, inv1, inv2, Chat);
         const bool finite = isfinite(Chat[0][0]) && isfinite(Chat[1][0]) && isfinite(Chat[2][0]);
         if (!finite) atomicOr(A.status, kFlagNonFinite);
-        write_slot<R, FMT>(A, j, p, A.mass[p], A.mass_abs ? A.mass_abs[p] : 0.0f, Chat);
+        write_slot<R, FMT>(A, j, p, true, px, py, pz, A.mass[p],
+                           A.mass_abs ? A.mass_abs[p] : 0.0f, Chat);
     }
 }
 

@@ -17,7 +17,6 @@ struct AdvectArgs {
     const float *vel[3];
     const float *x, *y, *z;        // the ordered phase
     const uint32_t *cell_start;    // its cell starts
-    float *xn[3];                  // advected positions, in the phase's order
     uint32_t *key, *rank;          // key of each advected position and its arrival rank
     uint32_t *counts;              // per-key counts (zeroed by the caller)
     uint32_t *num_crowded;         // zeroed here for the sort that follows
@@ -27,15 +26,16 @@ struct AdvectArgs {
 cudaError_t advect(const AdvectArgs &A, int64_t num_tiles, cudaStream_t s);
 
 // G2P of an ordered phase into the next order: slot j of the output holds
-// input particle perm[j], fitted at its old position, with its advected
-// position xn and key.
+// input particle perm[j], fitted at its old position, advected again with
+// the velocity mode of that fit (the very value k_advect computed, from the
+// same arithmetic on the same nodes) and given the key k_advect sorted it by.
 struct OrderedG2PArgs {
     GridGeom g;
     int64_t count;
+    float dt;
     const float *vel[3];
     const float *x, *y, *z, *mass, *mass_abs;   // the input phase (old order)
-    const float *xn[3];                         // advected positions (old order)
-    const uint32_t *key_new;                    // their keys (old order)
+    const uint32_t *key_new;                    // keys of the advected positions (old order)
     const uint32_t *perm, *cell_start;          // the next order
     float *ox, *oy, *oz, *omass, *omass_abs;
     void *ocoeff;
