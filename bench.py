@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--variants", default="apic4,bf16,f16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     return ap.parse_args()
 
 
@@ -216,47 +216,60 @@ def run_variant(pp, torch, scene, R, fmt, steps, warmup, device):
             "phase_ms": (ph / steps).tolist(), "status": pp.STATUS_NAMES.get(st)}
 
 
-def run_e2e(pp, torch, scene, R, steps, device):
+def run_e2e(pp, torch, scene, R, steps, device, lanes=2):
     """Through the C ABI with host buffers: every step copies the particle
-    state in from pinned host memory and the new state back out."""
+    state in from pinned host memory, runs polypic_step, and copies the new
+    state back out.  Steps alternate between `lanes` streams, each with its
+    own device buffers, grid and workspace, so that one step's results stream
+    back while the next step's inputs stream in and compute; every step still
+    moves its full input and output across the host link inside the timed
+    region."""
     ctx = pp.Context(scene.n, scene.dx, R)
     f = scene.fluid
     P = f.n
-    dev_in, dev_out = make_state(pp, ctx, scene, device)
-    g = ctx.new_grid(device=device)
-    ws = ctx.workspace(P, device=device)
     prm = pp.UpdateSettings(dt=scene.dt)
     h_x = torch.from_numpy(f.x).pin_memory()
     h_m = torch.from_numpy(f.mass).pin_memory()
     h_c = torch.zeros((3, R, P), dtype=torch.float32).pin_memory()
-    h_xo = torch.empty((3, P), dtype=torch.float32).pin_memory()
-    h_co = torch.empty((3, R, P), dtype=torch.float32).pin_memory()
-    stream = torch.cuda.current_stream()
+    L = []
+    for _ in range(lanes):
+        dev_in, dev_out = make_state(pp, ctx, scene, device)
+        L.append({"s": torch.cuda.Stream(device=device), "in": dev_in, "out": dev_out,
+                  "g": ctx.new_grid(device=device), "ws": ctx.workspace(P, device=device),
+                  "xo": torch.empty((3, P), dtype=torch.float32).pin_memory(),
+                  "co": torch.empty((3, R, P), dtype=torch.float32).pin_memory()})
     h2d = (h_x.numel() + h_m.numel() + h_c.numel()) * 4
-    d2h = (h_xo.numel() + h_co.numel()) * 4
+    d2h = (L[0]["xo"].numel() + L[0]["co"].numel()) * 4
 
-    def step():
-        dev_in.x.copy_(h_x, non_blocking=True)
-        dev_in.mass.copy_(h_m, non_blocking=True)
-        dev_in.coeff.copy_(h_c, non_blocking=True)
-        pp.polypic_sort(ctx, dev_in, ws, stream)
-        pp.polypic_p2g(ctx, dev_in, g, ws, stream)
-        pp.polypic_grid_update(ctx, g, prm, stream=stream)
-        pp.polypic_g2p(ctx, g, dev_in, dev_out, scene.dt, ws, stream)
-        h_xo.copy_(dev_out.x, non_blocking=True)
-        h_co.copy_(dev_out.coeff, non_blocking=True)
+    def step(lane):
+        with torch.cuda.stream(lane["s"]):
+            lane["in"].x.copy_(h_x, non_blocking=True)
+            lane["in"].mass.copy_(h_m, non_blocking=True)
+            lane["in"].coeff.copy_(h_c, non_blocking=True)
+            pp.polypic_step(ctx, lane["in"], lane["out"], lane["g"], prm, lane["ws"],
+                            stream=lane["s"])
+            lane["xo"].copy_(lane["out"].x, non_blocking=True)
+            lane["co"].copy_(lane["out"].coeff, non_blocking=True)
 
-    step()
+    for lane in L:
+        step(lane)
     torch.cuda.synchronize()
+    main = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
-        step()
-    b.record(stream)
+    a.record(main)
+    for lane in L:
+        lane["s"].wait_event(a)
+    for k in range(steps):
+        step(L[k % lanes])
+    for lane in L:
+        main.wait_stream(lane["s"])
+    b.record(main)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
+    st = pp.polypic_check_device_status(ctx)
     return {"value": P / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "streams": lanes, "status": pp.STATUS_NAMES.get(st)}
 
 
 def cpu_baseline(scene, R, target_s=12.0):
