@@ -482,6 +482,7 @@ cudaError_t adjoint_g2p(const GridGeom &g, int64_t num_keys, int R, float dx,
     P.cell_start = in->cell_start;
     P.status = status;
     P.nblocks = (uint32_t)(num_keys / 32);
+    P.s1 = P.s2 = 1.0f;  // the scatter's fit rows carry their own 1/dx powers
     P.mu = mu;
     P.inv_dx = 1.0f / dx;
     P.inv_dx2 = 1.0f / (dx * dx);

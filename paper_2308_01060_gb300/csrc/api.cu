@@ -109,6 +109,10 @@ polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *
     P.status = c->d_status;
     P.nblocks = (uint32_t)(c->num_keys / 32);
     for (int l = 0; l < 7; ++l) P.dxpow[l] = (float)std::pow(c->cfg.dx, (double)l);
+    // FP32 coefficients are physical: the stencil's degree-1 and -2 factors carry dx, dx^2
+    const bool phys = c->cfg.coeff_format == POLYPIC_COEFF_F32;
+    P.s1 = phys ? P.dxpow[1] : 1.0f;
+    P.s2 = phys ? P.dxpow[2] : 1.0f;
     Workspace W{static_cast<char *>(ws), ws_bytes, 0};
     P.scratch = W.take<float>((size_t)(c->num_keys / 256) * kTileFloats);
     P.tile_live = W.take<uint8_t>((size_t)(c->num_keys / 256));
@@ -325,6 +329,9 @@ polypic_status polypic_p2g_noalloc(polypic_ctx *ctx, const polypic_particles *p,
     P.status = ctx->d_status;
     P.nblocks = (uint32_t)(ctx->num_keys / 32);
     for (int l = 0; l < 7; ++l) P.dxpow[l] = (float)std::pow(ctx->cfg.dx, (double)l);
+    const bool phys = ctx->cfg.coeff_format == POLYPIC_COEFF_F32;
+    P.s1 = phys ? P.dxpow[1] : 1.0f;
+    P.s2 = phys ? P.dxpow[2] : 1.0f;
     if (p2g_builtin_scratch(&P.scratch, &P.tile_live) != cudaSuccess) return POLYPIC_ERR_CUDA;
     return from_cuda(p2g(P, g->mass, g->mom, nullptr, 0.0f, nullptr, ctx->cfg.num_modes,
                          ctx->cfg.coeff_format, as_stream(stream)));

@@ -79,6 +79,8 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
                                          uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
                                          int gk, int lane, float *reg, float *stage, bool &bad) {
     using S = Stage<R>;
+    const bool interior = gi >= 1 && gi <= P.g.n[0] - 2 && gj >= 1 && gj <= P.g.n[1] - 2 &&
+                          gk >= 1 && gk <= P.g.n[2] - 2;
     float am[4][3][3], av[4][3][3];
 #pragma unroll
     for (int d = 0; d < 4; ++d)
@@ -97,9 +99,10 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
             if (!ADJ && P.mass_abs) mt += st[S::kMabs * 32 + lane];
             const float v0 = cell_coord(px, P.g.inv_dx), v1 = cell_coord(py, P.g.inv_dx),
                         v2 = cell_coord(pz, P.g.inv_dx);
-            const bool ok = coord_valid(v0, P.g.n[0]) && coord_valid(v1, P.g.n[1]) &&
-                            coord_valid(v2, P.g.n[2]) && (int)floorf(v0) == gi &&
-                            (int)floorf(v1) == gj && (int)floorf(v2) == gk;
+            // in an interior cell, being in the cell implies the valid region
+            const bool ok = (interior || (coord_valid(v0, P.g.n[0]) && coord_valid(v1, P.g.n[1]) &&
+                                          coord_valid(v2, P.g.n[2]))) &&
+                            (int)floorf(v0) == gi && (int)floorf(v1) == gj && (int)floorf(v2) == gk;
             if (ok) {
                 const float vu = A == 0 ? v0 : (A == 1 ? v1 : v2);
                 const float vv = A == 0 ? v1 : v0;
@@ -108,8 +111,8 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
                            aw = axis_decide(vw, false);
                 const int cu = A == 0 ? gi : (A == 1 ? gj : gk);
                 const int shift = au.base - (cu - 1);
-                accumulate<R, FMT, A, ADJ>(P, st, lane, mt, shift, stencil_1d(au.t),
-                                           stencil_1d(av_.t), stencil_1d(aw.t), au.guard,
+                accumulate<R, FMT, A, ADJ>(P, st, lane, mt, shift, stencil_1d_scaled(au.t, P.s1, P.s2),
+                                           stencil_1d_scaled(av_.t, P.s1, P.s2), stencil_1d_scaled(aw.t, P.s1, P.s2), au.guard,
                                            av_.guard, aw.guard, am, av);
             } else {
                 bad = true;

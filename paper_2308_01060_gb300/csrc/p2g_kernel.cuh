@@ -148,20 +148,27 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
         axis_factors<D>(fv, Fv);
         axis_factors<D>(fw, Fw);
     }
-    // FP32 coefficients are physical: dx^a goes into the degree-a factor rows
-    if constexpr (!ADJ && FMT == POLYPIC_COEFF_F32 && D > 1) {
+    // FP32 coefficients are physical: the caller's stencils carry dx^a in
+    // their degree-a factors.  The momentum weight (mass, and the 16-bit scale
+    // s_p) goes into the u factors once.
+    const float W0[3] = {Fu[0][0], Fu[0][1], Fu[0][2]};
+    const float mom_scale = FMT == POLYPIC_COEFF_F32 ? mt : mt * cscale;
 #pragma unroll
-        for (int a = 1; a < D; ++a)
+    for (int a = 0; a < D; ++a)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                Fu[a][k] *= P.dxpow[a];
-                Fv[a][k] *= P.dxpow[a];
-                Fw[a][k] *= P.dxpow[a];
-            }
-    }
+        for (int k = 0; k < 3; ++k) Fu[a][k] *= mom_scale;
     // mass weights first (padded along u: node d = k + shift)
     if constexpr (!ADJ) {
-        const float w0 = mt * Fu[0][0], w1 = mt * Fu[0][1], w2 = mt * Fu[0][2];
+        float w0, w1, w2;
+        if constexpr (FMT == POLYPIC_COEFF_F32) {
+            w0 = Fu[0][0];
+            w1 = Fu[0][1];
+            w2 = Fu[0][2];
+        } else {
+            w0 = mt * W0[0];
+            w1 = mt * W0[1];
+            w2 = mt * W0[2];
+        }
         const float Wm[4] = {shift ? 0.0f : w0, shift ? w0 : w1, shift ? w1 : w2, shift ? w2 : 0.0f};
 #pragma unroll
         for (int kv = 0; kv < 3; ++kv)
@@ -172,9 +179,9 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
                 for (int d = 0; d < 4; ++d) am[d][kv][kw] = fmaf(Wm[d], wvw, am[d][kv][kw]);
             }
     }
+    (void)W0;
     // momentum, streamed over the degree du along u: contract w, then v, then
-    // u into the padded footprint (mass and the 16-bit scale s_p folded in)
-    const float mom_scale = FMT == POLYPIC_COEFF_F32 ? mt : mt * cscale;
+    // u into the padded footprint
 #pragma unroll
     for (int du = 0; du < D; ++du) {
         float C[D][D];
@@ -209,8 +216,7 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
                         s = fmaf(C[dv][dw], Fw[dw][kw], s);
                 T1[dv][kw] = s;
             }
-        const float f0 = mom_scale * Fu[du][0], f1 = mom_scale * Fu[du][1],
-                    f2 = mom_scale * Fu[du][2];
+        const float f0 = Fu[du][0], f1 = Fu[du][1], f2 = Fu[du][2];
         const float Gu[4] = {shift ? 0.0f : f0, shift ? f0 : f1, shift ? f1 : f2, shift ? f2 : 0.0f};
 #pragma unroll
         for (int kv = 0; kv < 3; ++kv)

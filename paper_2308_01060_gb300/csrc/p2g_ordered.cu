@@ -95,8 +95,8 @@ __device__ __forceinline__ void opass(const P2GArgs &P, OPipe &q, uint32_t gs, u
                            aw = axis_decide(vw, false);
                 const int cu = A == 0 ? gi : (A == 1 ? gj : gk);
                 const int shift = au.base - (cu - 1);
-                accumulate<R, FMT, A, false>(P, st, lane, mt, shift, stencil_1d(au.t),
-                                             stencil_1d(av_.t), stencil_1d(aw.t), au.guard,
+                accumulate<R, FMT, A, false>(P, st, lane, mt, shift, stencil_1d_scaled(au.t, P.s1, P.s2),
+                                             stencil_1d_scaled(av_.t, P.s1, P.s2), stencil_1d_scaled(aw.t, P.s1, P.s2), au.guard,
                                              av_.guard, aw.guard, am, av);
             } else {
                 bad = true;

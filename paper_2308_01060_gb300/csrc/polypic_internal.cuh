@@ -134,6 +134,23 @@ __device__ __forceinline__ Stencil1D stencil_1d(float t) {
     return s;
 }
 
+// The same factors with F1 and phi multiplied by s1 and s2 (s1 = dx and
+// s2 = dx^2 turn them into physical units for FP32 coefficients), F1 formed
+// as its definition W_k z_k with z = (-1 - t, -t, 1 - t) in cells.
+__device__ __forceinline__ Stencil1D stencil_1d_scaled(float t, float s1, float s2) {
+    Stencil1D s;
+    float a = 0.5f - t, b = 0.5f + t;
+    s.W[0] = 0.5f * a * a;
+    s.W[1] = 0.75f - t * t;
+    s.W[2] = 0.5f * b * b;
+    s.F1[0] = s.W[0] * fmaf(-t, s1, -s1);
+    s.F1[1] = s.W[1] * (-t * s1);
+    s.F1[2] = s.W[2] * fmaf(-t, s1, s1);
+    float q = (1.0f - 2.0f * t) * (1.0f + 2.0f * t);
+    s.phi = q * q * (3.0f - 4.0f * t * t) * (s2 * (1.0f / 32.0f));
+    return s;
+}
+
 // ---------------------------------------------------------------- modes
 // Canonical mode index of the per-axis degrees (a, b, c), or -1.
 __host__ __device__ constexpr int mode_index(int a, int b, int c) {
