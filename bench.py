@@ -127,11 +127,11 @@ class ClockSampler:
 # ---------------------------------------------------------------- workload
 
 # DRAM bytes (read + write) per particle of one k_p2g_tiles<27, FP32> launch,
-# from a full ncu capture on the 96^3 dam break (1,557,376 particles: 537.3 MB
-# read, 13.6 MB written); P2G traffic grows in proportion to the particles, so
+# from a full ncu capture on the 96^3 dam break (1,557,376 particles: 537.2 MB
+# read, 13.8 MB written); P2G traffic grows in proportion to the particles, so
 # it scales to the 128^3 launch.  It must go back to None whenever the kernel
 # changes after that capture.
-P2G_TILES_DRAM_BYTES_PER_PARTICLE = (537.332224e6 + 13.564928e6) / 1557376
+P2G_TILES_DRAM_BYTES_PER_PARTICLE = (537.172736e6 + 13.766912e6) / 1557376
 
 
 def algorithmic_bytes(R: int, fmt: str):
