@@ -15,6 +15,8 @@
 // so comes out in physical units; the 16-bit formats fit c dx^L, divide by the
 // per-particle scale s_p = max |c dx^L| and round to nearest even.  Outputs
 // are written in sorted slot order (coalesced).
+#include <type_traits>
+
 #include "g2p.cuh"
 #include "g2p_fit.cuh"
 
@@ -70,43 +72,58 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
                   ck = cell_index(v2, g.n[2]) - 4 * tz;
         ok = ok && ci >= 0 && ci < 8 && cj >= 0 && cj < 8 && ck >= 0 && ck < 4;
 
-        float Chat[3][R];
-        if (ok) {
-            const Axis ac0 = axis_decide(v0, false), af0 = axis_decide(v0, true);
-            const Axis ac1 = axis_decide(v1, false), af1 = axis_decide(v1, true);
-            const Axis ac2 = axis_decide(v2, false), af2 = axis_decide(v2, true);
-            const Stencil1D sc0 = stencil_1d(ac0.t), sf0 = stencil_1d(af0.t);
-            const Stencil1D sc1 = stencil_1d(ac1.t), sf1 = stencil_1d(af1.t);
-            const Stencil1D sc2 = stencil_1d(ac2.t), sf2 = stencil_1d(af2.t);
-            g2p_component<R, 0, Tile<0>::X, Tile<0>::Y>(s_tile, af0.base - ox, ac1.base - oy,
-                                                        ac2.base - oz, sf0, af0.guard, sc1,
-                                                        ac1.guard, sc2, ac2.guard, inv1, inv2,
-                                                        Chat[0]);
-            g2p_component<R, 1, Tile<1>::X, Tile<1>::Y>(s_tile + kVelTileOff1, ac0.base - ox,
-                                                        af1.base - oy, ac2.base - oz, sc0,
-                                                        ac0.guard, sf1, af1.guard, sc2,
-                                                        ac2.guard, inv1, inv2, Chat[1]);
-            g2p_component<R, 2, Tile<2>::X, Tile<2>::Y>(s_tile + kVelTileOff2, ac0.base - ox,
-                                                        ac1.base - oy, af2.base - oz, sc0,
-                                                        ac0.guard, sc1, ac1.guard, sf2,
-                                                        af2.guard, inv1, inv2, Chat[2]);
-        } else {
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int r = 0; r < R; ++r) Chat[a][r] = 0.0f;
-        }
         if (!ok) atomicOr(A.status, kFlagOutOfDomain);
-        const bool finite = isfinite(Chat[0][0]) && isfinite(Chat[1][0]) && isfinite(Chat[2][0]);
-        if (!finite) atomicOr(A.status, kFlagNonFinite);
-
+        Axis ac0{}, af0{}, ac1{}, af1{}, ac2{}, af2{};
+        Stencil1D sc0{}, sf0{}, sc1{}, sf1{}, sc2{}, sf2{};
+        if (ok) {
+            ac0 = axis_decide(v0, false); af0 = axis_decide(v0, true);
+            ac1 = axis_decide(v1, false); af1 = axis_decide(v1, true);
+            ac2 = axis_decide(v2, false); af2 = axis_decide(v2, true);
+            sc0 = stencil_1d(ac0.t); sf0 = stencil_1d(af0.t);
+            sc1 = stencil_1d(ac1.t); sf1 = stencil_1d(af1.t);
+            sc2 = stencil_1d(ac2.t); sf2 = stencil_1d(af2.t);
+        }
+        // fit of component a (zero for a particle outside its tile)
+        auto fit = [&](auto acomp, float (&C)[R]) {
+            constexpr int a = decltype(acomp)::value;
+            if (ok) {
+                if constexpr (a == 0)
+                    g2p_component<R, 0, Tile<0>::X, Tile<0>::Y>(
+                        s_tile, af0.base - ox, ac1.base - oy, ac2.base - oz, sf0, af0.guard, sc1,
+                        ac1.guard, sc2, ac2.guard, inv1, inv2, C);
+                else if constexpr (a == 1)
+                    g2p_component<R, 1, Tile<1>::X, Tile<1>::Y>(
+                        s_tile + kVelTileOff1, ac0.base - ox, af1.base - oy, ac2.base - oz, sc0,
+                        ac0.guard, sf1, af1.guard, sc2, ac2.guard, inv1, inv2, C);
+                else
+                    g2p_component<R, 2, Tile<2>::X, Tile<2>::Y>(
+                        s_tile + kVelTileOff2, ac0.base - ox, ac1.base - oy, af2.base - oz, sc0,
+                        ac0.guard, sc1, ac1.guard, sf2, af2.guard, inv1, inv2, C);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) C[r] = 0.0f;
+            }
+        };
+        float vel[3];
         T *out = ocoeff + j;  // row (a, r) starts (a R + r) * cnt elements in
         if constexpr (FMT == POLYPIC_COEFF_F32) {
+            // each component's coefficients leave as soon as they are fitted,
+            // spreading the stores over the particle's arithmetic
+            auto fit_store = [&](auto acomp) {
+                float C[R];
+                fit(acomp, C);
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int r = 0; r < R; ++r, out += cnt) *out = Chat[a][r];
+                for (int r = 0; r < R; ++r, out += cnt) *out = C[r];
+                vel[decltype(acomp)::value] = C[0];
+            };
+            fit_store(std::integral_constant<int, 0>{});
+            fit_store(std::integral_constant<int, 1>{});
+            fit_store(std::integral_constant<int, 2>{});
         } else {
+            float Chat[3][R];
+            fit(std::integral_constant<int, 0>{}, Chat[0]);
+            fit(std::integral_constant<int, 1>{}, Chat[1]);
+            fit(std::integral_constant<int, 2>{}, Chat[2]);
             float s = 0.0f;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -118,10 +135,13 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
 #pragma unroll
                 for (int r = 0; r < R; ++r, out += cnt) *out = Codec<FMT>::encode(Chat[a][r] * inv);
             A.oscale[j] = s;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) vel[a] = Chat[a][0];
         }
+        const bool finite = isfinite(vel[0]) && isfinite(vel[1]) && isfinite(vel[2]);
+        if (!finite) atomicOr(A.status, kFlagNonFinite);
         // advection with the fitted velocity (unquantised)
-        const float vx = ok ? Chat[0][0] : 0.0f, vy = ok ? Chat[1][0] : 0.0f,
-                    vz = ok ? Chat[2][0] : 0.0f;
+        const float vx = ok ? vel[0] : 0.0f, vy = ok ? vel[1] : 0.0f, vz = ok ? vel[2] : 0.0f;
         A.ox[j] = ok ? fminf(fmaxf(fmaf(A.dt, vx, px), g.lo[0]), g.hi[0]) : px;
         A.oy[j] = ok ? fminf(fmaxf(fmaf(A.dt, vy, py), g.lo[1]), g.hi[1]) : py;
         A.oz[j] = ok ? fminf(fmaxf(fmaf(A.dt, vz, pz), g.lo[2]), g.hi[2]) : pz;
