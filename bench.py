@@ -149,8 +149,9 @@ def launches_per_step() -> int:
     """Kernels of ours per polypic_step (one phase, no projection): keys with
     arrival ranks, the 3-kernel count scan, the scatter, the per-cell order,
     the crowded-cell pass (exits at once when no cell holds more than 64
-    particles), P2G tiles + 3 reductions with the grid update fused in, G2P."""
-    return 1 + 3 + 1 + 1 + 1 + 4 + 1
+    particles), P2G tiles + the tile reduction with the grid update fused in,
+    G2P."""
+    return 1 + 3 + 1 + 1 + 1 + 2 + 1
 
 
 def make_state(pp, ctx, scene, device):
@@ -385,7 +386,7 @@ def our_arm(args):
         "traffic": (round(P * P2G_TILES_DRAM_BYTES_PER_PARTICLE / 1e9, 4)
                     if dominant == "p2g" and P2G_TILES_DRAM_BYTES_PER_PARTICLE else None),
         "traffic_unit": "GB per launch (k_p2g_tiles only, scaled from the 96^3 capture)",
-        "kernel": "polypic_p2g call (k_p2g_tiles + 3 x k_p2g_reduce)" if dominant == "p2g"
+        "kernel": "polypic_p2g call (k_p2g_tiles + k_p2g_reduce)" if dominant == "p2g"
         else "polypic_g2p (k_g2p_tiles)",
         "algorithmic_bytes_per_particle": p2g_b if dominant == "p2g" else g2p_b,
         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"

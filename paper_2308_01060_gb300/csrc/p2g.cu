@@ -19,8 +19,9 @@
 //     block region in 36 phases (one node offset per phase: distinct cells
 //     hit distinct nodes), then the CTA adds its 8 block regions into the
 //     tile region in ascending block order and writes it to scratch;
-//   * k_p2g_reduce sums the at most 8 tile regions covering each face node in
-//     ascending tile order and writes the grids.
+//   * k_p2g_reduce (one CTA per tile, the nodes it owns on the three face
+//     grids) sums the at most 8 tile regions covering each node in ascending
+//     tile order and writes the grids.
 #include <mutex>
 
 #include "p2g_kernel.cuh"
@@ -248,49 +249,109 @@ static cudaError_t launch_tiles(const P2GArgs &P, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Sum of the tile regions covering each node of face grid A, in ascending
-// tile order; tiles without particles wrote nothing and are skipped.  With
-// `fuse` set it also applies the single-phase grid update (v = mv/m, + dt g,
-// walls) and writes the velocity.  Launch: x over the x nodes, y over j, z
-// over k (grid-stride on y and z).
+// Sum over the (at most 8) tile regions covering node (i, j, k) of face grid
+// A, in ascending tile order (z, then y, then x); tiles without particles
+// wrote nothing and count as 0.  All candidate values are loaded before the
+// ordered sum, so a thread has up to 16 loads in flight.  With gv non-NULL it
+// also applies the single-phase grid update (v = mv/m, + dt g, walls).
 template <int A>
-__global__ void __launch_bounds__(128) k_p2g_reduce(GridGeom g, const uint8_t *__restrict__ live,
-                                                    const float *__restrict__ scratch,
-                                                    float *__restrict__ gm, float *__restrict__ gp,
-                                                    float *__restrict__ gv, float dt, float ga,
-                                                    bool accumulate) {
-    const int dX = g.n[0] + (A == 0), dY = g.n[1] + (A == 1), dZ = g.n[2] + (A == 2);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= dX) return;
-    const int tx0 = max(0, (i + 2 - TileReg<A>::X + 7) >> 3), tx1 = min(g.tiles[0] - 1, (i + 1) >> 3);
-    for (int k = blockIdx.z; k < dZ; k += gridDim.z) {
-        const int tz0 = max(0, (k + 2 - TileReg<A>::Z + 3) >> 2), tz1 = min(g.tiles[2] - 1, (k + 1) >> 2);
-        for (int j = blockIdx.y; j < dY; j += gridDim.y) {
-            const int ty0 = max(0, (j + 2 - TileReg<A>::Y + 7) >> 3),
-                      ty1 = min(g.tiles[1] - 1, (j + 1) >> 3);
-            float sm = 0.0f, sv = 0.0f;
-            for (int tz = tz0; tz <= tz1; ++tz)
-                for (int ty = ty0; ty <= ty1; ++ty)
-                    for (int tx = tx0; tx <= tx1; ++tx) {
-                        const uint32_t t = ((uint32_t)tz * g.tiles[1] + ty) * g.tiles[0] + tx;
-                        if (!live[t]) continue;
-                        const int lx = i - (8 * tx - 1), ly = j - (8 * ty - 1), lz = k - (4 * tz - 1);
-                        const int r = (lz * TileReg<A>::Y + ly) * TileReg<A>::X + lx;
-                        const float *src = scratch + (size_t)t * kTileFloats;
-                        sm += src[tile_off(A, 0) + r];
-                        sv += src[tile_off(A, 1) + r];
-                    }
-            const int64_t idx = ((int64_t)k * dY + j) * dX + i;
-            if (gm) gm[idx] = sm;
-            gp[idx] = accumulate ? gp[idx] + sv : sv;
-            if (gv) {
-                const int ia = A == 0 ? i : (A == 1 ? j : k);
-                float v = sm > 0.0f ? sv / sm : 0.0f;
-                v = fmaf(dt, ga, v);
-                gv[idx] = (ia == 0 || ia == g.n[A]) ? 0.0f : v;
-            }
+__device__ __forceinline__ void reduce_node(const GridGeom &g, const uint8_t *s_live, int ux,
+                                            int uy, int uz, int i, int j, int k,
+                                            const float *__restrict__ scratch,
+                                            float *__restrict__ gm, float *__restrict__ gp,
+                                            float *__restrict__ gv, float dt, float ga,
+                                            bool accumulate) {
+    constexpr int X = tile_x(A), Y = tile_y(A), Z = tile_z(A);
+    const int tx0 = max(0, (i + 2 - X + 7) >> 3), tx1 = min(g.tiles[0] - 1, (i + 1) >> 3);
+    const int ty0 = max(0, (j + 2 - Y + 7) >> 3), ty1 = min(g.tiles[1] - 1, (j + 1) >> 3);
+    const int tz0 = max(0, (k + 2 - Z + 3) >> 2), tz1 = min(g.tiles[2] - 1, (k + 1) >> 2);
+    float m[8], v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int tz = tz0 + (c >> 2), ty = ty0 + ((c >> 1) & 1), tx = tx0 + (c & 1);
+        const bool use = tz <= tz1 && ty <= ty1 && tx <= tx1 &&
+                         s_live[((tz - uz + 1) * 3 + (ty - uy + 1)) * 3 + (tx - ux + 1)];
+        m[c] = v[c] = 0.0f;
+        if (use) {
+            const uint32_t t = ((uint32_t)tz * g.tiles[1] + ty) * g.tiles[0] + tx;
+            const int r = ((k - 4 * tz + 1) * Y + (j - 8 * ty + 1)) * X + (i - 8 * tx + 1);
+            const float *src = scratch + (size_t)t * kTileFloats + r;
+            m[c] = __ldg(src + tile_off(A, 0));
+            v[c] = __ldg(src + tile_off(A, 1));
         }
     }
+    // +0 starts the sum, so it is never -0 and the zeros of unused slots
+    // leave it unchanged: the same bits as summing the used tiles alone
+    float sm = 0.0f, sv = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        sm += m[c];
+        sv += v[c];
+    }
+    const int dX = g.n[0] + (A == 0), dY = g.n[1] + (A == 1);
+    const int64_t idx = ((int64_t)k * dY + j) * dX + i;
+    if (gm) gm[idx] = sm;
+    gp[idx] = accumulate ? gp[idx] + sv : sv;
+    if (gv) {
+        const int ia = A == 0 ? i : (A == 1 ? j : k);
+        float vel = sm > 0.0f ? sv / sm : 0.0f;
+        vel = fmaf(dt, ga, vel);
+        gv[idx] = (ia == 0 || ia == g.n[A]) ? 0.0f : vel;
+    }
+}
+
+// One CTA per key tile writes the nodes the tile owns on all three face
+// grids: [8tx, 8tx + 8) x [8ty, 8ty + 8) x [4tz, 4tz + 4), the last tile
+// along axis A also the wall layer n[A] of face grid A.  Thread (lx, ly, lz)
+// takes one owned node per face; the owned nodes only draw on the 27 tiles
+// around this one, whose live flags are staged first.
+struct ReduceOut {
+    float *gm[3], *gp[3], *gv[3];
+    float ga[3];
+};
+
+__global__ void __launch_bounds__(256) k_p2g_reduce(GridGeom g, const uint8_t *__restrict__ live,
+                                                    const float *__restrict__ scratch,
+                                                    ReduceOut O, float dt, bool accumulate) {
+    __shared__ uint8_t s_live[27];
+    const uint32_t tile = blockIdx.x;
+    const int ux = (int)(tile % (uint32_t)g.tiles[0]);
+    const int uy = (int)((tile / (uint32_t)g.tiles[0]) % (uint32_t)g.tiles[1]);
+    const int uz = (int)(tile / ((uint32_t)g.tiles[0] * (uint32_t)g.tiles[1]));
+    const int t = threadIdx.x;
+    if (t < 27) {
+        const int vz = uz + t / 9 - 1, vy = uy + (t / 3) % 3 - 1, vx = ux + t % 3 - 1;
+        const bool in = vx >= 0 && vx < g.tiles[0] && vy >= 0 && vy < g.tiles[1] && vz >= 0 &&
+                        vz < g.tiles[2];
+        s_live[t] = in ? live[((uint32_t)vz * g.tiles[1] + vy) * g.tiles[0] + vx] : 0;
+    }
+    __syncthreads();
+    const int i = 8 * ux + (t & 7), j = 8 * uy + ((t >> 3) & 7), k = 4 * uz + (t >> 6);
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    // a tile at the grid's upper edge may extend past the cells (n not a
+    // multiple of the tile): nodes beyond the face grid are not written
+    if (i < nx + 1 && j < ny && k < nz)
+        reduce_node<0>(g, s_live, ux, uy, uz, i, j, k, scratch, O.gm[0], O.gp[0], O.gv[0], dt,
+                       O.ga[0], accumulate);
+    if (i < nx && j < ny + 1 && k < nz)
+        reduce_node<1>(g, s_live, ux, uy, uz, i, j, k, scratch, O.gm[1], O.gp[1], O.gv[1], dt,
+                       O.ga[1], accumulate);
+    if (i < nx && j < ny && k < nz + 1)
+        reduce_node<2>(g, s_live, ux, uy, uz, i, j, k, scratch, O.gm[2], O.gp[2], O.gv[2], dt,
+                       O.ga[2], accumulate);
+    // the wall layer n[A] lies one past the last tile when the tile size
+    // divides n[A]: 8 x 4, 8 x 4 and 8 x 8 more nodes
+    const int i8 = 8 * ux + (t & 7), j8 = 8 * uy + (t & 7);   // t < 32: 8 x 4
+    const int k4 = 4 * uz + (t >> 3), j64 = 8 * uy + (t >> 3);  // t < 64: 8 x 8
+    if (ux == g.tiles[0] - 1 && 8 * g.tiles[0] == nx && t < 32 && j8 < ny && k4 < nz)
+        reduce_node<0>(g, s_live, ux, uy, uz, nx, j8, k4, scratch, O.gm[0], O.gp[0], O.gv[0],
+                       dt, O.ga[0], accumulate);
+    if (uy == g.tiles[1] - 1 && 8 * g.tiles[1] == ny && t < 32 && i8 < nx && k4 < nz)
+        reduce_node<1>(g, s_live, ux, uy, uz, i8, ny, k4, scratch, O.gm[1], O.gp[1], O.gv[1], dt,
+                       O.ga[1], accumulate);
+    if (uz == g.tiles[2] - 1 && 4 * g.tiles[2] == nz && t < 64 && i8 < nx && j64 < ny)
+        reduce_node<2>(g, s_live, ux, uy, uz, i8, j64, nz, scratch, O.gm[2], O.gp[2], O.gv[2], dt,
+                       O.ga[2], accumulate);
 }
 
 // ---------------------------------------------------------------- built-in scratch
@@ -336,17 +397,15 @@ size_t p2g_scratch_bytes(int64_t num_keys) {
 
 static cudaError_t reduce_tiles(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3],
                                 float dt, const float gravity[3], bool accumulate, cudaStream_t s) {
-    const GridGeom &g = P.g;
-    auto launch = [&](auto kern, int a) {
-        const int dX = g.n[0] + (a == 0), dY = g.n[1] + (a == 1), dZ = g.n[2] + (a == 2);
-        dim3 grid((dX + 127) / 128, dY < 1024 ? dY : 1024, dZ < 64 ? dZ : 64);
-        kern<<<grid, 128, 0, s>>>(g, P.tile_live, P.scratch, gm ? gm[a] : nullptr, gp[a],
-                                 gv ? gv[a] : nullptr, dt, gravity ? gravity[a] : 0.0f,
-                                 accumulate);
-    };
-    launch(k_p2g_reduce<0>, 0);
-    launch(k_p2g_reduce<1>, 1);
-    launch(k_p2g_reduce<2>, 2);
+    ReduceOut O;
+    for (int a = 0; a < 3; ++a) {
+        O.gm[a] = gm ? gm[a] : nullptr;
+        O.gp[a] = gp[a];
+        O.gv[a] = gv ? gv[a] : nullptr;
+        O.ga[a] = gravity ? gravity[a] : 0.0f;
+    }
+    const int ntiles = (int)(P.nblocks / kP2GWarps);
+    k_p2g_reduce<<<ntiles, 256, 0, s>>>(P.g, P.tile_live, P.scratch, O, dt, accumulate);
     return cudaGetLastError();
 }
 
