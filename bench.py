@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--rows", default="coupled,update,projection,adjoint",
+                    help="the other rows of the path, each timed on its own workload")
     return ap.parse_args()
 
 
@@ -215,6 +217,177 @@ def run_variant(pp, torch, scene, R, fmt, steps, warmup, device):
     st = pp.polypic_check_device_status(ctx)
     return {"ctx": ctx, "count": src.count, "total_ms": total_ms,
             "phase_ms": (ph / steps).tolist(), "status": pp.STATUS_NAMES.get(st)}
+
+
+class L2Flush:
+    """Writes a 256 MB buffer (twice the 129 MB L2) before each timed call of
+    a workload whose data would otherwise stay in L2 between calls."""
+
+    def __init__(self, torch, device):
+        self.buf = torch.empty(64 << 20, dtype=torch.float32, device=device)
+
+    def __call__(self):
+        self.buf.fill_(1.0)
+
+
+def time_calls(torch, fn, iters, flush, stream):
+    """Median device time (ms) of `iters` calls of fn, each bracketed by CUDA
+    events on `stream` after an L2 flush (not timed)."""
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    evs = []
+    for _ in range(iters):
+        flush()
+        a, b = E(), E()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+
+def face_nodes(n):
+    return sum((n[0] + (a == 0)) * (n[1] + (a == 1)) * (n[2] + (a == 2)) for a in range(3))
+
+
+def run_rows(pp, torch, scenes, device, hbm, which, iters=10, warmup=3):
+    """The rows of the path outside the headline step, each on the workload
+    it is defined on: the coupled fluid + fabric step (splash scene, 128^3),
+    the grid update and the pressure projection (dam break, 128^3), and the
+    three adjoints (random-velocity half box, 64^3, 27 modes).  Each figure is
+    the median of `iters` calls with L2 flushed before each."""
+    stream = torch.cuda.current_stream()
+    flush = L2Flush(torch, device)
+    rows = {}
+
+    def gbs(nbytes, ms):
+        v = nbytes / (ms * 1e-3) / 1e9
+        return {"achieved_gbs": round(v, 1), "frac_of_peak": round(v / hbm, 4),
+                "algorithmic_bytes": int(nbytes)}
+
+    if "coupled" in which:
+        sc = scenes.splash_scene(n=128, R_fluid=27, R_solid=27)
+        ctx = pp.Context(sc.n, sc.dx, 27)
+        fi = pp.upload_particles(ctx, sc.fluid.x, sc.fluid.mass, sc.fluid.coeff, device=device)
+        si = pp.upload_particles(ctx, sc.solid.x, sc.solid.mass, None,
+                                 mass_abs=sc.solid.mass_abs, device=device)
+        fo = ctx.new_particles(fi.count, device=device)
+        so = ctx.new_particles(si.count, solid=True, device=device)
+        gf, gs = ctx.new_grid(device=device), ctx.new_grid(device=device)
+        ws = ctx.workspace(fi.count, si.count, device=device)
+        prm = pp.UpdateSettings(dt=sc.dt, drag_k=5.0)
+        st = {"f": (fi, fo), "s": (si, so)}
+
+        def step():
+            (a, b), (c, d) = st["f"], st["s"]
+            pp.polypic_step(ctx, a, b, gf, prm, ws, solid_in=c, solid_out=d, gs=gs,
+                            stream=stream)
+            st["f"], st["s"] = (b, a), (d, c)
+        for _ in range(warmup):
+            step()
+        ms = time_calls(torch, step, iters, flush, stream)
+        npart = fi.count + si.count
+        p2g_b, g2p_b = algorithmic_bytes(27, "f32")
+        nbytes = fi.count * (p2g_b + g2p_b) + si.count * (p2g_b + 4 + g2p_b + 4)
+        rows["A2_coupled_step"] = {
+            "workload": f"splash 128^3: fluid sphere {fi.count} + sheet {si.count} particles, "
+                        "27 modes FP32, drag K 5", "ms": round(ms, 4),
+            "value": round(npart / (ms * 1e-3) / 1e6, 1), "unit": UNIT,
+            **gbs(nbytes, ms),
+            "bytes_note": "P2G+G2P algorithmic bytes of both phases over the whole step "
+                          "(sort, two P2G, drag update, two G2P)",
+            "status": pp.STATUS_NAMES.get(pp.polypic_check_device_status(ctx))}
+        del ctx, fi, si, fo, so, gf, gs, ws
+
+    if "update" in which or "projection" in which:
+        sc = scenes.dam_break_scene(n=128, R=27)
+        ctx = pp.Context(sc.n, sc.dx, 27)
+        a = pp.upload_particles(ctx, sc.fluid.x, sc.fluid.mass, None, device=device)
+        b = ctx.new_particles(a.count, device=device)
+        g = ctx.new_grid(device=device)
+        ws = ctx.workspace(a.count, device=device)
+        prm = pp.UpdateSettings(dt=sc.dt)
+        for _ in range(10):
+            pp.polypic_step(ctx, a, b, g, prm, ws, stream=stream)
+            a, b = b, a
+        pp.polypic_sort(ctx, a, ws, stream)
+        pp.polypic_p2g(ctx, a, g, ws, stream)
+        upd = lambda: pp.polypic_grid_update(ctx, g, prm, stream=stream)
+        for _ in range(warmup):
+            upd()
+        ms_u = time_calls(torch, upd, iters, flush, stream)
+        nodes = face_nodes(sc.n)
+        if "update" in which:
+            rows["A3_grid_update"] = {
+                "workload": "dam break 128^3 after 10 steps, 3 face grids", "ms": round(ms_u, 4),
+                "face_nodes": nodes, **gbs(12 * nodes, ms_u),
+                "bytes_note": "12 B per face node: m and mv read, v written"}
+        if "projection" in which:
+            prj = pp.UpdateSettings(dt=sc.dt, project=True, pcg_maxiter=2000)
+            pr = lambda: pp.polypic_grid_update(ctx, g, prj, fluid_particles=a, ws=ws,
+                                                stream=stream)
+            pr()
+            ms_p = time_calls(torch, pr, 3, flush, stream)
+            rows["A4_projection"] = {
+                "workload": "dam break 128^3 after 10 steps: 64x128x64 fluid cells, "
+                            "Jacobi-PCG rtol 1e-6, at most 2000 iterations",
+                "ms_update_and_projection": round(ms_p, 3),
+                "ms_projection": round(ms_p - ms_u, 3),
+                "note": "not in the headline step; the host reads the residual every 8 "
+                        "iterations",
+                "status": pp.STATUS_NAMES.get(pp.polypic_check_device_status(ctx))}
+        del ctx, a, b, g, ws
+
+    if "adjoint" in which:
+        R = 27
+        sc = scenes.random_velocity_scene(n=64, R=R, seed=0, sigma_v=0.3, dt=1e-3)
+        ctx = pp.Context(sc.n, sc.dx, R)
+        ps = pp.upload_particles(ctx, sc.fluid.x, sc.fluid.mass, sc.fluid.coeff, device=device)
+        ws = ctx.workspace(ps.count, device=device)
+        g = ctx.new_grid(device=device)
+        prm = pp.UpdateSettings(dt=sc.dt)
+        pp.polypic_sort(ctx, ps, ws, stream)
+        pp.polypic_p2g(ctx, ps, g, ws, stream)
+        pp.polypic_grid_update(ctx, g, prm, stream=stream)
+        gen = torch.Generator(device=device).manual_seed(1)
+        bar_out = ctx.new_particles(ps.count, device=device)
+        bar_out.coeff.normal_(generator=gen)
+        bar_out.x.normal_(generator=gen)
+        bar_grid, bar_mid = ctx.new_grid(device=device), ctx.new_grid(device=device)
+        bar_in = ctx.new_particles(ps.count, device=device)
+        calls = {
+            "g2p_adjoint": lambda: pp.polypic_g2p_adjoint(ctx, g, ps, sc.dt, bar_out, bar_grid,
+                                                          bar_in, ws, stream=stream),
+            "grid_update_adjoint": lambda: pp.polypic_grid_update_adjoint(
+                ctx, g, prm, bar_grid, bar_mid, stream=stream),
+            "p2g_adjoint": lambda: pp.polypic_p2g_adjoint(ctx, ps, bar_mid, bar_in, ws,
+                                                          accumulate=True, stream=stream),
+        }
+        P, cells, nodes = ps.count, int(np.prod(sc.n)), face_nodes(sc.n)
+        nbytes = {
+            "g2p_adjoint": P * (12 + 24 + 12 * R + 12) + 2 * 4 * nodes,
+            "grid_update_adjoint": 20 * nodes,
+            "p2g_adjoint": P * (12 + 4 + 12 * R + 12 * R + 24) + 8 * nodes,
+        }
+        out = {"workload": f"random-velocity half box 64^3: {P} particles, 27 modes FP32"}
+        tot = 0.0
+        for name, fn in calls.items():
+            for _ in range(warmup):
+                fn()
+            ms = time_calls(torch, fn, iters, flush, stream)
+            tot += ms
+            out[name] = {"ms": round(ms, 4), **gbs(nbytes[name], ms)}
+        out["ms_adjoint_step"] = round(tot, 4)
+        out["value"] = round(P / (tot * 1e-3) / 1e6, 1)
+        out["unit"] = "M particle-steps/s (adjoint of one transfer step)"
+        out["bytes_note"] = ("g2p_adjoint: x, bar c, bar x in, bar x out, v and bar v; "
+                             "p2g_adjoint: x, m, c, bar c, bar x (read-modify-write), bar grid")
+        out["status"] = pp.STATUS_NAMES.get(pp.polypic_check_device_status(ctx))
+        rows["A8_adjoints"] = out
+        del ctx, ps, ws, g, bar_out, bar_grid, bar_mid, bar_in
+    del flush
+    torch.cuda.empty_cache()
+    return rows
 
 
 def run_e2e(pp, torch, scene, R, steps, device, lanes=2):
@@ -411,6 +584,9 @@ def our_arm(args):
         }
         del r
 
+    rows = run_rows(pp, torch, scenes, device, hbm, [r for r in args.rows.split(",") if r]) \
+        if args.rows else {}
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(pp, torch, scene, 27, args.e2e_steps, device)
@@ -447,6 +623,7 @@ def our_arm(args):
                              "frac_of_peak": round(pair_gbs / hbm, 4)},
             "roofline": roofline,
             "variants": variants,
+            "rows": rows,
             "e2e": e2e,
             "gpu_launches": launches_per_step() * args.steps,
             "clocks": clocks,
