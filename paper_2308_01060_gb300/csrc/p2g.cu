@@ -249,6 +249,33 @@ static cudaError_t launch_tiles(const P2GArgs &P, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Candidate tiles of a node along one axis: node n (owner tile u, tile size
+// S, region width Wd, T tiles) lies in the regions of tiles u + o0 and, when
+// `two`, u + o0 + 1, with o0 in {-1, 0}.  For candidate c the tile and
+// region offsets are separable: `part[c]` = tile offset x tile stride +
+// (n - S (u + o) + 1) x region stride, `live[c]` the neighbour index term.
+struct AxisCand {
+    int part[2], live[2];
+    bool ok[2];
+};
+
+__device__ __forceinline__ AxisCand axis_cand(int n, int u, int S, int Wd, int T,
+                                              int64_t tile_stride, int reg_stride,
+                                              int live_stride) {
+    // S is 8 or 4: floor division by a power of two (n + 2 - Wd may be < 0)
+    const int sh = S == 8 ? 3 : 2;
+    const int lo = max(0, (n + 2 - Wd + S - 1) >> sh), hi = min(T - 1, (n + 1) >> sh);
+    AxisCand c;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int t = lo + k;
+        c.ok[k] = t <= hi;
+        c.part[k] = (int)((t - u) * tile_stride) + (n - S * t + 1) * reg_stride;
+        c.live[k] = (t - u + 1) * live_stride;
+    }
+    return c;
+}
+
 // Sum over the (at most 8) tile regions covering node (i, j, k) of face grid
 // A, in ascending tile order (z, then y, then x); tiles without particles
 // wrote nothing and count as 0.  All candidate values are loaded before the
@@ -257,25 +284,23 @@ static cudaError_t launch_tiles(const P2GArgs &P, int grid, cudaStream_t s) {
 template <int A>
 __device__ __forceinline__ void reduce_node(const GridGeom &g, const uint8_t *s_live, int ux,
                                             int uy, int uz, int i, int j, int k,
-                                            const float *__restrict__ scratch,
+                                            const float *__restrict__ tile_base,
                                             float *__restrict__ gm, float *__restrict__ gp,
                                             float *__restrict__ gv, float dt, float ga,
                                             bool accumulate) {
     constexpr int X = tile_x(A), Y = tile_y(A), Z = tile_z(A);
-    const int tx0 = max(0, (i + 2 - X + 7) >> 3), tx1 = min(g.tiles[0] - 1, (i + 1) >> 3);
-    const int ty0 = max(0, (j + 2 - Y + 7) >> 3), ty1 = min(g.tiles[1] - 1, (j + 1) >> 3);
-    const int tz0 = max(0, (k + 2 - Z + 3) >> 2), tz1 = min(g.tiles[2] - 1, (k + 1) >> 2);
+    const int64_t F = kTileFloats;
+    const AxisCand cx = axis_cand(i, ux, 8, X, g.tiles[0], F, 1, 1);
+    const AxisCand cy = axis_cand(j, uy, 8, Y, g.tiles[1], F * g.tiles[0], X, 3);
+    const AxisCand cz = axis_cand(k, uz, 4, Z, g.tiles[2], F * g.tiles[0] * g.tiles[1], X * Y, 9);
     float m[8], v[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const int tz = tz0 + (c >> 2), ty = ty0 + ((c >> 1) & 1), tx = tx0 + (c & 1);
-        const bool use = tz <= tz1 && ty <= ty1 && tx <= tx1 &&
-                         s_live[((tz - uz + 1) * 3 + (ty - uy + 1)) * 3 + (tx - ux + 1)];
+        const int az = c >> 2, ay = (c >> 1) & 1, ax = c & 1;
         m[c] = v[c] = 0.0f;
-        if (use) {
-            const uint32_t t = ((uint32_t)tz * g.tiles[1] + ty) * g.tiles[0] + tx;
-            const int r = ((k - 4 * tz + 1) * Y + (j - 8 * ty + 1)) * X + (i - 8 * tx + 1);
-            const float *src = scratch + (size_t)t * kTileFloats + r;
+        if (cz.ok[az] && cy.ok[ay] && cx.ok[ax] &&
+            s_live[cz.live[az] + cy.live[ay] + cx.live[ax]]) {
+            const float *src = tile_base + (cz.part[az] + cy.part[ay] + cx.part[ax]);
             m[c] = __ldg(src + tile_off(A, 0));
             v[c] = __ldg(src + tile_off(A, 1));
         }
@@ -328,6 +353,8 @@ __global__ void __launch_bounds__(256) k_p2g_reduce(GridGeom g, const uint8_t *_
     __syncthreads();
     const int i = 8 * ux + (t & 7), j = 8 * uy + ((t >> 3) & 7), k = 4 * uz + (t >> 6);
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    // candidate offsets are relative to the owner tile, within +-1 tile of it
+    scratch += (size_t)tile * kTileFloats;
     // a tile at the grid's upper edge may extend past the cells (n not a
     // multiple of the tile): nodes beyond the face grid are not written
     if (i < nx + 1 && j < ny && k < nz)
