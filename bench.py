@@ -46,7 +46,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="grid cells per axis (default 128)")
-    ap.add_argument("--variants", default="apic4,bf16,f16")
+    ap.add_argument("--variants", default="apic4,apic4_gradw,apic4_affine,bf16,f16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
@@ -163,11 +163,12 @@ def make_state(pp, ctx, scene, device):
     return a, b
 
 
-def run_variant(pp, torch, scene, R, fmt, steps, warmup, device):
+def run_variant(pp, torch, scene, R, fmt, steps, warmup, device, **ctx_opts):
     """Times `steps` calls of polypic_step (the whole path, as a user runs it),
     then `steps` steps made of the individual calls (sort, P2G, grid update,
-    G2P) with events between them for the per-phase split."""
-    ctx = pp.Context(scene.n, scene.dx, R, coeff_format=fmt)
+    G2P) with events between them for the per-phase split.  ctx_opts: the
+    context's map_affine / apic_grad_w variants."""
+    ctx = pp.Context(scene.n, scene.dx, R, coeff_format=fmt, **ctx_opts)
     src, dst = make_state(pp, ctx, scene, device)
     g = ctx.new_grid(device=device)
     ws = ctx.workspace(src.count, device=device)
@@ -177,7 +178,7 @@ def run_variant(pp, torch, scene, R, fmt, steps, warmup, device):
     def phases(s, d, ev):
         pp.polypic_sort(ctx, s, ws, stream)
         ev[0].record(stream)
-        pp.polypic_p2g(ctx, s, g, ws, stream)
+        pp.polypic_p2g_mapped(ctx, s, g, scene.dt, ws, stream)
         ev[1].record(stream)
         pp.polypic_grid_update(ctx, g, prm, stream=stream)
         ev[2].record(stream)
@@ -573,13 +574,20 @@ def our_arm(args):
     }
 
     variants = {}
+    variant_defs = {
+        "apic4": (4, "f32", {}),
+        "apic4_gradw": (4, "f32", {"apic_grad_w": True}),     # Eq 10 in G2P
+        "apic4_affine": (4, "f32", {"map_affine": True}),     # Eq 12 in P2G
+        "bf16": (27, "bf16", {}),
+        "f16": (27, "f16", {}),
+    }
     for v in [s for s in args.variants.split(",") if s]:
-        R, fmt = (4, "f32") if v == "apic4" else (27, v)
-        r = run_variant(pp, torch, scene, R, fmt, args.steps, args.warmup, device)
+        R, fmt, opts = variant_defs[v]
+        r = run_variant(pp, torch, scene, R, fmt, args.steps, args.warmup, device, **opts)
         pb, gb = algorithmic_bytes(R, fmt)
         vph = r["phase_ms"]
         variants[v] = {
-            "modes": R, "coeff_format": fmt,
+            "modes": R, "coeff_format": fmt, **({"options": opts} if opts else {}),
             "value": P * args.steps / (r["total_ms"] * 1e-3) / 1e6,
             "ms_per_step": r["total_ms"] / args.steps,
             "phase_ms": [round(x, 4) for x in vph],

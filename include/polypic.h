@@ -92,8 +92,14 @@ typedef struct polypic_config {
     double dx;             /* cell width (> 0) */
     int32_t num_modes;     /* N_r: 1, 4, 8 or 27 */
     int32_t coeff_format;  /* POLYPIC_COEFF_* */
-    int32_t map;           /* POLYPIC_MAP_CONSTANT (Eq 12's affine map: UNSUPPORTED) */
-    int32_t apic_variant;  /* POLYPIC_APIC_TRUNCATION (Eq 10's grad-w form: UNSUPPORTED) */
+    int32_t map;           /* POLYPIC_MAP_CONSTANT, or POLYPIC_MAP_AFFINE (Eq 12):
+                              P2G evaluates the modes at xi = (I + dt C_p)^-1 (x_ia - x_p),
+                              C_p the linear-mode coefficients (C_ab = c_{a,1+b}); the
+                              identity when |det(I + dt C_p)| < 1e-6.  Built for
+                              num_modes 1 and 4 with FP32 coefficients, else UNSUPPORTED */
+    int32_t apic_variant;  /* POLYPIC_APIC_TRUNCATION, or POLYPIC_APIC_GRAD_W (Eq 10,
+                              num_modes 4 only, else INVALID_ARG): G2P sets the linear
+                              modes to sum_i (dw_ipa/dx_pb) v~_ia instead of the fit */
 } polypic_config;
 
 /* One phase of particles (Section 3.4: fluid, or solid with absorbed mass).
@@ -184,6 +190,16 @@ polypic_status polypic_sort(polypic_ctx *ctx, polypic_particles *p, void *ws, si
  * bit-identical from run to run (fixed summation order, no float atomics). */
 polypic_status polypic_p2g(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
                            void *ws, size_t ws_bytes, void *stream);
+
+/* P2G over a step of dt: polypic_p2g for the constant map; with
+ * POLYPIC_MAP_AFFINE (4 modes) the modes are evaluated at Eq 12's mapped
+ * offsets xi = (I + dt C_p)^-1 (x_ia - x_p), which turns the linear
+ * coefficients of component a into sum_b c_{a,1+b} M_bg (M = the inverse).
+ * polypic_p2g and polypic_p2g_noalloc return INVALID_ARG on such contexts
+ * (they have no dt); polypic_step passes its own.  Non-finite dt:
+ * INVALID_ARG. */
+polypic_status polypic_p2g_mapped(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
+                                  float dt, void *ws, size_t ws_bytes, void *stream);
 
 /* P2G exactly as polypic_p2g, but without a caller workspace: for callers
  * that cannot allocate device memory while they run, e.g. a host application
@@ -283,6 +299,9 @@ polypic_status polypic_step_ordered(polypic_ctx *ctx, const polypic_particles *i
                                     size_t ws_bytes, void *stream);
 
 /* ---- adjoints (constant map, single phase, no projection) ---------------- *
+ * Contexts with POLYPIC_MAP_AFFINE (4 modes) or POLYPIC_APIC_GRAD_W get
+ * UNSUPPORTED from the G2P adjoint, and with the affine map from the P2G
+ * adjoint.
  * Transposes of the forward calls at the forward state.  Adjoint particle
  * data reuse polypic_particles (x[3] = dL/dx, coeff = dL/dc as float
  * [3][num_modes][count]) and adjoint grids reuse polypic_grid (mass = dL/dm,

@@ -91,10 +91,17 @@ polypic_status do_sort(polypic_ctx *c, polypic_particles *p, void *ws, size_t ws
                                     W, s));
 }
 
+// Eq 12's map changes the transfer (4 modes; with one mode C = 0 and M = I).
+bool mapped(const polypic_ctx *c) {
+    return c->cfg.map == POLYPIC_MAP_AFFINE && c->cfg.num_modes == 4;
+}
+
 polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *g, void *ws,
                       size_t ws_bytes, cudaStream_t s, const polypic_update_params *fused = nullptr,
-                      bool ordered = false) {
+                      bool ordered = false, float map_dt = 0.0f) {
     P2GArgs P{};
+    P.affine = mapped(c);
+    P.map_dt = map_dt;
     P.g = c->geom;
     P.count = p->count;
     P.x = p->x[0];
@@ -145,6 +152,7 @@ polypic_status do_g2p(polypic_ctx *c, const polypic_grid *g, const polypic_parti
     A.oscale = out->coeff_scale;
     A.status = c->d_status;
     for (int l = 0; l < 7; ++l) A.inv_dxpow[l] = (float)std::pow(c->cfg.dx, -(double)l);
+    A.grad_w = c->cfg.apic_variant == POLYPIC_APIC_GRAD_W;
     int64_t tiles = c->num_keys / 256;
     return from_cuda(g2p(A, tiles, c->cfg.num_modes, c->cfg.coeff_format, s));
 }
@@ -225,10 +233,18 @@ polypic_status polypic_create(const polypic_config *cfg, polypic_ctx **out) {
     if (!valid_modes(cfg->num_modes)) return POLYPIC_ERR_INVALID_ARG;
     if (cfg->coeff_format < POLYPIC_COEFF_F32 || cfg->coeff_format > POLYPIC_COEFF_F16)
         return POLYPIC_ERR_INVALID_ARG;
-    if (cfg->map == POLYPIC_MAP_AFFINE) return POLYPIC_ERR_UNSUPPORTED;
-    if (cfg->map != POLYPIC_MAP_CONSTANT) return POLYPIC_ERR_INVALID_ARG;
-    if (cfg->apic_variant == POLYPIC_APIC_GRAD_W) return POLYPIC_ERR_UNSUPPORTED;
-    if (cfg->apic_variant != POLYPIC_APIC_TRUNCATION) return POLYPIC_ERR_INVALID_ARG;
+    if (cfg->map != POLYPIC_MAP_CONSTANT && cfg->map != POLYPIC_MAP_AFFINE)
+        return POLYPIC_ERR_INVALID_ARG;
+    // Eq 12's map keeps the 4-mode sum separable (a transform of the linear
+    // coefficients); with more modes it is not built
+    if (cfg->map == POLYPIC_MAP_AFFINE &&
+        (cfg->num_modes > 4 || cfg->coeff_format != POLYPIC_COEFF_F32))
+        return POLYPIC_ERR_UNSUPPORTED;
+    if (cfg->apic_variant != POLYPIC_APIC_TRUNCATION && cfg->apic_variant != POLYPIC_APIC_GRAD_W)
+        return POLYPIC_ERR_INVALID_ARG;
+    // Eq 10's gradient form replaces the linear modes of the 4-mode set
+    if (cfg->apic_variant == POLYPIC_APIC_GRAD_W && cfg->num_modes != 4)
+        return POLYPIC_ERR_INVALID_ARG;
 
     GridGeom g{};
     for (int a = 0; a < 3; ++a) g.n[a] = cfg->n[a];
@@ -297,7 +313,7 @@ polypic_status polypic_sort(polypic_ctx *ctx, polypic_particles *p, void *ws, si
 
 polypic_status polypic_p2g(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
                            void *ws, size_t ws_bytes, void *stream) {
-    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    if (!ctx || mapped(ctx)) return POLYPIC_ERR_INVALID_ARG;  // the map needs dt
     polypic_status s = check_sorted(p);
     if (s != POLYPIC_OK) return s;
     if ((s = check_coeff(ctx, p)) != POLYPIC_OK) return s;
@@ -306,9 +322,20 @@ polypic_status polypic_p2g(polypic_ctx *ctx, const polypic_particles *p, polypic
     return do_p2g(ctx, p, g, ws, ws_bytes, as_stream(stream));
 }
 
+polypic_status polypic_p2g_mapped(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
+                                  float dt, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !std::isfinite(dt)) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s = check_sorted(p);
+    if (s != POLYPIC_OK) return s;
+    if ((s = check_coeff(ctx, p)) != POLYPIC_OK) return s;
+    if (!grid_ok(g, true, true, false)) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_ws(ctx, p->count, ws, ws_bytes)) != POLYPIC_OK) return s;
+    return do_p2g(ctx, p, g, ws, ws_bytes, as_stream(stream), nullptr, false, dt);
+}
+
 polypic_status polypic_p2g_noalloc(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
                                    void *stream) {
-    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    if (!ctx || mapped(ctx)) return POLYPIC_ERR_INVALID_ARG;  // the map needs dt
     polypic_status s = check_sorted(p);
     if (s != POLYPIC_OK) return s;
     if ((s = check_coeff(ctx, p)) != POLYPIC_OK) return s;
@@ -396,11 +423,14 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
     // a single phase without projection gets the grid update fused into P2G's reduce
     const bool fuse = !solid && !params->project;
     if ((s = do_sort(ctx, fluid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
-    if ((s = do_p2g(ctx, fluid_in, gf, ws, ws_bytes, st, fuse ? params : nullptr)) != POLYPIC_OK)
+    if ((s = do_p2g(ctx, fluid_in, gf, ws, ws_bytes, st, fuse ? params : nullptr, false,
+                    params->dt)) != POLYPIC_OK)
         return s;
     if (solid) {
         if ((s = do_sort(ctx, solid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
-        if ((s = do_p2g(ctx, solid_in, gs, ws, ws_bytes, st)) != POLYPIC_OK) return s;
+        if ((s = do_p2g(ctx, solid_in, gs, ws, ws_bytes, st, nullptr, false, params->dt)) !=
+            POLYPIC_OK)
+            return s;
     }
     if (!fuse && (s = do_grid_update(ctx, gf, solid ? gs : nullptr, fluid_in, params, ws, ws_bytes,
                                      st)) != POLYPIC_OK)
@@ -453,6 +483,9 @@ polypic_status polypic_step_ordered(polypic_ctx *ctx, const polypic_particles *i
                                     const polypic_update_params *params, void *ws,
                                     size_t ws_bytes, void *stream) {
     if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    // ordered phases fit with the truncation form and the constant map only
+    if (mapped(ctx) || ctx->cfg.apic_variant != POLYPIC_APIC_TRUNCATION)
+        return POLYPIC_ERR_UNSUPPORTED;
     polypic_status s = check_positions(in);
     if (s != POLYPIC_OK) return s;
     if (!in->cell_start) return POLYPIC_ERR_INVALID_ARG;
@@ -534,6 +567,9 @@ polypic_status polypic_g2p_adjoint(polypic_ctx *ctx, const polypic_grid *g,
                                    polypic_particles *bar_in, int32_t flags, void *ws,
                                    size_t ws_bytes, void *stream) {
     if (!ctx || !std::isfinite(dt)) return POLYPIC_ERR_INVALID_ARG;
+    // the adjoints transpose the constant map and the truncation form
+    if (mapped(ctx) || ctx->cfg.apic_variant != POLYPIC_APIC_TRUNCATION)
+        return POLYPIC_ERR_UNSUPPORTED;
     if (ctx->cfg.coeff_format != POLYPIC_COEFF_F32) return POLYPIC_ERR_UNSUPPORTED;
     polypic_status s = check_sorted(in);
     if (s != POLYPIC_OK) return s;
@@ -582,7 +618,7 @@ polypic_status polypic_p2g_adjoint(polypic_ctx *ctx, const polypic_particles *in
                                    const polypic_grid *bar_grid, polypic_particles *bar_in,
                                    int32_t flags, void *ws, size_t ws_bytes, void *stream) {
     if (!ctx) return POLYPIC_ERR_INVALID_ARG;
-    if (ctx->cfg.coeff_format != POLYPIC_COEFF_F32) return POLYPIC_ERR_UNSUPPORTED;
+    if (ctx->cfg.coeff_format != POLYPIC_COEFF_F32 || mapped(ctx)) return POLYPIC_ERR_UNSUPPORTED;
     polypic_status s = check_sorted(in);
     if (s != POLYPIC_OK) return s;
     if ((s = check_coeff(ctx, in)) != POLYPIC_OK) return s;

@@ -14,7 +14,8 @@
 // FP32 output folds 1/dx and 1/dx^2 into the degree-1 and degree-2 factors and
 // so comes out in physical units; the 16-bit formats fit c dx^L, divide by the
 // per-particle scale s_p = max |c dx^L| and round to nearest even.  Outputs
-// are written in sorted slot order (coalesced).
+// are written in sorted slot order (coalesced).  With Eq 10's gradient form
+// (4 modes) the linear modes are sum_i dw_ipa/dx_p v~_ia instead of the fit.
 #include <type_traits>
 
 #include "g2p.cuh"
@@ -22,7 +23,7 @@
 
 namespace polypic {
 
-template <int R, int FMT>
+template <int R, int FMT, bool GRADW>
 __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
     __shared__ float s_tile[kVelTileFloats];
     const GridGeom &g = A.g;
@@ -88,17 +89,19 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
             constexpr int a = decltype(acomp)::value;
             if (ok) {
                 if constexpr (a == 0)
-                    g2p_component<R, 0, Tile<0>::X, Tile<0>::Y>(
+                    g2p_component<R, 0, Tile<0>::X, Tile<0>::Y, GRADW>(
                         s_tile, af0.base - ox, ac1.base - oy, ac2.base - oz, sf0, af0.guard, sc1,
-                        ac1.guard, sc2, ac2.guard, inv1, inv2, C);
+                        ac1.guard, sc2, ac2.guard, inv1, inv2, C, af0.t, ac1.t, ac2.t);
                 else if constexpr (a == 1)
-                    g2p_component<R, 1, Tile<1>::X, Tile<1>::Y>(
+                    g2p_component<R, 1, Tile<1>::X, Tile<1>::Y, GRADW>(
                         s_tile + kVelTileOff1, ac0.base - ox, af1.base - oy, ac2.base - oz, sc0,
-                        ac0.guard, sf1, af1.guard, sc2, ac2.guard, inv1, inv2, C);
+                        ac0.guard, sf1, af1.guard, sc2, ac2.guard, inv1, inv2, C, ac0.t, af1.t,
+                        ac2.t);
                 else
-                    g2p_component<R, 2, Tile<2>::X, Tile<2>::Y>(
+                    g2p_component<R, 2, Tile<2>::X, Tile<2>::Y, GRADW>(
                         s_tile + kVelTileOff2, ac0.base - ox, ac1.base - oy, af2.base - oz, sc0,
-                        ac0.guard, sc1, ac1.guard, sf2, af2.guard, inv1, inv2, C);
+                        ac0.guard, sc1, ac1.guard, sf2, af2.guard, inv1, inv2, C, ac0.t, ac1.t,
+                        af2.t);
             } else {
 #pragma unroll
                 for (int r = 0; r < R; ++r) C[r] = 0.0f;
@@ -153,9 +156,17 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
 
 cudaError_t g2p(const G2PArgs &A, int64_t num_tiles, int R, int fmt, cudaStream_t s) {
     const int grid = (int)num_tiles;
+    if (A.grad_w) {  // Eq 10's gradient form: 4 modes only
+        if (R != 4) return cudaErrorInvalidValue;
+        if (fmt == POLYPIC_COEFF_F32) k_g2p_tiles<4, POLYPIC_COEFF_F32, true><<<grid, kG2PThreads, 0, s>>>(A);
+        else if (fmt == POLYPIC_COEFF_BF16) k_g2p_tiles<4, POLYPIC_COEFF_BF16, true><<<grid, kG2PThreads, 0, s>>>(A);
+        else if (fmt == POLYPIC_COEFF_F16) k_g2p_tiles<4, POLYPIC_COEFF_F16, true><<<grid, kG2PThreads, 0, s>>>(A);
+        else return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
 #define POLYPIC_G2P_CASE(RR, FF)                                          \
     if (R == RR && fmt == FF) {                                          \
-        k_g2p_tiles<RR, FF><<<grid, kG2PThreads, 0, s>>>(A);             \
+        k_g2p_tiles<RR, FF, false><<<grid, kG2PThreads, 0, s>>>(A);      \
         return cudaGetLastError();                                       \
     }
     POLYPIC_G2P_CASE(1, POLYPIC_COEFF_F32)

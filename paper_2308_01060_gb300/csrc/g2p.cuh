@@ -16,6 +16,7 @@ struct G2PArgs {
     float *oscale;
     uint32_t *status;
     float inv_dxpow[7];   // 1 / dx^L, L = 0..6
+    bool grad_w;          // Eq 10's gradient form of the linear modes (4 modes)
 };
 
 cudaError_t g2p(const G2PArgs &A, int64_t num_tiles, int R, int fmt, cudaStream_t s);

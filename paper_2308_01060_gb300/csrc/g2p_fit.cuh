@@ -69,20 +69,38 @@ __device__ __forceinline__ void fit_factors(const Stencil1D &s, bool guard, floa
     }
 }
 
+// Eq 10's gradient form of the linear modes (4 modes only): the degree-1
+// factor of an axis becomes dW_k/dx_p = (t - 1/2, -2t, t + 1/2) / dx, the
+// x_p-derivative of the B-spline weights (inv1 = 1/dx, or 1 for c dx).
+template <int D>
+__device__ __forceinline__ void grad_w_factors(float t, float inv1, float (&G)[D][3]) {
+    static_assert(D == 2, "the gradient form replaces the linear modes of the 4-mode set");
+    G[1][0] = (t - 0.5f) * inv1;
+    G[1][1] = -2.0f * t * inv1;
+    G[1][2] = (t + 0.5f) * inv1;
+}
+
 // Fit of component A for one particle; Chat receives the dimensionless
 // coefficients c dx^L in canonical order (only the first R entries are set).
 // t: the staged values of face grid A, rows of TX nodes, planes of TY rows;
-// (lx, ly, lz): the stencil's lowest node in it.
-template <int R, int A, int TX, int TY>
+// (lx, ly, lz): the stencil's lowest node in it.  GRADW (4 modes): the
+// linear modes take Eq 10's weight gradients; (tx, ty, tz) are the axes' t.
+template <int R, int A, int TX, int TY, bool GRADW = false>
 __device__ __forceinline__ void g2p_component(const float *t, int lx, int ly, int lz,
                                               const Stencil1D &sx, bool gx, const Stencil1D &sy,
                                               bool gy, const Stencil1D &sz, bool gz, float inv1,
-                                              float inv2, float (&Chat)[R]) {
+                                              float inv2, float (&Chat)[R], float tx = 0.0f,
+                                              float ty = 0.0f, float tz = 0.0f) {
     constexpr int D = axis_degrees(R);
     float Gx[D][3], Gy[D][3], Gz[D][3];
     fit_factors<D>(sx, gx, inv1, inv2, Gx);
     fit_factors<D>(sy, gy, inv1, inv2, Gy);
     fit_factors<D>(sz, gz, inv1, inv2, Gz);
+    if constexpr (GRADW) {
+        grad_w_factors<D>(tx, inv1, Gx);
+        grad_w_factors<D>(ty, inv1, Gy);
+        grad_w_factors<D>(tz, inv1, Gz);
+    }
     // contract x
     float U1[D][3][3];
 #pragma unroll

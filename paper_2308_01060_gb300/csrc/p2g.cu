@@ -40,8 +40,8 @@ __device__ __forceinline__ int region_index(int ix, int iy, int iz) {
     return (iz * Reg<A>::Y + iy) * Reg<A>::X + ix;
 }
 
-template <int R> constexpr int p2g_smem_bytes() {
-    return (kP2GWarps * kRegionFloats + kP2GWarps * kStages * Stage<R>::NV * 32) * 4;
+template <int R, bool AFF = false> constexpr int p2g_smem_bytes() {
+    return (kP2GWarps * kRegionFloats + kP2GWarps * kStages * Stage<R, AFF>::NV * 32) * 4;
 }
 static_assert(p2g_smem_bytes<27>() <= 227 * 1024, "P2G staging exceeds the shared memory of a CTA");
 
@@ -56,13 +56,13 @@ struct Pipe {
     int ring;  // stage holding the next round to consume
 };
 
-template <int R, int FMT, bool ADJ>
+template <int R, int FMT, bool ADJ, bool AFF>
 __device__ __forceinline__ void pipe_issue(const P2GArgs &P, Pipe &q, uint32_t bs, uint32_t n_c,
                                            uint32_t maxn, unsigned lt, float *st, int lane) {
     if (q.ia < 3 && n_c > q.ir) {  // q.ia is warp-uniform
-        if (q.ia == 0) stage_particle<R, FMT, 0, ADJ>(P, q.pn, q.sn, st, lane);
-        else if (q.ia == 1) stage_particle<R, FMT, 1, ADJ>(P, q.pn, q.sn, st, lane);
-        else stage_particle<R, FMT, 2, ADJ>(P, q.pn, q.sn, st, lane);
+        if (q.ia == 0) stage_particle<R, FMT, 0, ADJ, AFF>(P, q.pn, q.sn, st, lane);
+        else if (q.ia == 1) stage_particle<R, FMT, 1, ADJ, AFF>(P, q.pn, q.sn, st, lane);
+        else stage_particle<R, FMT, 2, ADJ, AFF>(P, q.pn, q.sn, st, lane);
     }
     cp_async_commit();
     if (q.ia < 3 && ++q.ir == maxn) {
@@ -75,11 +75,11 @@ __device__ __forceinline__ void pipe_issue(const P2GArgs &P, Pipe &q, uint32_t b
     }
 }
 
-template <int R, int FMT, int A, bool ADJ>
+template <int R, int FMT, int A, bool ADJ, bool AFF>
 __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs, uint32_t n_c,
                                          uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
                                          int gk, int lane, float *reg, float *stage, bool &bad) {
-    using S = Stage<R>;
+    using S = Stage<R, AFF>;
     const bool interior = gi >= 1 && gi <= P.g.n[0] - 2 && gj >= 1 && gj <= P.g.n[1] - 2 &&
                           gk >= 1 && gk <= P.g.n[2] - 2;
     float am[4][3][3], av[4][3][3];
@@ -112,7 +112,7 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
                            aw = axis_decide(vw, false);
                 const int cu = A == 0 ? gi : (A == 1 ? gj : gk);
                 const int shift = au.base - (cu - 1);
-                accumulate<R, FMT, A, ADJ>(P, st, lane, mt, shift, stencil_1d_scaled(au.t, P.s1, P.s2),
+                accumulate<R, FMT, A, ADJ, AFF>(P, st, lane, mt, shift, stencil_1d_scaled(au.t, P.s1, P.s2),
                                            stencil_1d_scaled(av_.t, P.s1, P.s2), stencil_1d_scaled(aw.t, P.s1, P.s2), au.guard,
                                            av_.guard, aw.guard, am, av);
             } else {
@@ -120,7 +120,7 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
             }
         }
         // refill the stage just consumed with the next round of the stream
-        pipe_issue<R, FMT, ADJ>(P, q, bs, n_c, maxn, lt, st, lane);
+        pipe_issue<R, FMT, ADJ, AFF>(P, q, bs, n_c, maxn, lt, st, lane);
         q.ring = q.ring + 1 == kStages ? 0 : q.ring + 1;
     }
     // merge the 32 footprints into the block region, one node offset per phase
@@ -147,7 +147,7 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
 }
 
 // All three passes of one block: the prologue fills the ring once.
-template <int R, int FMT, bool ADJ>
+template <int R, int FMT, bool ADJ, bool AFF>
 __device__ __forceinline__ void p2g_block(const P2GArgs &P, uint32_t bs, uint32_t n_c,
                                           uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
                                           int gk, int lane, float *reg, float *stage, bool &bad) {
@@ -160,10 +160,11 @@ __device__ __forceinline__ void p2g_block(const P2GArgs &P, uint32_t bs, uint32_
     q.pn = n_c > 0 ? P.perm[q.sn] : 0u;
 #pragma unroll
     for (int k = 0; k < kStages; ++k)
-        pipe_issue<R, FMT, ADJ>(P, q, bs, n_c, maxn, lt, stage + k * Stage<R>::NV * 32, lane);
-    p2g_pass<R, FMT, 0, ADJ>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-    p2g_pass<R, FMT, 1, ADJ>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-    p2g_pass<R, FMT, 2, ADJ>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+        pipe_issue<R, FMT, ADJ, AFF>(P, q, bs, n_c, maxn, lt, stage + k * Stage<R, AFF>::NV * 32,
+                                     lane);
+    p2g_pass<R, FMT, 0, ADJ, AFF>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+    p2g_pass<R, FMT, 1, ADJ, AFF>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+    p2g_pass<R, FMT, 2, ADJ, AFF>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
     cp_async_wait<0>();
 }
 
@@ -192,7 +193,7 @@ __device__ __forceinline__ void merge_tile(const float *smem_regions, const bool
     }
 }
 
-template <int R, int FMT, bool ADJ>
+template <int R, int FMT, bool ADJ, bool AFF>
 // 27 modes keep the compiler's register allocation (one CTA per SM measured
 // faster); fewer modes fit two CTAs per SM without spills.
 __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles(P2GArgs P) {
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles
     const uint32_t bs = P.cell_start[b * 32];
     const uint32_t maxn = __reduce_max_sync(0xffffffffu, n_c);
     float *reg = s_reg + warp * kRegionFloats;
-    float *stage = s_stage + warp * kStages * Stage<R>::NV * 32;
+    float *stage = s_stage + warp * kStages * Stage<R, AFF>::NV * 32;
     if (lane == 0) s_empty[warp] = maxn == 0;
     if (maxn > 0) {
         for (int i = lane; i < kRegionFloats; i += 32) reg[i] = 0.0f;
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles
         const int ci = lane & 3, cj = (lane >> 2) & 3, ck = lane >> 4;
         const int gi = i0 + ci, gj = j0 + cj, gk = k0 + ck;
         bool bad = false;
-        p2g_block<R, FMT, ADJ>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
+        p2g_block<R, FMT, ADJ, AFF>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.status, kFlagOutOfDomain);
     }
     __syncthreads();
@@ -233,19 +234,19 @@ __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles
     merge_tile<2>(s_reg, s_empty, dst);
 }
 
-template <int R, int FMT, bool ADJ>
+template <int R, int FMT, bool ADJ, bool AFF = false>
 static cudaError_t launch_tiles(const P2GArgs &P, int grid, cudaStream_t s) {
-    const int smem = p2g_smem_bytes<R>();
+    const int smem = p2g_smem_bytes<R, AFF>();
     static int configured_device = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (configured_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_p2g_tiles<R, FMT, ADJ>,
+        cudaError_t e = cudaFuncSetAttribute(k_p2g_tiles<R, FMT, ADJ, AFF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured_device = dev;
     }
-    k_p2g_tiles<R, FMT, ADJ><<<grid, kP2GWarps * 32, smem, s>>>(P);
+    k_p2g_tiles<R, FMT, ADJ, AFF><<<grid, kP2GWarps * 32, smem, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -457,6 +458,12 @@ cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], floa
         return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
     }
     cudaError_t e = cudaErrorInvalidValue;
+    if (P.affine) {  // Eq 12's affine map: 4 modes, FP32 coefficients
+        if (R != 4 || fmt != POLYPIC_COEFF_F32) return cudaErrorInvalidValue;
+        e = launch_tiles<4, POLYPIC_COEFF_F32, false, true>(P, grid, s);
+        if (e != cudaSuccess) return e;
+        return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
+    }
 #define POLYPIC_P2G_CASE(RR, FF) \
     if (R == RR && fmt == FF) e = launch_tiles<RR, FF, false>(P, grid, s);
     POLYPIC_P2G_CASE(1, POLYPIC_COEFF_F32)

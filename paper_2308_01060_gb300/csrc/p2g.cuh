@@ -43,6 +43,9 @@ struct P2GArgs {
     uint32_t nblocks;          // num_keys / 32
     float dxpow[7];            // dx^L, L = 0..6 (FP32 coefficients -> dimensionless)
     float s1, s2;              // stencil scales of F1 and phi: dx, dx^2 for FP32 P2G, else 1
+    // Eq 12's affine map (4 modes, FP32): M = (I + map_dt C_p)^-1
+    bool affine;
+    float map_dt;
     // adjoint scatter only: mu [3][R][count] in slot order, 1/dx, 1/dx^2
     const float *mu;
     float inv_dx, inv_dx2;

@@ -46,9 +46,12 @@ template <int A> __host__ __device__ constexpr int deg_z(int du, int dv, int dw)
 // a private multi-stage buffer laid out [stage][value][lane] (conflict-free):
 // x, y, z, m, m_abs, s_p, the particle index, then one 32-bit word per mode
 // (the coefficient, or for 16-bit formats the aligned word holding its code).
-template <int R> struct Stage {
+// With Eq 12's affine map (AFF) six more words follow: the linear-mode
+// coefficients of the two other components (their C rows).
+template <int R, bool AFF = false> struct Stage {
     static constexpr int kX = 0, kY = 1, kZ = 2, kM = 3, kMabs = 4, kScale = 5, kIdx = 6, kC = 7;
-    static constexpr int NV = kC + R;
+    static constexpr int kL = kC + R;
+    static constexpr int NV = kL + (AFF ? 6 : 0);
 };
 
 __device__ __forceinline__ void cp_async4(float *dst, const void *src) {
@@ -62,10 +65,10 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int R, int FMT, int A, bool ADJ>
+template <int R, int FMT, int A, bool ADJ, bool AFF = false>
 __device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, uint32_t slot,
                                                float *st, int lane) {
-    using S = Stage<R>;
+    using S = Stage<R, AFF>;
     cp_async4(st + S::kX * 32 + lane, P.x + p);
     cp_async4(st + S::kY * 32 + lane, P.y + p);
     cp_async4(st + S::kZ * 32 + lane, P.z + p);
@@ -85,6 +88,18 @@ __device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, uin
         const float *c = reinterpret_cast<const float *>(P.coeff) + (int64_t)A * R * P.count + p;
 #pragma unroll
         for (int r = 0; r < R; ++r, c += P.count) cp_async4(st + (S::kC + r) * 32 + lane, c);
+        if constexpr (AFF) {
+            static_assert(R == 4, "the affine map is staged for the 4-mode set");
+            const float *cf = reinterpret_cast<const float *>(P.coeff) + p;
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int a2 = o < A ? o : o + 1;  // the other two components, ascending
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    cp_async4(st + (S::kL + 3 * o + b) * 32 + lane,
+                              cf + ((int64_t)a2 * R + 1 + b) * P.count);
+            }
+        }
     } else {
         cp_async4(st + S::kScale * 32 + lane, P.scale + p);
         // byte offset of code (A R + r, p); its aligned 4-byte word holds it
@@ -126,12 +141,54 @@ __device__ __forceinline__ void fit_rows(const Stencil1D &s, bool guard, float i
     }
 }
 
-template <int R, int FMT, int A, bool ADJ>
+// Eq 12's affine map for the 4-mode set: with C_ab = c_{a, 1+b} (the linear
+// modes of all three components) and M = (I + dt C)^-1 (the identity when
+// |det(I + dt C)| < 1e-6), sum_r c_r s_r(M z) = c_0 + sum_g (sum_b c_{1+b}
+// M_bg) z_g: the map turns component A's linear coefficients into (M^T c)_g.
+template <int R, int A>
+__device__ __forceinline__ void affine_linear(const float *st, int lane, float dt,
+                                              float (&cl)[3]) {
+    using S = Stage<R, true>;
+    float C[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int slot = a == A ? S::kC + 1 + b : S::kL + 3 * (a < A ? a : a - 1) + b;
+            C[a][b] = fmaf(dt, st[slot * 32 + lane], a == b ? 1.0f : 0.0f);
+        }
+    const float m00 = C[1][1] * C[2][2] - C[1][2] * C[2][1];
+    const float m01 = C[0][2] * C[2][1] - C[0][1] * C[2][2];
+    const float m02 = C[0][1] * C[1][2] - C[0][2] * C[1][1];
+    const float m10 = C[1][2] * C[2][0] - C[1][0] * C[2][2];
+    const float m11 = C[0][0] * C[2][2] - C[0][2] * C[2][0];
+    const float m12 = C[0][2] * C[1][0] - C[0][0] * C[1][2];
+    const float m20 = C[1][0] * C[2][1] - C[1][1] * C[2][0];
+    const float m21 = C[0][1] * C[2][0] - C[0][0] * C[2][1];
+    const float m22 = C[0][0] * C[1][1] - C[0][1] * C[1][0];
+    const float det = C[0][0] * m00 + C[0][1] * m10 + C[0][2] * m20;
+    const float c1 = st[(S::kC + 1) * 32 + lane], c2 = st[(S::kC + 2) * 32 + lane],
+                c3 = st[(S::kC + 3) * 32 + lane];
+    if (fabsf(det) < 1e-6f) {
+        cl[0] = c1;
+        cl[1] = c2;
+        cl[2] = c3;
+        return;
+    }
+    const float id = 1.0f / det;
+    cl[0] = (c1 * m00 + c2 * m10 + c3 * m20) * id;
+    cl[1] = (c1 * m01 + c2 * m11 + c3 * m21) * id;
+    cl[2] = (c1 * m02 + c2 * m12 + c3 * m22) * id;
+}
+
+template <int R, int FMT, int A, bool ADJ, bool AFF = false>
 __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, int lane, float mt,
                                            int shift, const Stencil1D &fu, const Stencil1D &fv,
                                            const Stencil1D &fw, bool gu, bool gv, bool gw,
                                            float (&am)[4][3][3], float (&av)[4][3][3]) {
-    using S = Stage<R>;
+    using S = Stage<R, AFF>;
+    float cl[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr (AFF) affine_linear<R, A>(st, lane, P.map_dt, cl);
     constexpr int D = axis_degrees(R);
     const float cscale = FMT == POLYPIC_COEFF_F32 ? 1.0f : st[S::kScale * 32 + lane];
     // 16-bit codes: element e = (A R + r) count + p sits in the high half of
@@ -194,7 +251,9 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
                 C[dv][dw] = 0.0f;
                 if (has_mode(R, a, b, c)) {
                     const int r = mode_index(a, b, c);
-                    if constexpr (FMT == POLYPIC_COEFF_F32) {
+                    if constexpr (AFF) {
+                        C[dv][dw] = r >= 1 && r <= 3 ? cl[r - 1] : st[(S::kC + r) * 32 + lane];
+                    } else if constexpr (FMT == POLYPIC_COEFF_F32) {
                         C[dv][dw] = st[(S::kC + r) * 32 + lane];
                     } else {
                         const uint32_t word =

@@ -69,7 +69,7 @@ _lib = None
 EXPORTS = [
     "polypic_create", "polypic_destroy", "polypic_num_keys", "polypic_cell_key",
     "polypic_grid_dims", "polypic_workspace_bytes", "polypic_sort", "polypic_p2g",
-    "polypic_p2g_noalloc",
+    "polypic_p2g_mapped", "polypic_p2g_noalloc",
     "polypic_grid_update", "polypic_g2p", "polypic_step", "polypic_order",
     "polypic_step_ordered", "polypic_g2p_adjoint",
     "polypic_grid_update_adjoint", "polypic_p2g_adjoint", "polypic_check_device_status",
@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH):
         "polypic_workspace_bytes": (ctypes.c_size_t, [_vp, ctypes.c_int64, ctypes.c_int64]),
         "polypic_sort": (st, [_vp, P(Particles), _vp, ctypes.c_size_t, _vp]),
         "polypic_p2g": (st, [_vp, P(Particles), P(Grid), _vp, ctypes.c_size_t, _vp]),
+        "polypic_p2g_mapped": (st, [_vp, P(Particles), P(Grid), ctypes.c_float, _vp,
+                                    ctypes.c_size_t, _vp]),
         "polypic_p2g_noalloc": (st, [_vp, P(Particles), P(Grid), _vp]),
         "polypic_grid_update": (st, [_vp, P(Grid), P(Grid), P(Particles), P(UpdateParams), _vp,
                                      ctypes.c_size_t, _vp]),
@@ -308,6 +310,18 @@ def polypic_p2g(ctx: Context, p: ParticleState, g: GridState, ws: torch.Tensor, 
     wp, wb = _ws(ws)
     _check(load_library().polypic_p2g(ctx.handle, ctypes.byref(cs), ctypes.byref(cg), wp, wb,
                                       _stream(stream)), "polypic_p2g")
+
+
+def polypic_p2g_mapped(ctx: Context, p: ParticleState, g: GridState, dt: float,
+                       ws: torch.Tensor, stream=None):
+    """P2G over a step of dt (Eq 12's affine map on contexts made with
+    map_affine=True; the same as polypic_p2g otherwise)."""
+    cs = p.c_struct()
+    cg = g.c_struct()
+    wp, wb = _ws(ws)
+    _check(load_library().polypic_p2g_mapped(ctx.handle, ctypes.byref(cs), ctypes.byref(cg),
+                                             float(dt), wp, wb, _stream(stream)),
+           "polypic_p2g_mapped")
 
 
 def polypic_p2g_noalloc(ctx: Context, p: ParticleState, g: GridState, stream=None):
