@@ -12,6 +12,11 @@ substitution g = z^2 - (mu3/mu2) z - mu2), and forms
 No base index, no 3x3x3 stencil, no guard: callers keep every particle away
 from the degenerate band 1 - 4t^2 < 2^-10.  Mode order is passed in as a list
 of (a, b, c) degree triples so that this module holds no mode table.
+
+p2g_mapped evaluates the modes at Eq 12's mapped offsets xi = M z with
+M = (I + dt C_p)^-1 from numpy's matrix inverse (C_ab = the coefficient of the
+linear mode along b for component a), the per-axis basis constants from the
+unmapped weights.
 """
 from __future__ import annotations
 
@@ -35,6 +40,49 @@ def _axis(xb, dx, offset, nnodes):
     kappa = mu3 / mu2
     f = np.stack([np.ones_like(z), z, z * z - kappa * z - mu2])
     return w, f
+
+
+def _axis_moments(xb, dx, offset, nnodes):
+    """Weights, node offsets z and the constants kappa, mu2 of one axis."""
+    nodes = np.arange(nnodes, dtype=np.float64)
+    X = xb / dx - offset
+    w = bspline2(X - nodes)
+    z = (nodes - X) * dx
+    mu2 = np.sum(w * z ** 2)
+    return w, z, np.sum(w * z ** 3) / mu2, mu2
+
+
+def p2g_mapped(x, mass, coeff, n, dx, modes, dt):
+    """P2G with the modes of particle p evaluated at xi = M_p z for every node."""
+    x = np.asarray(x, dtype=np.float64)
+    coeff = np.asarray(coeff, dtype=np.float64)
+    P = x.shape[1]
+    lin = {(1, 0, 0): 0, (0, 1, 0): 1, (0, 0, 1): 2}
+    gm, gp = [], []
+    for alpha in range(3):
+        dims = [int(n[b]) + (1 if b == alpha else 0) for b in range(3)]
+        m_acc = np.zeros((dims[2], dims[1], dims[0]))
+        p_acc = np.zeros_like(m_acc)
+        for p in range(P):
+            C = np.zeros((3, 3))
+            for r, abc in enumerate(modes):
+                if abc in lin:
+                    C[:, lin[abc]] = coeff[:, r, p]
+            A = np.eye(3) + dt * C
+            M = np.eye(3) if abs(np.linalg.det(A)) < 1e-6 else np.linalg.inv(A)
+            ax = [_axis_moments(x[b, p], dx, 0.0 if b == alpha else 0.5, dims[b]) for b in range(3)]
+            Z = np.stack(np.meshgrid(ax[2][1], ax[1][1], ax[0][1], indexing="ij")[::-1])  # (x, y, z)
+            xi = np.einsum("bc,ckji->bkji", M, Z)
+            w = np.einsum("k,j,i->kji", ax[2][0], ax[1][0], ax[0][0])
+            f = [np.stack([np.ones_like(xi[b]), xi[b], xi[b] ** 2 - ax[b][2] * xi[b] - ax[b][3]])
+                 for b in range(3)]
+            S = sum(coeff[alpha, r, p] * f[0][a] * f[1][b] * f[2][c]
+                    for r, (a, b, c) in enumerate(modes))
+            m_acc += mass[p] * w
+            p_acc += mass[p] * w * S
+        gm.append(m_acc)
+        gp.append(p_acc)
+    return gm, gp
 
 
 def _particle_grid(pos, alpha, n, dx, modes):

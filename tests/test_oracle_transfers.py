@@ -592,3 +592,42 @@ def test_affine_map_reduces_to_constant_map_at_zero_dt():
         assert np.array_equal(gm0[a], gm1[a]) and np.allclose(gp0[a], gp1[a], rtol=0, atol=0)
         assert np.array_equal(gm0[a], gm2[a])          # the map moves modes, not weights
         assert not np.allclose(gp0[a], gp2[a], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("R", [4, 8, 27])
+def test_affine_map_matches_all_pairs_mapped_evaluation(R):
+    """Eq 12: the oracle's stencil P2G with the affine map against an all-pairs
+    evaluation at xi = M z, M from numpy's inverse of I + dt C_p."""
+    rng = np.random.default_rng(70 + R)
+    n, dx, P, dt = (6, 6, 6), 1.0 / 6, 8, 2e-3
+    x = _safe_positions(rng, P, 6, lo=1.1, hi=4.9)
+    mass = rng.uniform(0.5, 1.5, P)
+    coeff = 0.05 * rng.standard_normal((3, R, P)) / (dx ** scenes.mode_degrees(R))[None, :, None]
+    coeff[:, 1:4] = rng.normal(0.0, 40.0, (3, 3, P))          # dt C ~ 0.08: the map matters
+    gm, gp = oracle.p2g(x, mass, coeff, n, dx, map_affine=True, dt=dt)
+    bm, bp = bruteforce.p2g_mapped(x, mass, coeff, n, dx, _modes(R), dt)
+    _, gp0 = oracle.p2g(x, mass, coeff, n, dx)
+    for a in range(3):
+        assert np.allclose(gm[a], bm[a], rtol=0, atol=1e-13)
+        assert np.abs(gp[a] - bp[a]).max() <= 1e-11 * np.abs(bp[a]).max()
+        assert np.abs(gp[a] - gp0[a]).max() > 1e-3 * np.abs(gp0[a]).max()
+
+
+def test_affine_map_with_four_modes_is_a_transform_of_the_linear_coefficients():
+    """With the 4-mode set, sum_r c_r s_r(M z) = c_0 + (M^T c_lin) . z: the
+    mapped P2G equals the constant-map P2G of the transformed coefficients."""
+    rng = np.random.default_rng(77)
+    n, dx, P, dt = (8, 8, 8), 1.0 / 8, 40, 2e-3
+    x = _safe_positions(rng, P, 8)
+    mass = rng.uniform(0.5, 1.5, P)
+    coeff = np.zeros((3, 4, P))
+    coeff[:, 0] = rng.normal(0.0, 0.3, (3, P))
+    coeff[:, 1:] = rng.normal(0.0, 40.0, (3, 3, P))
+    ct = coeff.copy()
+    for p in range(P):
+        M = np.linalg.inv(np.eye(3) + dt * coeff[:, 1:, p])
+        ct[:, 1:, p] = coeff[:, 1:, p] @ M                  # row a: sum_b c_{a,1+b} M_bg
+    _, gp = oracle.p2g(x, mass, coeff, n, dx, map_affine=True, dt=dt)
+    _, gt = oracle.p2g(x, mass, ct, n, dx)
+    for a in range(3):
+        assert np.abs(gp[a] - gt[a]).max() <= 1e-12 * np.abs(gt[a]).max()
