@@ -270,24 +270,28 @@ __device__ __forceinline__ void g2p_adj_component(const AdjG2PArgs &G, const Par
         }
     const float xn = fmaf(G.dt, c0, px_a);
     const bool clamped = xn < G.g.lo[A] || xn > G.g.hi[A];
-    const float lxo = G.bar_x[A][j];
-    float mu[D][D][D];
+    const float lxo = __ldg(G.bar_x[A] + j);
+    // all loads of the component first (read-only path), then the stores:
+    // the loads go out together instead of one per store
     const int64_t cnt = G.count;
+    const float *__restrict__ bc = G.bar_c + (int64_t)A * R * cnt + j;
+    float *__restrict__ mo = G.mu + (int64_t)A * R * cnt + j;
+    float mu[D][D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b)
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                float m = 0.0f;
-                if (has_mode(R, a, b, c)) {
-                    const int r = mode_index(a, b, c);
-                    m = G.bar_c[((int64_t)A * R + r) * cnt + j];
-                    if (r == 0 && !clamped) m = fmaf(G.dt, lxo, m);
-                    G.mu[((int64_t)A * R + r) * cnt + j] = m;
-                }
-                mu[a][b][c] = m;
-            }
+            for (int c = 0; c < D; ++c)
+                mu[a][b][c] = has_mode(R, a, b, c) ? __ldg(bc + mode_index(a, b, c) * cnt) : 0.0f;
+    if (!clamped) mu[0][0][0] = fmaf(G.dt, lxo, mu[0][0][0]);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                if (has_mode(R, a, b, c)) mo[mode_index(a, b, c) * cnt] = mu[a][b][c];
     float Dx = 0.0f, Dy = 0.0f, Dz = 0.0f;
     adj_position<R, D>(X, dX, Y, dY, Z, dZ, v, mu, Dx, Dy, Dz);
     lx[0] += Dx;
@@ -309,9 +313,25 @@ __global__ void __launch_bounds__(kAdjThreads) k_g2p_adjoint(AdjG2PArgs G) {
     const int ox = 8 * tx - 1, oy = 8 * ty - 1, oz = 4 * tz - 1;
     stage_tile(g, G.vel, ox, oy, oz, s_tile);
     __syncthreads();
-    for (uint32_t j = jb + threadIdx.x; j < je; j += kAdjThreads) {
-        const uint32_t p = G.perm[j];
-        const float px = G.x[0][p], py = G.x[1][p], pz = G.x[2][p];
+    // software pipeline: the next particle's index and position load while
+    // this one is computed
+    uint32_t j = jb + threadIdx.x;
+    uint32_t pn = j < je ? G.perm[j] : 0u;
+    float nx = 0.0f, ny = 0.0f, nz = 0.0f;
+    if (j < je) {
+        nx = G.x[0][pn];
+        ny = G.x[1][pn];
+        nz = G.x[2][pn];
+    }
+    for (; j < je; j += kAdjThreads) {
+        const uint32_t p = pn;
+        const float px = nx, py = ny, pz = nz;
+        if (j + kAdjThreads < je) {
+            pn = G.perm[j + kAdjThreads];
+            nx = G.x[0][pn];
+            ny = G.x[1][pn];
+            nz = G.x[2][pn];
+        }
         const ParticleAxes pa = particle_axes(g, px, py, pz, tx, ty, tz);
         float lx[3] = {0.0f, 0.0f, 0.0f};
         if (pa.ok) {
@@ -323,9 +343,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_g2p_adjoint(AdjG2PArgs G) {
             for (int a = 0; a < 3; ++a)
                 for (int r = 0; r < R; ++r) G.mu[((int64_t)a * R + r) * G.count + j] = 0.0f;
         }
+        if (G.accumulate) {  // three loads, then three stores
+            const float o0 = G.out_x[0][p], o1 = G.out_x[1][p], o2 = G.out_x[2][p];
+            lx[0] += o0;
+            lx[1] += o1;
+            lx[2] += o2;
+        }
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-            G.out_x[b][p] = G.accumulate ? G.out_x[b][p] + lx[b] : lx[b];
+        for (int b = 0; b < 3; ++b) G.out_x[b][p] = lx[b];
     }
 }
 
@@ -349,24 +374,45 @@ __device__ __forceinline__ void p2g_adj_component(const AdjP2GArgs &Q, const Par
     read_stencil<A>(tile_v, lx0, ly0, lz0, lmv);
     read_stencil<A>(tile_m, lx0, ly0, lz0, lm);
     const int64_t cnt = Q.count;
-    // coefficient adjoint
-    float lc[D][D][D];
-    contract_modes<R, D>(X, Y, Z, lmv, lc);
+    // the component's coefficients first (read-only path, all in flight at
+    // once), then the coefficient adjoint and its stores
+    const float *__restrict__ cin = Q.coeff + (int64_t)A * R * cnt + p;
+    float *__restrict__ cout = Q.out_c + (int64_t)A * R * cnt + p;
     float c[D][D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b)
 #pragma unroll
-            for (int cc = 0; cc < D; ++cc) {
-                c[a][b][cc] = 0.0f;
-                if (has_mode(R, a, b, cc)) {
-                    const int r = mode_index(a, b, cc);
-                    c[a][b][cc] = Q.coeff[((int64_t)A * R + r) * cnt + p];
-                    float* o = Q.out_c + ((int64_t)A * R + r) * cnt + p;
-                    *o = Q.accumulate ? *o + mt * lc[a][b][cc] : mt * lc[a][b][cc];
-                }
-            }
+            for (int cc = 0; cc < D; ++cc)
+                c[a][b][cc] = has_mode(R, a, b, cc) ? __ldg(cin + mode_index(a, b, cc) * cnt) : 0.0f;
+    float lc[D][D][D];
+    contract_modes<R, D>(X, Y, Z, lmv, lc);
+    if (Q.accumulate) {  // the old values, all loaded before the first store
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc)
+                    lc[a][b][cc] = has_mode(R, a, b, cc)
+                                       ? fmaf(mt, lc[a][b][cc], cout[mode_index(a, b, cc) * cnt])
+                                       : 0.0f;
+    } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc) lc[a][b][cc] *= mt;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc)
+                if (has_mode(R, a, b, cc)) cout[mode_index(a, b, cc) * cnt] = lc[a][b][cc];
     // position terms: momentum through the modes, mass through the weights
     float Dx = 0.0f, Dy = 0.0f, Dz = 0.0f;
     adj_position<R, D>(X, dX, Y, dY, Z, dZ, lmv, c, Dx, Dy, Dz);
@@ -399,10 +445,27 @@ __global__ void __launch_bounds__(kAdjThreads) k_p2g_adjoint(AdjP2GArgs Q) {
     stage_tile(g, Q.lm, ox, oy, oz, tile_m);
     stage_tile(g, Q.lmv, ox, oy, oz, tile_v);
     __syncthreads();
-    for (uint32_t j = jb + threadIdx.x; j < je; j += kAdjThreads) {
-        const uint32_t p = Q.perm[j];
-        const float px = Q.x[0][p], py = Q.x[1][p], pz = Q.x[2][p];
-        const float mt = Q.mass[p] + (Q.mass_abs ? Q.mass_abs[p] : 0.0f);
+    // software pipeline: the next particle's index, position and mass load
+    // while this one is computed
+    uint32_t j = jb + threadIdx.x;
+    uint32_t pn = j < je ? Q.perm[j] : 0u;
+    float nx = 0.0f, ny = 0.0f, nz = 0.0f, nm = 0.0f;
+    if (j < je) {
+        nx = Q.x[0][pn];
+        ny = Q.x[1][pn];
+        nz = Q.x[2][pn];
+        nm = Q.mass[pn] + (Q.mass_abs ? Q.mass_abs[pn] : 0.0f);
+    }
+    for (; j < je; j += kAdjThreads) {
+        const uint32_t p = pn;
+        const float px = nx, py = ny, pz = nz, mt = nm;
+        if (j + kAdjThreads < je) {
+            pn = Q.perm[j + kAdjThreads];
+            nx = Q.x[0][pn];
+            ny = Q.x[1][pn];
+            nz = Q.x[2][pn];
+            nm = Q.mass[pn] + (Q.mass_abs ? Q.mass_abs[pn] : 0.0f);
+        }
         const ParticleAxes pa = particle_axes(g, px, py, pz, tx, ty, tz);
         float lx[3] = {0.0f, 0.0f, 0.0f};
         if (pa.ok) {
@@ -417,9 +480,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_p2g_adjoint(AdjP2GArgs Q) {
                     if (!Q.accumulate) *o = 0.0f;
                 }
         }
+        if (Q.accumulate) {  // three loads, then three stores
+            const float o0 = Q.out_x[0][p], o1 = Q.out_x[1][p], o2 = Q.out_x[2][p];
+            lx[0] += o0;
+            lx[1] += o1;
+            lx[2] += o2;
+        }
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-            Q.out_x[b][p] = Q.accumulate ? Q.out_x[b][p] + lx[b] : lx[b];
+        for (int b = 0; b < 3; ++b) Q.out_x[b][p] = lx[b];
     }
 }
 
