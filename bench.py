@@ -46,7 +46,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="grid cells per axis (default 128)")
-    ap.add_argument("--variants", default="apic4,apic4_gradw,apic4_affine,bf16,f16")
+    ap.add_argument("--variants", default="apic4,apic4_gradw,apic4_affine,affine27,bf16,f16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
@@ -578,6 +578,7 @@ def our_arm(args):
         "apic4": (4, "f32", {}),
         "apic4_gradw": (4, "f32", {"apic_grad_w": True}),     # Eq 10 in G2P
         "apic4_affine": (4, "f32", {"map_affine": True}),     # Eq 12 in P2G
+        "affine27": (27, "f32", {"map_affine": True}),        # Eq 12, per-node modes
         "bf16": (27, "bf16", {}),
         "f16": (27, "f16", {}),
     }

@@ -95,8 +95,10 @@ typedef struct polypic_config {
     int32_t map;           /* POLYPIC_MAP_CONSTANT, or POLYPIC_MAP_AFFINE (Eq 12):
                               P2G evaluates the modes at xi = (I + dt C_p)^-1 (x_ia - x_p),
                               C_p the linear-mode coefficients (C_ab = c_{a,1+b}); the
-                              identity when |det(I + dt C_p)| < 1e-6.  Built for
-                              num_modes 1 and 4 with FP32 coefficients, else UNSUPPORTED */
+                              identity when |det(I + dt C_p)| < 1e-6.  FP32
+                              coefficients only (16-bit: UNSUPPORTED); 8 and 27 modes
+                              evaluate the mapped modes per stencil node, ~3.5x the
+                              arithmetic of the constant map */
     int32_t apic_variant;  /* POLYPIC_APIC_TRUNCATION, or POLYPIC_APIC_GRAD_W (Eq 10,
                               num_modes 4 only, else INVALID_ARG): G2P sets the linear
                               modes to sum_i (dw_ipa/dx_pb) v~_ia instead of the fit */
@@ -192,9 +194,9 @@ polypic_status polypic_p2g(polypic_ctx *ctx, const polypic_particles *p, polypic
                            void *ws, size_t ws_bytes, void *stream);
 
 /* P2G over a step of dt: polypic_p2g for the constant map; with
- * POLYPIC_MAP_AFFINE (4 modes) the modes are evaluated at Eq 12's mapped
- * offsets xi = (I + dt C_p)^-1 (x_ia - x_p), which turns the linear
- * coefficients of component a into sum_b c_{a,1+b} M_bg (M = the inverse).
+ * POLYPIC_MAP_AFFINE the modes are evaluated at Eq 12's mapped offsets
+ * xi = (I + dt C_p)^-1 (x_ia - x_p) (for 4 modes this turns the linear
+ * coefficients of component a into sum_b c_{a,1+b} M_bg, M = the inverse).
  * polypic_p2g and polypic_p2g_noalloc return INVALID_ARG on such contexts
  * (they have no dt); polypic_step passes its own.  Non-finite dt:
  * INVALID_ARG. */
@@ -299,7 +301,7 @@ polypic_status polypic_step_ordered(polypic_ctx *ctx, const polypic_particles *i
                                     size_t ws_bytes, void *stream);
 
 /* ---- adjoints (constant map, single phase, no projection) ---------------- *
- * Contexts with POLYPIC_MAP_AFFINE (4 modes) or POLYPIC_APIC_GRAD_W get
+ * Contexts with POLYPIC_MAP_AFFINE (4 modes or more) or POLYPIC_APIC_GRAD_W get
  * UNSUPPORTED from the G2P adjoint, and with the affine map from the P2G
  * adjoint.
  * Transposes of the forward calls at the forward state.  Adjoint particle

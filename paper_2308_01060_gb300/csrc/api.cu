@@ -91,9 +91,9 @@ polypic_status do_sort(polypic_ctx *c, polypic_particles *p, void *ws, size_t ws
                                     W, s));
 }
 
-// Eq 12's map changes the transfer (4 modes; with one mode C = 0 and M = I).
+// Eq 12's map changes the transfer (with one mode C = 0 and M = I).
 bool mapped(const polypic_ctx *c) {
-    return c->cfg.map == POLYPIC_MAP_AFFINE && c->cfg.num_modes == 4;
+    return c->cfg.map == POLYPIC_MAP_AFFINE && c->cfg.num_modes >= 4;
 }
 
 polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *g, void *ws,
@@ -235,10 +235,9 @@ polypic_status polypic_create(const polypic_config *cfg, polypic_ctx **out) {
         return POLYPIC_ERR_INVALID_ARG;
     if (cfg->map != POLYPIC_MAP_CONSTANT && cfg->map != POLYPIC_MAP_AFFINE)
         return POLYPIC_ERR_INVALID_ARG;
-    // Eq 12's map keeps the 4-mode sum separable (a transform of the linear
-    // coefficients); with more modes it is not built
-    if (cfg->map == POLYPIC_MAP_AFFINE &&
-        (cfg->num_modes > 4 || cfg->coeff_format != POLYPIC_COEFF_F32))
+    // Eq 12's map is built for FP32 coefficients (a transform of the linear
+    // coefficients for 4 modes, per-node evaluation for 8 and 27)
+    if (cfg->map == POLYPIC_MAP_AFFINE && cfg->coeff_format != POLYPIC_COEFF_F32)
         return POLYPIC_ERR_UNSUPPORTED;
     if (cfg->apic_variant != POLYPIC_APIC_TRUNCATION && cfg->apic_variant != POLYPIC_APIC_GRAD_W)
         return POLYPIC_ERR_INVALID_ARG;

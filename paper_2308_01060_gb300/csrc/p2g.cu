@@ -114,7 +114,7 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
                 const int shift = au.base - (cu - 1);
                 accumulate<R, FMT, A, ADJ, AFF>(P, st, lane, mt, shift, stencil_1d_scaled(au.t, P.s1, P.s2),
                                            stencil_1d_scaled(av_.t, P.s1, P.s2), stencil_1d_scaled(aw.t, P.s1, P.s2), au.guard,
-                                           av_.guard, aw.guard, am, av);
+                                           av_.guard, aw.guard, am, av, au.t, av_.t, aw.t);
             } else {
                 bad = true;
             }
@@ -195,8 +195,10 @@ __device__ __forceinline__ void merge_tile(const float *smem_regions, const bool
 
 template <int R, int FMT, bool ADJ, bool AFF>
 // 27 modes keep the compiler's register allocation (one CTA per SM measured
-// faster); fewer modes fit two CTAs per SM without spills.
-__global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 ? 1 : 2)) k_p2g_tiles(P2GArgs P) {
+// faster); fewer modes fit two CTAs per SM without spills, except the
+// per-node evaluation of the affine map.
+__global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 || (AFF && R > 4) ? 1 : 2))
+    k_p2g_tiles(P2GArgs P) {
     extern __shared__ float smem[];
     __shared__ bool s_empty[kP2GWarps];
     float *s_reg = smem;                                     // [8][kRegionFloats]
@@ -458,9 +460,11 @@ cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], floa
         return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
     }
     cudaError_t e = cudaErrorInvalidValue;
-    if (P.affine) {  // Eq 12's affine map: 4 modes, FP32 coefficients
-        if (R != 4 || fmt != POLYPIC_COEFF_F32) return cudaErrorInvalidValue;
-        e = launch_tiles<4, POLYPIC_COEFF_F32, false, true>(P, grid, s);
+    if (P.affine) {  // Eq 12's affine map: FP32 coefficients, 4, 8 or 27 modes
+        if (fmt != POLYPIC_COEFF_F32) return cudaErrorInvalidValue;
+        if (R == 4) e = launch_tiles<4, POLYPIC_COEFF_F32, false, true>(P, grid, s);
+        else if (R == 8) e = launch_tiles<8, POLYPIC_COEFF_F32, false, true>(P, grid, s);
+        else if (R == 27) e = launch_tiles<27, POLYPIC_COEFF_F32, false, true>(P, grid, s);
         if (e != cudaSuccess) return e;
         return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
     }

@@ -89,7 +89,6 @@ __device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, uin
 #pragma unroll
         for (int r = 0; r < R; ++r, c += P.count) cp_async4(st + (S::kC + r) * 32 + lane, c);
         if constexpr (AFF) {
-            static_assert(R == 4, "the affine map is staged for the 4-mode set");
             const float *cf = reinterpret_cast<const float *>(P.coeff) + p;
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
@@ -141,13 +140,12 @@ __device__ __forceinline__ void fit_rows(const Stencil1D &s, bool guard, float i
     }
 }
 
-// Eq 12's affine map for the 4-mode set: with C_ab = c_{a, 1+b} (the linear
-// modes of all three components) and M = (I + dt C)^-1 (the identity when
-// |det(I + dt C)| < 1e-6), sum_r c_r s_r(M z) = c_0 + sum_g (sum_b c_{1+b}
-// M_bg) z_g: the map turns component A's linear coefficients into (M^T c)_g.
+// Eq 12's affine map: M = (I + dt C)^-1 with C_ab = c_{a, 1+b} (the linear
+// modes of all three components, component A's own row from its staged
+// coefficients), the identity when |det(I + dt C)| < 1e-6.
 template <int R, int A>
-__device__ __forceinline__ void affine_linear(const float *st, int lane, float dt,
-                                              float (&cl)[3]) {
+__device__ __forceinline__ void affine_inverse(const float *st, int lane, float dt,
+                                               float (&M)[3][3]) {
     using S = Stage<R, true>;
     float C[3][3];
 #pragma unroll
@@ -167,26 +165,120 @@ __device__ __forceinline__ void affine_linear(const float *st, int lane, float d
     const float m21 = C[0][1] * C[2][0] - C[0][0] * C[2][1];
     const float m22 = C[0][0] * C[1][1] - C[0][1] * C[1][0];
     const float det = C[0][0] * m00 + C[0][1] * m10 + C[0][2] * m20;
-    const float c1 = st[(S::kC + 1) * 32 + lane], c2 = st[(S::kC + 2) * 32 + lane],
-                c3 = st[(S::kC + 3) * 32 + lane];
     if (fabsf(det) < 1e-6f) {
-        cl[0] = c1;
-        cl[1] = c2;
-        cl[2] = c3;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) M[a][b] = a == b ? 1.0f : 0.0f;
         return;
     }
     const float id = 1.0f / det;
-    cl[0] = (c1 * m00 + c2 * m10 + c3 * m20) * id;
-    cl[1] = (c1 * m01 + c2 * m11 + c3 * m21) * id;
-    cl[2] = (c1 * m02 + c2 * m12 + c3 * m22) * id;
+    M[0][0] = m00 * id; M[0][1] = m01 * id; M[0][2] = m02 * id;
+    M[1][0] = m10 * id; M[1][1] = m11 * id; M[1][2] = m12 * id;
+    M[2][0] = m20 * id; M[2][1] = m21 * id; M[2][2] = m22 * id;
+}
+
+// The 4-mode set under the map: sum_r c_r s_r(M z) = c_0 + sum_g (sum_b
+// c_{1+b} M_bg) z_g, so component A's linear coefficients become (M^T c)_g.
+template <int R, int A>
+__device__ __forceinline__ void affine_linear(const float *st, int lane, float dt,
+                                              float (&cl)[3]) {
+    using S = Stage<R, true>;
+    float M[3][3];
+    affine_inverse<R, A>(st, lane, dt, M);
+    const float c1 = st[(S::kC + 1) * 32 + lane], c2 = st[(S::kC + 2) * 32 + lane],
+                c3 = st[(S::kC + 3) * 32 + lane];
+#pragma unroll
+    for (int g = 0; g < 3; ++g) cl[g] = c1 * M[0][g] + c2 * M[1][g] + c3 * M[2][g];
+}
+
+// 8 and 27 modes under the map are not separable per axis: every stencil node
+// evaluates s_r(xi) = f_a(xi_x) f_b(xi_y) f_c(xi_z) at xi = M z, with
+// f_2(xi) = xi^2 - kappa xi - mu2 from the particle's own (unmapped) axis
+// constants kappa = dx t (1 - 4t^2), mu2 = dx^2 / 4, and adds
+// mt w(node) sum_r c_r s_r(xi) into the padded footprint (FP32, physical c).
+template <int R, int A>
+__device__ __forceinline__ void accumulate_mapped(const P2GArgs &P, const float *st, int lane,
+                                                  float mt, int shift, float tu, float tv,
+                                                  float tw, const Stencil1D &fu,
+                                                  const Stencil1D &fv, const Stencil1D &fw,
+                                                  float (&am)[4][3][3], float (&av)[4][3][3]) {
+    using S = Stage<R, true>;
+    constexpr int D = axis_degrees(R);
+    float M[3][3];
+    affine_inverse<R, A>(st, lane, P.map_dt, M);
+    const float dx = P.dxpow[1], mu2 = 0.25f * P.dxpow[2];
+    // axes u (= A), v, w as x, y, z indices, and each axis's node offsets
+    constexpr int U = A, V = A == 0 ? 1 : 0, Wx = A == 2 ? 1 : 2;
+    const float t3[3] = {tu, tv, tw};
+    float kap[3];   // by x, y, z
+    float Mz[3][3][3];  // [axis u/v/w][node k][component of xi]
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int ax = e == 0 ? U : (e == 1 ? V : Wx);
+        const float t = t3[e];
+        kap[ax] = dx * t * ((1.0f - 2.0f * t) * (1.0f + 2.0f * t));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float z = ((float)(k - 1) - t) * dx;
+#pragma unroll
+            for (int g = 0; g < 3; ++g) Mz[e][k][g] = M[g][ax] * z;
+        }
+    }
+    float c[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) c[r] = st[(S::kC + r) * 32 + lane];
+#pragma unroll
+    for (int ku = 0; ku < 3; ++ku)
+#pragma unroll
+        for (int kv = 0; kv < 3; ++kv)
+#pragma unroll
+            for (int kw = 0; kw < 3; ++kw) {
+                float f[3][3];  // [axis x/y/z][degree]
+#pragma unroll
+                for (int g = 0; g < 3; ++g) {
+                    const float xi = Mz[0][ku][g] + Mz[1][kv][g] + Mz[2][kw][g];
+                    f[g][0] = 1.0f;
+                    f[g][1] = xi;
+                    f[g][2] = fmaf(xi, xi - kap[g], -mu2);
+                }
+                float Sn = 0.0f;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    float Sa = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < D; ++b) {
+                        float Sb = 0.0f;
+#pragma unroll
+                        for (int cc = 0; cc < D; ++cc)
+                            if (has_mode(R, a, b, cc))
+                                Sb = fmaf(c[mode_index(a, b, cc)], f[2][cc], Sb);
+                        Sa = fmaf(Sb, f[1][b], Sa);
+                    }
+                    Sn = fmaf(Sa, f[0][a], Sn);
+                }
+                // node ku lands on footprint row ku + shift; both candidate
+                // rows are static indices (the footprint stays in registers)
+                const float w = mt * fu.W[ku] * fv.W[kv] * fw.W[kw];
+                const float wS = w * Sn;
+                am[ku][kv][kw] += shift ? 0.0f : w;
+                am[ku + 1][kv][kw] += shift ? w : 0.0f;
+                av[ku][kv][kw] += shift ? 0.0f : wS;
+                av[ku + 1][kv][kw] += shift ? wS : 0.0f;
+            }
 }
 
 template <int R, int FMT, int A, bool ADJ, bool AFF = false>
 __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, int lane, float mt,
                                            int shift, const Stencil1D &fu, const Stencil1D &fv,
                                            const Stencil1D &fw, bool gu, bool gv, bool gw,
-                                           float (&am)[4][3][3], float (&av)[4][3][3]) {
+                                           float (&am)[4][3][3], float (&av)[4][3][3],
+                                           float tu = 0.0f, float tv = 0.0f, float tw = 0.0f) {
     using S = Stage<R, AFF>;
+    if constexpr (AFF && R > 4) {
+        accumulate_mapped<R, A>(P, st, lane, mt, shift, tu, tv, tw, fu, fv, fw, am, av);
+        return;
+    }
     float cl[3] = {0.0f, 0.0f, 0.0f};
     if constexpr (AFF) affine_linear<R, A>(st, lane, P.map_dt, cl);
     constexpr int D = axis_degrees(R);

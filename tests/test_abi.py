@@ -63,7 +63,12 @@ def test_host_validation_without_gpu(lib):
     cfg.num_modes = 5                                   # not 1, 4, 8, 27
     assert L.polypic_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
     cfg.num_modes = 27
-    cfg.map = 1                                         # Eq 12 affine map: not built
+    cfg.map, cfg.coeff_format = 1, 1                    # Eq 12 map with 16-bit codes: not built
     assert L.polypic_create(ctypes.byref(cfg), ctypes.byref(h)) == 2
+    cfg.map, cfg.coeff_format = 2, 0                    # no such map
+    assert L.polypic_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    cfg.map, cfg.apic_variant = 0, 1                    # Eq 10's form needs the 4-mode set
+    assert L.polypic_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    cfg.apic_variant = 0
     assert L.polypic_p2g(None, None, None, None, 0, None) == 1
     assert L.polypic_step(None, None, None, None, None, None, None, None, None, 0, None) == 1

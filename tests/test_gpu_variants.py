@@ -3,8 +3,9 @@ FP64 oracle.
 
   * Eq 10's gradient form of the linear modes in G2P (apic_grad_w): FP32
     coefficients and positions, and the BF16 codes through a P2G round trip;
-  * Eq 12's affine map in P2G (map_affine): momentum with linear modes large
-    enough that the map changes it well beyond the tolerance; the identity
+  * Eq 12's affine map in P2G (map_affine; 4, 8 and 27 modes): momentum with
+    linear modes large enough that the map changes it well beyond the
+    tolerance; the identity
     fallback when det(I + dt C) vanishes; dt = 0 equal bit for bit to the
     constant map; a whole step with both variants;
   * the configurations that are not built return their documented status.
@@ -86,11 +87,17 @@ def test_g2p_grad_w_16bit_round_trip():
 
 # ------------------------------------------------------------------ Eq 12
 
-def test_p2g_affine_map_matches_oracle():
-    sc = _scene(seed=43)
-    f = _linear_heavy(sc.fluid, seed=1)
+@pytest.mark.parametrize("R", [4, 8, 27])
+def test_p2g_affine_map_matches_oracle(R):
+    """4 modes: the linear-coefficient transform; 8 and 27: per-node
+    evaluation of the mapped modes."""
+    sc = scenes.parity_scene(n=32, R=R, seed=43, random_mode_init=True)
+    f = sc.fluid
+    c = f.coeff.copy()
+    c[:, 1:4] = np.random.default_rng(1).normal(0.0, 30.0, (3, 3, f.n)).astype(np.float32)
+    f = scenes.ParticleSet(x=f.x, mass=f.mass, coeff=c, num_modes=R)
     dt = 2e-3
-    ctx = pp.Context(sc.n, sc.dx, 4, map_affine=True)
+    ctx = pp.Context(sc.n, sc.dx, R, map_affine=True)
     ps, ws = sorted_particles(ctx, f)
     g = ctx.new_grid(vel=False)
     pp.polypic_p2g_mapped(ctx, ps, g, dt, ws)
@@ -188,10 +195,10 @@ def _create_status(**kw):
 def test_variant_configurations_report_their_status():
     assert _create_status(R=4, map=1) == 0
     assert _create_status(R=1, map=1) == 0
+    assert _create_status(R=8, map=1) == 0
+    assert _create_status(R=27, map=1) == 0
     assert _create_status(R=4, apic=1) == 0
     assert _create_status(R=4, apic=1, fmt="bf16") == 0
-    assert pp.STATUS_NAMES[_create_status(R=8, map=1)] == "UNSUPPORTED"
-    assert pp.STATUS_NAMES[_create_status(R=27, map=1)] == "UNSUPPORTED"
     assert pp.STATUS_NAMES[_create_status(R=4, map=1, fmt="bf16")] == "UNSUPPORTED"
     assert pp.STATUS_NAMES[_create_status(R=8, apic=1)] == "INVALID_ARG"
     assert pp.STATUS_NAMES[_create_status(R=4, map=2)] == "INVALID_ARG"
