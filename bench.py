@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-lanes", type=int, default=3,
+                    help="streams (each with its own device buffers) the e2e steps rotate over")
     ap.add_argument("--rows", default="coupled,update,projection,adjoint",
                     help="the other rows of the path, each timed on its own workload")
     return ap.parse_args()
@@ -604,7 +606,7 @@ def our_arm(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(pp, torch, scene, 27, args.e2e_steps, device)
+        e2e = run_e2e(pp, torch, scene, 27, args.e2e_steps, device, lanes=args.e2e_lanes)
         if world > 1:
             import torch.distributed as dist
             t = torch.tensor([e2e["ms_per_step"]], device=device)
