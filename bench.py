@@ -333,7 +333,7 @@ def run_rows(pp, torch, scenes, device, hbm, which, iters=10, warmup=3):
             ms_p = time_calls(torch, pr, 3, flush, stream)
             rows["A4_projection"] = {
                 "workload": "dam break 128^3 after 10 steps: 64x128x64 fluid cells, "
-                            "Jacobi-PCG rtol 1e-6, at most 2000 iterations",
+                            "multigrid-preconditioned CG to rtol 1e-6, at most 2000 iterations",
                 "ms_update_and_projection": round(ms_p, 3),
                 "ms_projection": round(ms_p - ms_u, 3),
                 "note": "not in the headline step; the host reads the residual every 8 "

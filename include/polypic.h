@@ -228,7 +228,8 @@ polypic_status polypic_p2g_noalloc(polypic_ctx *ctx, const polypic_particles *p,
  * v~ = v + dt g; with a solid grid and drag_k > 0, implicit two-phase drag on
  * faces where both masses are positive, u' = u / (1 + dt K (1/m_f + 1/m_s))
  * for u = v_f - v_s, keeping the mass-weighted mean; v~_a = 0 on the wall
- * faces i_a in {0, n_a}; optional pressure projection (Jacobi-PCG on cells
+ * faces i_a in {0, n_a}; optional pressure projection (CG preconditioned by
+ * a multigrid V-cycle on cells
  * holding fluid particles, FP64 dot products and norms) needs
  * fluid_particles->cell_start.  Writes fluid->vel (and solid->vel).
  * `solid` and `fluid_particles` may be NULL. */

@@ -352,8 +352,9 @@ def test_16bit_coefficients_round_trip(fmt, tol):
 # ------------------------------------------------------------------ projection
 
 def test_pcg_projection_matches_oracle():
-    """Jacobi-PCG with FP64 reductions on the cells holding fluid particles:
-    same projected field as the oracle's FP64 solve, divergence-free."""
+    """Multigrid-preconditioned CG with FP64 reductions on the cells holding
+    fluid particles: same projected field as the oracle's FP64 solve,
+    divergence-free."""
     sc = scenes.dam_break_scene(n=24, R=1, dt=1e-3)
     f = sc.fluid
     ctx = pp.Context(sc.n, sc.dx, 1)
@@ -377,6 +378,34 @@ def test_pcg_projection_matches_oracle():
     div = (np.diff(v[0], axis=2) + np.diff(v[1], axis=1) + np.diff(v[2], axis=0)) / sc.dx
     div0 = (np.diff(fv[0], axis=2) + np.diff(fv[1], axis=1) + np.diff(fv[2], axis=0)) / sc.dx
     assert np.abs(div[fluid]).max() <= 1e-4 * np.abs(div0[fluid]).max()
+
+
+@pytest.mark.parametrize("n,maxiter", [((19, 13, 11), 48), ((32, 16, 8), 48), ((512, 4, 4), 2000)])
+def test_pcg_projection_odd_and_flat_grids(n, maxiter):
+    """The multigrid hierarchy on grids whose sides halve to odd sizes and to
+    1: the projected field against the oracle's FP64 solve (convergence
+    within 48 iterations on the compact grids)."""
+    dx = 1.0 / n[0]
+    rng = np.random.default_rng(11)
+    cells = np.stack([rng.integers(1, n[b] - 1, 4000) for b in range(3)])
+    keep = cells[1] < (2 * n[1]) // 3                        # a lower slab of fluid
+    x = ((cells[:, keep] + rng.uniform(0.1, 0.9, (3, keep.sum()))) * dx).astype(np.float32)
+    ctx = pp.Context(n, dx, 1)
+    ps, ws = sorted_particles(ctx, scenes.ParticleSet(x=x, mass=np.ones(x.shape[1], np.float32),
+                                                      coeff=None, num_modes=1))
+    gv = random_grid_velocity(n, dx, seed=79)
+    gm = [np.ones_like(v) for v in gv]
+    g = grid_from_host(ctx, mass=gm, mom=gv)
+    prm = pp.UpdateSettings(dt=1e-3, project=True, pcg_rtol=1e-6, pcg_maxiter=maxiter)
+    pp.polypic_grid_update(ctx, g, prm, fluid_particles=ps, ws=ws)
+    assert pp.polypic_check_device_status(ctx) == 0
+    fv = oracle.grid_update(n, prm.dt, prm.gravity, gm, gv)
+    fluid = np.zeros((n[2], n[1], n[0]), dtype=bool)
+    c32 = np.floor(x * np.float32(1 / dx)).astype(int)
+    fluid[c32[2], c32[1], c32[0]] = True
+    vp, _, _ = oracle.pcg_project(n, dx, prm.dt, 1000.0, fluid, fv, rtol=1e-10, maxiter=5000)
+    for a in range(3):
+        assert rel(np_(g.vel[a]), vp[a]) < 1e-4
 
 
 def test_pcg_reports_not_converged():
