@@ -3,9 +3,10 @@
 // The paper has no sort; it is the device that makes the transfers
 // deterministic and coalesced.  No kernel waits on another CTA:
 //   1. k_keys:     key of every particle (FP32 cell decision), domain check,
-//                  per-key counts with warp-aggregated integer atomics (exact:
-//                  integer addition is order independent) whose return values
-//                  give each particle an arrival rank inside its cell;
+//                  per-key counts with integer atomics, one per run of equal
+//                  keys along a lane (exact: integer addition is order
+//                  independent), whose return values give each particle an
+//                  arrival rank inside its cell;
 //   2. scan:       exclusive prefix sum of the counts -> cell_start;
 //   3. k_scatter:  particle p to cell_start[key] + arrival rank, so every
 //                  cell's particles fill its range in a timing-dependent order;
@@ -24,6 +25,14 @@
 namespace polypic {
 
 // ---------------------------------------------------------------- keys
+// A warp takes kKeyRuns x 32 consecutive particles, lane l the particles
+// l, l + 32, l + 64, ... of its chunk.  In the slot order the previous step's
+// G2P wrote, a full round of a block is 32 consecutive slots of 32 different
+// cells, so a lane's successive particles tend to share a cell: each run of
+// equal keys along a lane takes one atomicAdd of its length (integer, exact)
+// and ranks its particles from the returned count.
+constexpr int kKeyRuns = 8;
+
 __global__ void __launch_bounds__(256) k_keys(int64_t n, const float *__restrict__ x,
                                               const float *__restrict__ y,
                                               const float *__restrict__ z, GridGeom g,
@@ -32,29 +41,48 @@ __global__ void __launch_bounds__(256) k_keys(int64_t n, const float *__restrict
                                               uint32_t *__restrict__ counts,
                                               uint32_t *__restrict__ num_crowded,
                                               uint32_t *__restrict__ status) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0) *num_crowded = 0;
-    bool live = p < n;
-    uint32_t k = 0;
-    bool bad = false;
-    if (live) {
-        float vx = cell_coord(x[p], g.inv_dx);
-        float vy = cell_coord(y[p], g.inv_dx);
-        float vz = cell_coord(z[p], g.inv_dx);
-        bad = !(coord_valid(vx, g.n[0]) && coord_valid(vy, g.n[1]) && coord_valid(vz, g.n[2]));
-        k = cell_key(g, cell_index(vx, g.n[0]), cell_index(vy, g.n[1]), cell_index(vz, g.n[2]));
-        key[p] = k;
-    }
     const int lane = threadIdx.x & 31;
+    const int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * (32 * kKeyRuns) + lane;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *num_crowded = 0;
+    uint32_t k[kKeyRuns];
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < kKeyRuns; ++m) {
+        const int64_t p = base + 32 * m;
+        k[m] = 0;
+        if (p < n) {
+            const float vx = cell_coord(x[p], g.inv_dx);
+            const float vy = cell_coord(y[p], g.inv_dx);
+            const float vz = cell_coord(z[p], g.inv_dx);
+            bad |= !(coord_valid(vx, g.n[0]) && coord_valid(vy, g.n[1]) && coord_valid(vz, g.n[2]));
+            k[m] = cell_key(g, cell_index(vx, g.n[0]), cell_index(vy, g.n[1]),
+                            cell_index(vz, g.n[2]));
+            key[p] = k[m];
+        }
+    }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kFlagOutOfDomain);
-    unsigned active = __ballot_sync(0xffffffffu, live);
-    if (live) {
-        const unsigned peers = __match_any_sync(active, k);
-        const int leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (lane == leader) old = atomicAdd(&counts[k], (uint32_t)__popc(peers));
-        old = __shfl_sync(active, old, leader);
-        rank[p] = old + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    // runs of equal keys along the lane (the live particles are a prefix)
+    bool start[kKeyRuns];
+    uint32_t len[kKeyRuns], old[kKeyRuns];
+#pragma unroll
+    for (int m = 0; m < kKeyRuns; ++m)
+        start[m] = base + 32 * m < n && (m == 0 || k[m] != k[m - 1]);
+    len[kKeyRuns - 1] = base + 32 * (kKeyRuns - 1) < n ? 1u : 0u;
+#pragma unroll
+    for (int m = kKeyRuns - 2; m >= 0; --m) {
+        const bool cont = base + 32 * (m + 1) < n && !start[m + 1];  // run goes on at m + 1
+        len[m] = base + 32 * m < n ? (cont ? len[m + 1] + 1u : 1u) : 0u;
+    }
+#pragma unroll
+    for (int m = 0; m < kKeyRuns; ++m) old[m] = start[m] ? atomicAdd(&counts[k[m]], len[m]) : 0u;
+    uint32_t r = 0;
+#pragma unroll
+    for (int m = 0; m < kKeyRuns; ++m) {
+        const int64_t p = base + 32 * m;
+        if (p < n) {
+            r = start[m] ? old[m] : r + 1u;
+            rank[p] = r;
+        }
     }
 }
 
@@ -409,8 +437,8 @@ cudaError_t sort_particles(const GridGeom &g, int64_t num_keys, int64_t count, c
     SortScratch S;
     if (!take_sort_scratch(ws, count, num_keys, S)) return cudaErrorInvalidValue;
     if (!key) key = S.key;
-    k_keys<<<(int)((count + 255) / 256), 256, 0, s>>>(count, x, y, z, g, key, S.rank, cell_start,
-                                                      S.num_crowded, status);
+    k_keys<<<(int)((count + 256 * kKeyRuns - 1) / (256 * kKeyRuns)), 256, 0, s>>>(
+        count, x, y, z, g, key, S.rank, cell_start, S.num_crowded, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return finish_order(num_keys, count, key, cell_start, perm, layout, S, s);
 }
