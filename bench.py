@@ -66,6 +66,20 @@ def dist_env():
     return rank, world, local
 
 
+def job_throughput(torch, ms_local: float, units_per_rank: int, steps: int, world: int,
+                   device) -> tuple:
+    """Whole-job throughput of N independent replicas: the slowest rank's time
+    (max over ranks, an all_reduce on the process group when world > 1) and
+    the units all ranks processed per second over it, in millions."""
+    ms = ms_local
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * world * steps / (ms * 1e-3) / 1e6
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -546,13 +560,7 @@ def our_arm(args):
     barrier()
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
-    ms = main["total_ms"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = P * world * args.steps / (ms * 1e-3) / 1e6
+    ms, value = job_throughput(torch, main["total_ms"], P, args.steps, world, device)
     ms_step = ms / args.steps
 
     p2g_b, g2p_b = algorithmic_bytes(27, "f32")
@@ -607,11 +615,8 @@ def our_arm(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(pp, torch, scene, 27, args.e2e_steps, device, lanes=args.e2e_lanes)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e["ms_per_step"]], device=device)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e["value"] = P * world / (float(t.item()) * 1e-3) / 1e6
+        e2e["ms_per_step"], e2e["value"] = job_throughput(torch, e2e["ms_per_step"], P, 1, world,
+                                                          device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
