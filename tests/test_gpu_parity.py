@@ -225,6 +225,27 @@ def test_g2p_parity(R):
     assert pp.polypic_check_device_status(ctx) == 0
 
 
+def test_g2p_flags_non_finite_velocity():
+    """A NaN on the grid reaches the particles whose stencil covers it: G2P
+    latches NONFINITE in the device status (and the call itself succeeds);
+    the others' coefficients stay finite."""
+    sc = _scene(R=8, seed=13)
+    f = sc.fluid
+    ctx = pp.Context(sc.n, sc.dx, 8)
+    ps, ws = sorted_particles(ctx, f)
+    gv = random_grid_velocity(sc.n, sc.dx, seed=14)
+    i, j, k = 8, 5, 9                                  # a face-x node inside the fluid
+    gv[0][k, j, i] = np.nan
+    g = grid_from_host(ctx, vel=gv)
+    out = ctx.new_particles(ps.count)
+    pp.polypic_g2p(ctx, g, ps, out, 1e-3, ws)
+    assert pp.STATUS_NAMES[pp.polypic_check_device_status(ctx)] == "NONFINITE"
+    c = np_(out.coeff)
+    bad = ~np.isfinite(c).all(axis=(0, 1))
+    assert 0 < bad.sum() < 0.01 * ps.count              # only the particles around the node
+    assert pp.polypic_check_device_status(ctx) == 0       # reading clears the latch
+
+
 def _offset_particles(ctx, count, shift):
     """Output arrays whose first element sits `shift` elements past an
     allocation start, so that rows begin at every 16-byte phase."""
