@@ -290,31 +290,33 @@ __device__ __forceinline__ void reduce_node(const GridGeom &g, const uint8_t *s_
                                             const float *__restrict__ tile_base,
                                             float *__restrict__ gm, float *__restrict__ gp,
                                             float *__restrict__ gv, float dt, float ga,
-                                            bool accumulate) {
-    constexpr int X = tile_x(A), Y = tile_y(A), Z = tile_z(A);
-    const int64_t F = kTileFloats;
-    const AxisCand cx = axis_cand(i, ux, 8, X, g.tiles[0], F, 1, 1);
-    const AxisCand cy = axis_cand(j, uy, 8, Y, g.tiles[1], F * g.tiles[0], X, 3);
-    const AxisCand cz = axis_cand(k, uz, 4, Z, g.tiles[2], F * g.tiles[0] * g.tiles[1], X * Y, 9);
-    float m[8], v[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int az = c >> 2, ay = (c >> 1) & 1, ax = c & 1;
-        m[c] = v[c] = 0.0f;
-        if (cz.ok[az] && cy.ok[ay] && cx.ok[ax] &&
-            s_live[cz.live[az] + cy.live[ay] + cx.live[ax]]) {
-            const float *src = tile_base + (cz.part[az] + cy.part[ay] + cx.part[ax]);
-            m[c] = __ldg(src + tile_off(A, 0));
-            v[c] = __ldg(src + tile_off(A, 1));
-        }
-    }
+                                            bool accumulate, bool any_live) {
     // +0 starts the sum, so it is never -0 and the zeros of unused slots
     // leave it unchanged: the same bits as summing the used tiles alone
     float sm = 0.0f, sv = 0.0f;
+    if (any_live) {  // CTA-uniform: no tile around this one holds particles otherwise
+        constexpr int X = tile_x(A), Y = tile_y(A), Z = tile_z(A);
+        const int64_t F = kTileFloats;
+        const AxisCand cx = axis_cand(i, ux, 8, X, g.tiles[0], F, 1, 1);
+        const AxisCand cy = axis_cand(j, uy, 8, Y, g.tiles[1], F * g.tiles[0], X, 3);
+        const AxisCand cz = axis_cand(k, uz, 4, Z, g.tiles[2], F * g.tiles[0] * g.tiles[1], X * Y, 9);
+        float m[8], v[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        sm += m[c];
-        sv += v[c];
+        for (int c = 0; c < 8; ++c) {
+            const int az = c >> 2, ay = (c >> 1) & 1, ax = c & 1;
+            m[c] = v[c] = 0.0f;
+            if (cz.ok[az] && cy.ok[ay] && cx.ok[ax] &&
+                s_live[cz.live[az] + cy.live[ay] + cx.live[ax]]) {
+                const float *src = tile_base + (cz.part[az] + cy.part[ay] + cx.part[ax]);
+                m[c] = __ldg(src + tile_off(A, 0));
+                v[c] = __ldg(src + tile_off(A, 1));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            sm += m[c];
+            sv += v[c];
+        }
     }
     const int dX = g.n[0] + (A == 0), dY = g.n[1] + (A == 1);
     const int64_t idx = ((int64_t)k * dY + j) * dX + i;
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(256) k_p2g_reduce(GridGeom g, const uint8_t *_
                         vz < g.tiles[2];
         s_live[t] = in ? live[((uint32_t)vz * g.tiles[1] + vy) * g.tiles[0] + vx] : 0;
     }
-    __syncthreads();
+    const bool any_live = __syncthreads_or(t < 27 && s_live[t]);
     const int i = 8 * ux + (t & 7), j = 8 * uy + ((t >> 3) & 7), k = 4 * uz + (t >> 6);
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     // candidate offsets are relative to the owner tile, within +-1 tile of it
@@ -362,26 +364,26 @@ __global__ void __launch_bounds__(256) k_p2g_reduce(GridGeom g, const uint8_t *_
     // multiple of the tile): nodes beyond the face grid are not written
     if (i < nx + 1 && j < ny && k < nz)
         reduce_node<0>(g, s_live, ux, uy, uz, i, j, k, scratch, O.gm[0], O.gp[0], O.gv[0], dt,
-                       O.ga[0], accumulate);
+                       O.ga[0], accumulate, any_live);
     if (i < nx && j < ny + 1 && k < nz)
         reduce_node<1>(g, s_live, ux, uy, uz, i, j, k, scratch, O.gm[1], O.gp[1], O.gv[1], dt,
-                       O.ga[1], accumulate);
+                       O.ga[1], accumulate, any_live);
     if (i < nx && j < ny && k < nz + 1)
         reduce_node<2>(g, s_live, ux, uy, uz, i, j, k, scratch, O.gm[2], O.gp[2], O.gv[2], dt,
-                       O.ga[2], accumulate);
+                       O.ga[2], accumulate, any_live);
     // the wall layer n[A] lies one past the last tile when the tile size
     // divides n[A]: 8 x 4, 8 x 4 and 8 x 8 more nodes
     const int i8 = 8 * ux + (t & 7), j8 = 8 * uy + (t & 7);   // t < 32: 8 x 4
     const int k4 = 4 * uz + (t >> 3), j64 = 8 * uy + (t >> 3);  // t < 64: 8 x 8
     if (ux == g.tiles[0] - 1 && 8 * g.tiles[0] == nx && t < 32 && j8 < ny && k4 < nz)
         reduce_node<0>(g, s_live, ux, uy, uz, nx, j8, k4, scratch, O.gm[0], O.gp[0], O.gv[0],
-                       dt, O.ga[0], accumulate);
+                       dt, O.ga[0], accumulate, any_live);
     if (uy == g.tiles[1] - 1 && 8 * g.tiles[1] == ny && t < 32 && i8 < nx && k4 < nz)
         reduce_node<1>(g, s_live, ux, uy, uz, i8, ny, k4, scratch, O.gm[1], O.gp[1], O.gv[1], dt,
-                       O.ga[1], accumulate);
+                       O.ga[1], accumulate, any_live);
     if (uz == g.tiles[2] - 1 && 4 * g.tiles[2] == nz && t < 64 && i8 < nx && j64 < ny)
         reduce_node<2>(g, s_live, ux, uy, uz, i8, j64, nz, scratch, O.gm[2], O.gp[2], O.gv[2], dt,
-                       O.ga[2], accumulate);
+                       O.ga[2], accumulate, any_live);
 }
 
 // ---------------------------------------------------------------- built-in scratch
