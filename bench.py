@@ -179,6 +179,23 @@ def make_state(pp, ctx, scene, device):
     return a, b
 
 
+def state_stats(pp, torch, ps, dt, dx, steps_run):
+    """Stability of a state (reported, not gated: the paper found 27 fluid
+    modes unstable in coupled runs): the particle velocity c_p0 (decoded for
+    16-bit codes), its largest magnitude, the CFL number max |v| dt / dx, the
+    kinetic energy per particle and whether every coefficient is finite."""
+    c = ps.coeff.float()
+    v = c[:, 0, :]
+    if ps.scale is not None and ps.coeff.dtype != torch.float32:
+        v = v * ps.scale[None, :]
+    speed = torch.sqrt((v.double() ** 2).sum(dim=0))
+    vmax = float(speed.max().item()) if speed.numel() else 0.0
+    ke = float((0.5 * ps.mass.double() * speed ** 2).mean().item()) if speed.numel() else 0.0
+    return {"steps_run": steps_run, "max_speed_m_s": round(vmax, 4),
+            "cfl": round(vmax * dt / dx, 4), "kinetic_energy_per_particle_j": ke,
+            "finite": bool(torch.isfinite(c).all().item())}
+
+
 def run_variant(pp, torch, scene, R, fmt, steps, warmup, device, **ctx_opts):
     """Times `steps` calls of polypic_step (the whole path, as a user runs it),
     then `steps` steps made of the individual calls (sort, P2G, grid update,
@@ -233,7 +250,8 @@ def run_variant(pp, torch, scene, R, fmt, steps, warmup, device, **ctx_opts):
         ph[3] += evs[k][2].elapsed_time(evs[k][3])
     st = pp.polypic_check_device_status(ctx)
     return {"ctx": ctx, "count": src.count, "total_ms": total_ms,
-            "phase_ms": (ph / steps).tolist(), "status": pp.STATUS_NAMES.get(st)}
+            "phase_ms": (ph / steps).tolist(), "status": pp.STATUS_NAMES.get(st),
+            "stability": state_stats(pp, torch, src, scene.dt, scene.dx, warmup + 2 * steps)}
 
 
 class L2Flush:
@@ -647,6 +665,7 @@ def our_arm(args):
             "p2g_g2p_gbs": round(P * (pb + gb) / ((vph[1] + vph[3]) * 1e-3) / 1e9, 1),
             "speedup_vs_f32_step": round(ms_step / (r["total_ms"] / args.steps), 3),
             "speedup_vs_f32_p2g_g2p": round((ph[1] + ph[3]) / (vph[1] + vph[3]), 3),
+            "stability": r["stability"],
             "status": r["status"],
         }
         del r
@@ -693,6 +712,7 @@ def our_arm(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "device_status": main["status"],
+            "stability": main["stability"],
             "wall_s_headline": round(wall, 2),
         }
         print(json.dumps(line), flush=True)
