@@ -35,7 +35,7 @@ struct PcgBuffers {
     float *x, *r, *z, *d, *d2, *Ap, *diag, *wd;  // d / d2: directions (ping-pong), wd = omega / diag
     uint8_t *fluid;
     double *partial;  // [2][kPcgMaxBlocks]
-    double *scal;     // rz, rz_new, pAp, rr, bb, alpha, beta
+    double *scal;     // the scalars named by the enum below
 };
 
 // scal[]: rz of the current and the previous direction, pAp, |r|^2, |b|^2, rz
