@@ -391,8 +391,8 @@ __device__ __forceinline__ uint32_t round_slot(uint32_t bs, uint32_t n_c, uint32
 }
 
 // Rounds in flight per lane (cp.async groups).  Two measured fastest at 27
-// modes (four were 8% slower: the pipeline restarts for each component and
-// the prologue grows with the depth).
+// modes (three were 2% slower, four 8%: the ring takes shared memory from
+// L1).
 #ifndef POLYPIC_P2G_STAGES
 #define POLYPIC_P2G_STAGES 2
 #endif
