@@ -24,233 +24,9 @@
 //     tile order and writes the grids.
 #include <mutex>
 
-#include "p2g_kernel.cuh"
+#include "p2g_tiles.cuh"
 
 namespace polypic {
-
-constexpr int kP2GWarps = 8;
-
-template <int A> struct Reg {
-    static constexpr int X = reg_x(A), Y = reg_y(A), Z = reg_z(A);
-};
-
-// Index in block region A of node (ix, iy, iz) relative to the region origin.
-template <int A>
-__device__ __forceinline__ int region_index(int ix, int iy, int iz) {
-    return (iz * Reg<A>::Y + iy) * Reg<A>::X + ix;
-}
-
-template <int R, bool AFF = false> constexpr int p2g_smem_bytes() {
-    return (kP2GWarps * kRegionFloats + kP2GWarps * kStages * Stage<R, AFF>::NV * 32) * 4;
-}
-static_assert(p2g_smem_bytes<27>() <= 227 * 1024, "P2G staging exceeds the shared memory of a CTA");
-
-// The rounds of the three component passes form one stream (pass 0 rounds
-// 0 .. maxn-1, then pass 1, then pass 2) that flows through the stage ring
-// without draining: while a pass finishes and merges, the first rounds of the
-// next one are already in flight.  `ia` / `ir` name the next round to issue,
-// `sn` / `pn` its slot and particle index (loaded one round ahead).
-struct Pipe {
-    int ia;
-    uint32_t ir, sn, pn;
-    int ring;  // stage holding the next round to consume
-};
-
-template <int R, int FMT, bool ADJ, bool AFF>
-__device__ __forceinline__ void pipe_issue(const P2GArgs &P, Pipe &q, uint32_t bs, uint32_t n_c,
-                                           uint32_t maxn, unsigned lt, float *st, int lane) {
-    if (q.ia < 3 && n_c > q.ir) {  // q.ia is warp-uniform
-        if (q.ia == 0) stage_particle<R, FMT, 0, ADJ, AFF>(P, q.pn, q.sn, st, lane);
-        else if (q.ia == 1) stage_particle<R, FMT, 1, ADJ, AFF>(P, q.pn, q.sn, st, lane);
-        else stage_particle<R, FMT, 2, ADJ, AFF>(P, q.pn, q.sn, st, lane);
-    }
-    cp_async_commit();
-    if (q.ia < 3 && ++q.ir == maxn) {
-        q.ir = 0;
-        ++q.ia;
-    }
-    if (q.ia < 3) {
-        q.sn = round_slot(bs, n_c, q.ir, lt);
-        q.pn = n_c > q.ir ? P.perm[q.sn] : 0u;
-    }
-}
-
-template <int R, int FMT, int A, bool ADJ, bool AFF>
-__device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs, uint32_t n_c,
-                                         uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
-                                         int gk, int lane, float *reg, float *stage, bool &bad) {
-    using S = Stage<R, AFF>;
-    const bool interior = gi >= 1 && gi <= P.g.n[0] - 2 && gj >= 1 && gj <= P.g.n[1] - 2 &&
-                          gk >= 1 && gk <= P.g.n[2] - 2;
-    float am[4][3][3], av[4][3][3];
-#pragma unroll
-    for (int d = 0; d < 4; ++d)
-#pragma unroll
-        for (int kv = 0; kv < 3; ++kv)
-#pragma unroll
-            for (int kw = 0; kw < 3; ++kw) am[d][kv][kw] = av[d][kv][kw] = 0.0f;
-    const unsigned lt = (1u << lane) - 1u;
-    for (uint32_t r = 0; r < maxn; ++r) {
-        float *st = stage + q.ring * S::NV * 32;
-        cp_async_wait<kStages - 1>();
-        if (n_c > r) {
-            const float px = st[S::kX * 32 + lane], py = st[S::kY * 32 + lane],
-                        pz = st[S::kZ * 32 + lane];
-            float mt = st[S::kM * 32 + lane];
-            if (!ADJ && P.mass_abs) mt += st[S::kMabs * 32 + lane];
-            const float v0 = cell_coord(px, P.g.inv_dx), v1 = cell_coord(py, P.g.inv_dx),
-                        v2 = cell_coord(pz, P.g.inv_dx);
-            // in an interior cell, being in the cell implies the valid region
-            const bool ok = (interior || (coord_valid(v0, P.g.n[0]) && coord_valid(v1, P.g.n[1]) &&
-                                          coord_valid(v2, P.g.n[2]))) &&
-                            (int)floorf(v0) == gi && (int)floorf(v1) == gj && (int)floorf(v2) == gk;
-            if (ok) {
-                const float vu = A == 0 ? v0 : (A == 1 ? v1 : v2);
-                const float vv = A == 0 ? v1 : v0;
-                const float vw = A == 2 ? v1 : v2;
-                const Axis au = axis_decide(vu, true), av_ = axis_decide(vv, false),
-                           aw = axis_decide(vw, false);
-                const int cu = A == 0 ? gi : (A == 1 ? gj : gk);
-                const int shift = au.base - (cu - 1);
-                accumulate<R, FMT, A, ADJ, AFF>(P, st, lane, mt, shift, stencil_1d_scaled(au.t, P.s1, P.s2),
-                                           stencil_1d_scaled(av_.t, P.s1, P.s2), stencil_1d_scaled(aw.t, P.s1, P.s2), au.guard,
-                                           av_.guard, aw.guard, am, av, au.t, av_.t, aw.t);
-            } else {
-                bad = true;
-            }
-        }
-        // refill the stage just consumed with the next round of the stream
-        pipe_issue<R, FMT, ADJ, AFF>(P, q, bs, n_c, maxn, lt, st, lane);
-        q.ring = q.ring + 1 == kStages ? 0 : q.ring + 1;
-    }
-    // merge the 32 footprints into the block region, one node offset per phase
-    const int cu = A == 0 ? ci : (A == 1 ? cj : ck);
-    const int cv = A == 0 ? cj : ci;
-    const int cw = A == 2 ? cj : ck;
-    float *rm = reg + reg_off(A, 0);
-    float *rv = reg + reg_off(A, 1);
-#pragma unroll
-    for (int d = 0; d < 4; ++d)
-#pragma unroll
-        for (int kv = 0; kv < 3; ++kv)
-#pragma unroll
-            for (int kw = 0; kw < 3; ++kw) {
-                const int nu = cu + d, nv = cv + kv, nw = cw + kw;
-                const int ix = A == 0 ? nu : nv;
-                const int iy = A == 0 ? nv : (A == 1 ? nu : nw);
-                const int iz = A == 2 ? nu : nw;
-                const int idx = region_index<A>(ix, iy, iz);
-                rm[idx] += am[d][kv][kw];
-                rv[idx] += av[d][kv][kw];
-                __syncwarp();
-            }
-}
-
-// All three passes of one block: the prologue fills the ring once.
-template <int R, int FMT, bool ADJ, bool AFF>
-__device__ __forceinline__ void p2g_block(const P2GArgs &P, uint32_t bs, uint32_t n_c,
-                                          uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
-                                          int gk, int lane, float *reg, float *stage, bool &bad) {
-    const unsigned lt = (1u << lane) - 1u;
-    Pipe q;
-    q.ia = 0;
-    q.ir = 0;
-    q.ring = 0;
-    q.sn = round_slot(bs, n_c, 0, lt);
-    q.pn = n_c > 0 ? P.perm[q.sn] : 0u;
-#pragma unroll
-    for (int k = 0; k < kStages; ++k)
-        pipe_issue<R, FMT, ADJ, AFF>(P, q, bs, n_c, maxn, lt, stage + k * Stage<R, AFF>::NV * 32,
-                                     lane);
-    p2g_pass<R, FMT, 0, ADJ, AFF>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-    p2g_pass<R, FMT, 1, ADJ, AFF>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-    p2g_pass<R, FMT, 2, ADJ, AFF>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-    cp_async_wait<0>();
-}
-
-// Adds block region A of warp w into the tile region (written to dst).
-template <int A>
-__device__ __forceinline__ void merge_tile(const float *smem_regions, const bool *empty,
-                                           float *dst) {
-    constexpr int N = TileReg<A>::X * TileReg<A>::Y * TileReg<A>::Z;
-    for (int i = threadIdx.x; i < N; i += kP2GWarps * 32) {
-        const int lx = i % TileReg<A>::X, ly = (i / TileReg<A>::X) % TileReg<A>::Y,
-                  lz = i / (TileReg<A>::X * TileReg<A>::Y);
-        float sm = 0.0f, sv = 0.0f;
-#pragma unroll
-        for (int w = 0; w < kP2GWarps; ++w) {
-            if (empty[w]) continue;
-            const int bx = lx - 4 * (w & 1), by = ly - 4 * ((w >> 1) & 1), bz = lz - 2 * (w >> 2);
-            if (bx < 0 || bx >= Reg<A>::X || by < 0 || by >= Reg<A>::Y || bz < 0 || bz >= Reg<A>::Z)
-                continue;
-            const float *r = smem_regions + w * kRegionFloats;
-            const int idx = region_index<A>(bx, by, bz);
-            sm += r[reg_off(A, 0) + idx];
-            sv += r[reg_off(A, 1) + idx];
-        }
-        dst[tile_off(A, 0) + i] = sm;
-        dst[tile_off(A, 1) + i] = sv;
-    }
-}
-
-template <int R, int FMT, bool ADJ, bool AFF>
-// 27 modes keep the compiler's register allocation (one CTA per SM measured
-// faster); fewer modes fit two CTAs per SM without spills, except the
-// per-node evaluation of the affine map.
-__global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 || (AFF && R > 4) ? 1 : 2))
-    k_p2g_tiles(P2GArgs P) {
-    extern __shared__ float smem[];
-    __shared__ bool s_empty[kP2GWarps];
-    float *s_reg = smem;                                     // [8][kRegionFloats]
-    float *s_stage = smem + kP2GWarps * kRegionFloats;        // [8][kStages][NV][32]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t tile = blockIdx.x;
-    const bool tile_empty = P.cell_start[tile * 256] == P.cell_start[tile * 256 + 256];
-    if (threadIdx.x == 0) P.tile_live[tile] = tile_empty ? 0 : 1;
-    if (tile_empty) return;  // CTA-uniform
-
-    const uint32_t b = tile * kP2GWarps + warp;
-    const uint32_t k = b * 32 + lane;
-    const uint32_t cs0 = P.cell_start[k];
-    const uint32_t n_c = P.cell_start[k + 1] - cs0;
-    const uint32_t bs = P.cell_start[b * 32];
-    const uint32_t maxn = __reduce_max_sync(0xffffffffu, n_c);
-    float *reg = s_reg + warp * kRegionFloats;
-    float *stage = s_stage + warp * kStages * Stage<R, AFF>::NV * 32;
-    if (lane == 0) s_empty[warp] = maxn == 0;
-    if (maxn > 0) {
-        for (int i = lane; i < kRegionFloats; i += 32) reg[i] = 0.0f;
-        __syncwarp();
-        int i0, j0, k0;
-        block_origin(P.g, b, i0, j0, k0);
-        const int ci = lane & 3, cj = (lane >> 2) & 3, ck = lane >> 4;
-        const int gi = i0 + ci, gj = j0 + cj, gk = k0 + ck;
-        bool bad = false;
-        p2g_block<R, FMT, ADJ, AFF>(P, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
-        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.status, kFlagOutOfDomain);
-    }
-    __syncthreads();
-    float *dst = P.scratch + (size_t)tile * kTileFloats;
-    merge_tile<0>(s_reg, s_empty, dst);
-    merge_tile<1>(s_reg, s_empty, dst);
-    merge_tile<2>(s_reg, s_empty, dst);
-}
-
-template <int R, int FMT, bool ADJ, bool AFF = false>
-static cudaError_t launch_tiles(const P2GArgs &P, int grid, cudaStream_t s) {
-    const int smem = p2g_smem_bytes<R, AFF>();
-    static int configured_device = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (configured_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_p2g_tiles<R, FMT, ADJ, AFF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured_device = dev;
-    }
-    k_p2g_tiles<R, FMT, ADJ, AFF><<<grid, kP2GWarps * 32, smem, s>>>(P);
-    return cudaGetLastError();
-}
 
 // Candidate tiles of a node along one axis: node n (owner tile u, tile size
 // S, region width Wd, T tiles) lies in the regions of tiles u + o0 and, when
@@ -444,11 +220,7 @@ static cudaError_t reduce_tiles(const P2GArgs &P, float *gm[3], float *gp[3], fl
 cudaError_t p2g_adjoint_scatter(const P2GArgs &P, float *lv[3], bool accumulate, int R,
                                 cudaStream_t s) {
     const int grid = (int)(P.nblocks / kP2GWarps);
-    cudaError_t e = cudaErrorInvalidValue;
-    if (R == 1) e = launch_tiles<1, POLYPIC_COEFF_F32, true>(P, grid, s);
-    if (R == 4) e = launch_tiles<4, POLYPIC_COEFF_F32, true>(P, grid, s);
-    if (R == 8) e = launch_tiles<8, POLYPIC_COEFF_F32, true>(P, grid, s);
-    if (R == 27) e = launch_tiles<27, POLYPIC_COEFF_F32, true>(P, grid, s);
+    const cudaError_t e = launch_tiles_adj(P, R, grid, s);
     if (e != cudaSuccess) return e;
     return reduce_tiles(P, nullptr, lv, nullptr, 0.0f, nullptr, accumulate, s);
 }
@@ -461,30 +233,15 @@ cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], floa
         if (e != cudaSuccess) return e;
         return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
     }
-    cudaError_t e = cudaErrorInvalidValue;
+    cudaError_t e;
     if (P.affine) {  // Eq 12's affine map: FP32 coefficients, 4, 8 or 27 modes
         if (fmt != POLYPIC_COEFF_F32) return cudaErrorInvalidValue;
-        if (R == 4) e = launch_tiles<4, POLYPIC_COEFF_F32, false, true>(P, grid, s);
-        else if (R == 8) e = launch_tiles<8, POLYPIC_COEFF_F32, false, true>(P, grid, s);
-        else if (R == 27) e = launch_tiles<27, POLYPIC_COEFF_F32, false, true>(P, grid, s);
-        if (e != cudaSuccess) return e;
-        return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
+        e = launch_tiles_aff(P, R, grid, s);
+    } else if (fmt == POLYPIC_COEFF_F32) {
+        e = launch_tiles_f32(P, R, grid, s);
+    } else {
+        e = launch_tiles_16(P, R, fmt, grid, s);
     }
-#define POLYPIC_P2G_CASE(RR, FF) \
-    if (R == RR && fmt == FF) e = launch_tiles<RR, FF, false>(P, grid, s);
-    POLYPIC_P2G_CASE(1, POLYPIC_COEFF_F32)
-    POLYPIC_P2G_CASE(4, POLYPIC_COEFF_F32)
-    POLYPIC_P2G_CASE(8, POLYPIC_COEFF_F32)
-    POLYPIC_P2G_CASE(27, POLYPIC_COEFF_F32)
-    POLYPIC_P2G_CASE(1, POLYPIC_COEFF_BF16)
-    POLYPIC_P2G_CASE(4, POLYPIC_COEFF_BF16)
-    POLYPIC_P2G_CASE(8, POLYPIC_COEFF_BF16)
-    POLYPIC_P2G_CASE(27, POLYPIC_COEFF_BF16)
-    POLYPIC_P2G_CASE(1, POLYPIC_COEFF_F16)
-    POLYPIC_P2G_CASE(4, POLYPIC_COEFF_F16)
-    POLYPIC_P2G_CASE(8, POLYPIC_COEFF_F16)
-    POLYPIC_P2G_CASE(27, POLYPIC_COEFF_F16)
-#undef POLYPIC_P2G_CASE
     if (e != cudaSuccess) return e;
     return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
 }

@@ -1,0 +1,14 @@
+// p2g_tiles_adj.cu -- the tile kernels of the G2P adjoint scatter (fit factors, unit weight).
+#include "p2g_tiles.cuh"
+
+namespace polypic {
+
+cudaError_t launch_tiles_adj(const P2GArgs &P, int R, int grid, cudaStream_t s) {
+    if (R == 1) return launch_tiles<1, POLYPIC_COEFF_F32, true>(P, grid, s);
+    if (R == 4) return launch_tiles<4, POLYPIC_COEFF_F32, true>(P, grid, s);
+    if (R == 8) return launch_tiles<8, POLYPIC_COEFF_F32, true>(P, grid, s);
+    if (R == 27) return launch_tiles<27, POLYPIC_COEFF_F32, true>(P, grid, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace polypic
