@@ -17,7 +17,7 @@ FP64 CPU oracle timed on a bounded sample on the host.
 --impl reference times that oracle alone (the only reference available: the
 paper's own code is a CPU simulator that is not available here).
 --gpus N (under torchrun) runs N independent replicas, one per GPU: the
-transfers do not shard in this build, so no collective is involved.
+transfers are not sharded, so no collective is involved.
 """
 from __future__ import annotations
 

@@ -28,8 +28,8 @@
  * exactly as the library documents them, so that both sides take the same
  * decision; all arithmetic after the decision is FP64.
  *
- * Readings taken where the paper is silent or garbled (each also listed in
- * the design doc):
+ * Readings taken where the paper is silent or garbled (the library takes the
+ * same ones):
  *   - N(x) is the quadratic B-spline (Eq 14's dx^2/4 is its second moment).
  *   - Eq 14's printed symbols are read as g(z) = z^2 - (mu3/mu2) z - mu2, the
  *     Gram-Schmidt orthogonalisation of z^2 against {1, z} under the 1-D
