@@ -467,3 +467,40 @@ def test_step_replays_bit_identically_from_a_cuda_graph():
     for k in range(3):
         assert torch.equal(g2.vel[k], ref_v[k])
     assert pp.polypic_check_device_status(ctx) == 0
+
+
+def test_g2p_guard_band_matches_oracle():
+    """Particles in the band where a quadratic mode degenerates (q = 1 - 4t^2
+    < 2^-10, t within ~2e-4 of -1/2): on cell faces (centre grids) and cell
+    centres (the face grid) along each axis in turn.  The FP32 guard decision
+    and the zeroed quadratic coefficients agree with the oracle."""
+    sc = _scene(R=27, seed=19)
+    f = sc.fluid
+    rng = np.random.default_rng(20)
+    x = f.x.astype(np.float64).copy()
+    n = f.n
+    for axis in range(3):
+        sel = rng.choice(n, n // 8, replace=False)
+        cells = np.floor(x[axis, sel] / sc.dx)
+        off = np.where(rng.uniform(size=sel.size) < 0.5, 1.0, 0.5) + 1e-4
+        x[axis, sel] = (np.minimum(cells, sc.n[axis] - 3) + off) * sc.dx
+    x = x.astype(np.float32)
+    g_on = [np.count_nonzero(oracle.particle_modes(x[:, p], a, 27, sc.dx)[4])
+            for p in range(0, n, 97) for a in range(3)]
+    assert sum(g_on) > 0                                  # the band is populated
+    fg = scenes.ParticleSet(x=x, mass=f.mass, coeff=f.coeff, num_modes=27)
+    ctx = pp.Context(sc.n, sc.dx, 27)
+    ps, ws = sorted_particles(ctx, fg)
+    gv = random_grid_velocity(sc.n, sc.dx, seed=21)
+    g = grid_from_host(ctx, vel=gv)
+    out = ctx.new_particles(ps.count)
+    pp.polypic_g2p(ctx, g, ps, out, 1e-3, ws)
+    c_or, x_or = oracle.g2p(x, gv, 27, sc.n, sc.dx, 1e-3)
+    perm = oracle.particle_order(x, sc.n, sc.dx)[0]
+    c_or, x_or = c_or[:, :, perm], x_or[:, perm]
+    c_gpu = np_(out.coeff).astype(np.float64)
+    scale = (sc.dx ** scenes.mode_degrees(27))[None, :, None]
+    assert np.array_equal(c_gpu == 0.0, c_or == 0.0)       # the same coefficients zeroed
+    assert rel(c_gpu * scale, c_or * scale) < TOL
+    assert np.max(np.abs(np_(out.x) - x_or)) < 2e-7
+    assert pp.polypic_check_device_status(ctx) == 0
