@@ -71,4 +71,7 @@ def test_host_validation_without_gpu(lib):
     assert L.polypic_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
     cfg.apic_variant = 0
     assert L.polypic_p2g(None, None, None, None, 0, None) == 1
+    assert L.polypic_p2g_mapped(None, None, None, 1e-3, None, 0, None) == 1
+    assert L.polypic_p2g_mapped(None, None, None, float("nan"), None, 0, None) == 1
+    assert L.polypic_p2g_noalloc(None, None, None, None) == 1
     assert L.polypic_step(None, None, None, None, None, None, None, None, None, 0, None) == 1
