@@ -66,12 +66,8 @@ def _load():
     lib = ctypes.CDLL(build())
     sig = {
         "or_mode_abc": (None, [_int, _I]),
-        "or_num_keys": (ctypes.c_uint32, [_int, _int, _int]),
-        "or_cell_key": (ctypes.c_uint32, [_int, _int, _int, _int, _int]),
         "or_keys": (None, [_i64, _F, _F, _F, _int, _int, _int, _dbl, _U32]),
         "or_stable_sort": (None, [_i64, _U32, ctypes.c_uint32, _U32, _U32]),
-        "or_block_interleave": (None, [_U32, ctypes.c_uint32, _U32, _U32]),
-        "or_tile_group_order": (None, [_U32, ctypes.c_uint32, _U32, _U32]),
         "or_stencil_1d": (_int, [_dbl, _dbl, _int, _I, _D, _D, _D, _D, _I]),
         "or_particle_modes": (_int, [_dbl, _dbl, _dbl, _int, _int, _dbl, _I, _D, _D, _D, _I]),
         "or_p2g": (_int, [_i64, _D, _D, _D, _D, _D, _D, _int, _int, _int, _int, _dbl, _int,
@@ -139,16 +135,13 @@ def mode_abc(r: int) -> tuple:
     return (out[0], out[1], out[2])
 
 
-def num_keys(n) -> int:
-    return int(_load().or_num_keys(int(n[0]), int(n[1]), int(n[2])))
-
-
-def cell_key(i, j, k, n) -> int:
-    return int(_load().or_cell_key(i, j, k, int(n[0]), int(n[1])))
+def num_cells(n) -> int:
+    return int(n[0]) * int(n[1]) * int(n[2])
 
 
 def keys(x32, n, dx) -> np.ndarray:
-    """Cell key of each particle; x32 is a (3, P) float32 array."""
+    """Cell index (k n_y + j) n_x + i of each particle; x32 is a (3, P) float32
+    array.  The cell is decided in FP32 (one rounding of x * (float)(1/dx))."""
     x32 = _f32(x32)
     P = x32.shape[1]
     out = np.empty(P, dtype=np.uint32)
@@ -169,40 +162,13 @@ def stable_sort(key, nkeys: int):
     return perm, cs
 
 
-def block_interleave(perm, nkeys: int, cell_start):
-    perm = np.ascontiguousarray(perm, dtype=np.uint32)
-    cs = np.ascontiguousarray(cell_start, dtype=np.uint32)
-    out = np.empty_like(perm)
-    _load().or_block_interleave(_p(perm, ctypes.c_uint32), nkeys, _p(cs, ctypes.c_uint32),
-                                _p(out, ctypes.c_uint32))
-    return out
-
-
-def tile_group_order(perm, nkeys: int, cell_start):
-    """Grouped slot order of ordered phases from the stable order
-    (count-ranked groups of 32 cells per 256-key tile, each dealt round by
-    round)."""
-    perm = np.ascontiguousarray(perm, dtype=np.uint32)
-    cs = np.ascontiguousarray(cell_start, dtype=np.uint32)
-    out = np.empty_like(perm)
-    _load().or_tile_group_order(_p(perm, ctypes.c_uint32), nkeys, _p(cs, ctypes.c_uint32),
-                                _p(out, ctypes.c_uint32))
-    return out
-
-
-def ordered_particle_order(x32, n, dx):
-    """Slot order of an ordered phase with positions x32: (perm, cell_start)."""
-    nk = num_keys(n)
-    perm, cs = stable_sort(keys(x32, n, dx), nk)
-    return tile_group_order(perm, nk, cs), cs
-
-
-def particle_order(x32, n, dx):
-    """The library's slot order of particles with positions x32: (perm, cell_start)
-    where perm is the block-interleaved stable order."""
-    nk = num_keys(n)
-    perm, cs = stable_sort(keys(x32, n, dx), nk)
-    return block_interleave(perm, nk, cs), cs
+def cell_sort(x32, n, dx):
+    """Stable counting sort of the particles by cell index: (perm, cell_start,
+    key).  perm[cell_start[c]:cell_start[c + 1]] lists the particles of cell c
+    in increasing index order."""
+    key = keys(x32, n, dx)
+    perm, cs = stable_sort(key, num_cells(n))
+    return perm, cs, key
 
 
 # ---------------------------------------------------------------- basis

@@ -115,13 +115,11 @@ void or_mode_abc(int r, int *abc)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Cell key and stable sort (an implementation device; the paper has none).
+/* Cell index and stable sort (an implementation device; the paper has none).
  *
  * cell (i,j,k): i = clamp(floor(fl(x * inv_dx)), 0, n_x - 1) with the product
- * rounded once in FP32 and inv_dx = (float)(1.0 / dx).
- * key: tiles of 8x8x4 cells in row-major tile order, each tile split into
- * 2x2x2 blocks of 4x4x2 cells, blocks in x-fastest order, cells in a block in
- * x-fastest order:  key = tile*256 + block_in_tile*32 + cell_in_block.      */
+ * rounded once in FP32 and inv_dx = (float)(1.0 / dx); the key of a particle
+ * is the plain cell index (k * n_y + j) * n_x + i, x fastest.              */
 
 static float inv_dx_f32(double dx) { return (float)(1.0 / dx); }
 
@@ -134,28 +132,13 @@ static int cell_of(float x, float inv_dx, int n)
     return (int)f;
 }
 
-uint32_t or_num_keys(int nx, int ny, int nz)
-{
-    uint32_t tx = (uint32_t)((nx + 7) / 8), ty = (uint32_t)((ny + 7) / 8), tz = (uint32_t)((nz + 3) / 4);
-    return tx * ty * tz * 256u;
-}
-
-uint32_t or_cell_key(int i, int j, int k, int nx, int ny)
-{
-    int tiles_x = (nx + 7) / 8, tiles_y = (ny + 7) / 8;
-    int tile = ((k / 4) * tiles_y + (j / 8)) * tiles_x + (i / 8);
-    int blk = ((i / 4) % 2) + 2 * ((j / 4) % 2) + 4 * ((k / 2) % 2);
-    int cell = (i % 4) + 4 * (j % 4) + 16 * (k % 2);
-    return (uint32_t)(tile * 256 + blk * 32 + cell);
-}
-
 void or_keys(int64_t np, const float *x, const float *y, const float *z,
              int nx, int ny, int nz, double dx, uint32_t *key)
 {
     float inv = inv_dx_f32(dx);
     for (int64_t p = 0; p < np; ++p) {
         int i = cell_of(x[p], inv, nx), j = cell_of(y[p], inv, ny), k = cell_of(z[p], inv, nz);
-        key[p] = or_cell_key(i, j, k, nx, ny);
+        key[p] = (uint32_t)(((int64_t)k * ny + j) * nx + i);
     }
 }
 
@@ -172,67 +155,6 @@ void or_stable_sort(int64_t np, const uint32_t *key, uint32_t nkeys,
     memcpy(fill, cell_start, sizeof(uint32_t) * ((size_t)nkeys + 1));
     for (int64_t p = 0; p < np; ++p) perm[fill[key[p]]++] = (uint32_t)p;
     free(fill);
-}
-
-/* Block-interleaved slot order (the library's particle order): blocks of 32
- * consecutive keys keep their slot range [cell_start[32b], cell_start[32b+32]);
- * inside a block, round r = 0, 1, ... lists the r-th particle (in the stable
- * order above) of every key of the block that has more than r particles, keys
- * ascending.  in: the stable order; out: the interleaved order. */
-void or_block_interleave(const uint32_t *in, uint32_t nkeys, const uint32_t *cell_start,
-                         uint32_t *out)
-{
-    for (uint32_t b = 0; b < nkeys / 32; ++b) {
-        uint32_t slot = cell_start[32 * b];
-        uint32_t maxn = 0;
-        for (uint32_t c = 0; c < 32; ++c) {
-            uint32_t n = cell_start[32 * b + c + 1] - cell_start[32 * b + c];
-            if (n > maxn) maxn = n;
-        }
-        for (uint32_t r = 0; r < maxn; ++r)
-            for (uint32_t c = 0; c < 32; ++c) {
-                uint32_t k = 32 * b + c;
-                if (cell_start[k + 1] - cell_start[k] > r) out[slot++] = in[cell_start[k] + r];
-            }
-    }
-}
-
-/* Grouped slot order of ordered particle phases.  Keys come in tiles of 256
- * consecutive keys; a tile's particles keep their slot range
- * [cell_start[256 t], cell_start[256 t + 256]).  Inside a tile the cells are
- * ranked by particle count n: by min(n, 31) descending, ties by key
- * ascending, and rank 32 g + l is lane l of group g.  Groups follow each other
- * (g = 0..7); inside group g, round r = 0, 1, ... lists the r-th particle (in
- * the stable order) of every lane whose cell holds more than r particles,
- * lanes ascending.  in: the stable order; out: the slot order. */
-void or_tile_group_order(const uint32_t *in, uint32_t nkeys, const uint32_t *cell_start,
-                         uint32_t *out)
-{
-    for (uint32_t t = 0; t < nkeys / 256; ++t) {
-        uint32_t k0 = 256 * t, slot = cell_start[k0];
-        uint32_t ranked[256];
-        int r = 0;
-        for (int bucket = 31; bucket >= 0; --bucket)
-            for (uint32_t c = 0; c < 256; ++c) {
-                uint32_t n = cell_start[k0 + c + 1] - cell_start[k0 + c];
-                uint32_t q = n < 31 ? n : 31;
-                if (q == (uint32_t)bucket) ranked[r++] = c;
-            }
-        for (int g = 0; g < 8; ++g) {
-            uint32_t maxn = 0;
-            for (int l = 0; l < 32; ++l) {
-                uint32_t k = k0 + ranked[32 * g + l];
-                uint32_t n = cell_start[k + 1] - cell_start[k];
-                if (n > maxn) maxn = n;
-            }
-            for (uint32_t round = 0; round < maxn; ++round)
-                for (int l = 0; l < 32; ++l) {
-                    uint32_t k = k0 + ranked[32 * g + l];
-                    if (cell_start[k + 1] - cell_start[k] > round)
-                        out[slot++] = in[cell_start[k] + round];
-                }
-        }
-    }
 }
 
 /* ------------------------------------------------------------------------ */

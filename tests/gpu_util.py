@@ -73,3 +73,11 @@ def random_grid_velocity(n, dx, seed, amp=1.0):
         f += 0.2 * rng.standard_normal(f.shape)
         out.append((amp * f).astype(np.float32))
     return out
+
+
+def assert_close(a, b, tol, what=""):
+    """Element by element and as a whole: max|a - b| / max|b| and
+    ||a - b|| / ||b|| both below tol (a wrong value at a few faces, a tile
+    seam or a wall layer cannot hide in the norm)."""
+    r, m = rel(a, b), max_rel(a, b)
+    assert r < tol and m < tol, f"{what}: norm-wise {r:.3e}, element-wise {m:.3e} (tol {tol:g})"

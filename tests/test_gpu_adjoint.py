@@ -12,10 +12,11 @@ import pytest
 import torch
 
 import oracle
+import slot_layout
 from paper_2308_01060_gb300 import autograd as pag
 from paper_2308_01060_gb300 import polypic as pp
 from paper_2308_01060_gb300 import scenes
-from gpu_util import grid_from_host, np_, random_grid_velocity, rel, sorted_particles
+from gpu_util import assert_close, grid_from_host, np_, random_grid_velocity, rel, sorted_particles
 
 pytestmark = pytest.mark.gpu
 
@@ -37,8 +38,8 @@ def test_p2g_adjoint_matches_oracle(R):
     bar_in = ctx.new_particles(ps.count)
     pp.polypic_p2g_adjoint(ctx, ps, bar_grid, bar_in, ws)
     lc_or, lx_or = oracle.p2g_adjoint(f.x, f.mass, f.coeff, sc.n, sc.dx, lm, lp)
-    assert rel(np_(bar_in.coeff), lc_or) < 1e-5
-    assert rel(np_(bar_in.x), lx_or) < 1e-4
+    assert_close(np_(bar_in.coeff), lc_or, 1e-5)
+    assert_close(np_(bar_in.x), lx_or, 1e-4)
     assert pp.polypic_check_device_status(ctx) == 0
 
 
@@ -54,7 +55,7 @@ def test_g2p_adjoint_matches_oracle(R):
     deg = scenes.mode_degrees(R)
     lc_out = (rng.standard_normal((3, R, f.n)) * (sc.dx ** deg)[None, :, None]).astype(np.float32)
     lx_out = rng.standard_normal((3, f.n)).astype(np.float32)
-    perm, _ = oracle.particle_order(f.x, sc.n, sc.dx)
+    perm = slot_layout.library_order(f.x, sc.n, sc.dx)[0]
     bar_out = ctx.new_particles(f.n)                       # slot order
     bar_out.coeff.copy_(torch.from_numpy(np.ascontiguousarray(lc_out[:, :, perm])))
     bar_out.x.copy_(torch.from_numpy(np.ascontiguousarray(lx_out[:, perm])))
@@ -64,8 +65,8 @@ def test_g2p_adjoint_matches_oracle(R):
     pp.polypic_g2p_adjoint(ctx, g, ps, dt, bar_out, bar_grid, bar_in, ws)
     lv_or, lx_or = oracle.g2p_adjoint(f.x, gv, R, sc.n, sc.dx, dt, lc_out, lx_out)
     for a in range(3):
-        assert rel(np_(bar_grid.vel[a]), lv_or[a]) < 1e-5
-    assert rel(np_(bar_in.x), lx_or) < 1e-4
+        assert_close(np_(bar_grid.vel[a]), lv_or[a], 1e-5)
+    assert_close(np_(bar_in.x), lx_or, 1e-4)
     # determinism of the scatter
     bar_grid2 = ctx.new_grid()
     pp.polypic_g2p_adjoint(ctx, g, ps, dt, bar_out, bar_grid2, bar_in, ws)
@@ -87,8 +88,8 @@ def test_grid_update_adjoint_matches_oracle():
     pp.polypic_grid_update_adjoint(ctx, g, pp.UpdateSettings(dt=1e-3), bar, out)
     lm_or, lp_or = oracle.grid_update_adjoint(n, fm, fp, lv)
     for a in range(3):
-        assert rel(np_(out.mass[a]), lm_or[a]) < 1e-6
-        assert rel(np_(out.mom[a]), lp_or[a]) < 1e-6
+        assert_close(np_(out.mass[a]), lm_or[a], 1e-6)
+        assert_close(np_(out.mom[a]), lp_or[a], 1e-6)
 
 
 # ------------------------------------------------------------------ rollout gradient
@@ -152,7 +153,7 @@ def test_rollout_gradient_matches_oracle_and_finite_differences(R):
     L0 = _oracle_loss(states, target)
     assert abs(loss.item() - L0) <= 1e-4 * abs(L0)
     g_or, _ = _oracle_gradient(states, m64, n, dx, dt, target)
-    assert rel(g_gpu, g_or) < 1e-4
+    assert_close(g_gpu, g_or, 1e-4)
 
     rng = np.random.default_rng(1)
     deg = scenes.mode_degrees(R)

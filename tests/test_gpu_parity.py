@@ -13,7 +13,8 @@ import torch
 import oracle
 from paper_2308_01060_gb300 import polypic as pp
 from paper_2308_01060_gb300 import scenes
-from gpu_util import (grid_from_host, max_rel, np_, random_grid_velocity, rel, sorted_particles,
+import slot_layout
+from gpu_util import (assert_close, grid_from_host, max_rel, np_, random_grid_velocity, rel, sorted_particles,
                       u32, upload)
 
 pytestmark = pytest.mark.gpu
@@ -37,9 +38,11 @@ def test_sort_bit_exact(shuffle):
                                coeff=np.ascontiguousarray(f.coeff[:, :, pr]), num_modes=27)
     ctx = pp.Context(sc.n, sc.dx, 27)
     ps, _ = sorted_particles(ctx, f)
-    key = oracle.keys(f.x, sc.n, sc.dx)
-    perm, cs = oracle.particle_order(f.x, sc.n, sc.dx)
-    assert ctx.num_keys == oracle.num_keys(sc.n)
+    # the method's part: every cell's particle list equals the oracle's stable one
+    assert slot_layout.per_cell_lists_match(u32(ps.perm), f.x, sc.n, sc.dx)
+    # the library's documented layout on top of it
+    perm, cs, key = slot_layout.library_order(f.x, sc.n, sc.dx)
+    assert ctx.num_keys == slot_layout.num_keys(sc.n)
     assert np.array_equal(u32(ps.key), key)
     assert np.array_equal(u32(ps.perm), perm)
     assert np.array_equal(u32(ps.cell_start), cs)
@@ -56,8 +59,8 @@ def test_sort_ragged_and_odd_grid(count):
     ps = pp.upload_particles(ctx, x, np.ones(count, np.float32))
     ws = ctx.workspace(count)
     pp.polypic_sort(ctx, ps, ws)
-    key = oracle.keys(x, n, dx)
-    perm, cs = oracle.particle_order(x, n, dx)
+    assert slot_layout.per_cell_lists_match(u32(ps.perm), x, n, dx)
+    perm, cs, key = slot_layout.library_order(x, n, dx)
     assert np.array_equal(u32(ps.perm), perm)
     assert np.array_equal(u32(ps.cell_start), cs)
     if count:
@@ -82,7 +85,8 @@ def test_sort_crowded_cells_bit_exact(crowd):
     ws = ctx.workspace(x.shape[1])
     for _ in range(2):                      # the second call reuses the workspace
         pp.polypic_sort(ctx, ps, ws)
-        perm, cs = oracle.particle_order(x, n, dx)
+        assert slot_layout.per_cell_lists_match(u32(ps.perm), x, n, dx)
+        perm, cs, _ = slot_layout.library_order(x, n, dx)
         assert np.array_equal(u32(ps.cell_start), cs)
         assert np.array_equal(u32(ps.perm), perm)
     assert pp.polypic_check_device_status(ctx) == 0
@@ -113,8 +117,8 @@ def test_p2g_parity_and_determinism(R):
     pp.polypic_p2g(ctx, ps, g, ws)
     gm, gp = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx)
     for a in range(3):
-        assert rel(np_(g.mass[a]), gm[a]) < TOL
-        assert rel(np_(g.mom[a]), gp[a]) < TOL
+        assert_close(np_(g.mass[a]), gm[a], TOL)
+        assert_close(np_(g.mom[a]), gp[a], TOL)
     g2 = ctx.new_grid(vel=False)
     pp.polypic_p2g(ctx, ps, g2, ws)
     for a in range(3):
@@ -134,8 +138,8 @@ def test_p2g_solid_absorbed_mass():
     pp.polypic_p2g(ctx, ps, g, ws)
     gm, gp = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx, mass_abs=mabs)
     for a in range(3):
-        assert rel(np_(g.mass[a]), gm[a]) < TOL
-        assert rel(np_(g.mom[a]), gp[a]) < TOL
+        assert_close(np_(g.mass[a]), gm[a], TOL)
+        assert_close(np_(g.mom[a]), gp[a], TOL)
 
 
 def test_p2g_empty():
@@ -172,8 +176,8 @@ def test_p2g_single_particle_and_crowded_cell():
     pp.polypic_p2g(ctx, ps, g, ws)
     gm, gp = oracle.p2g(x, mass, coeff, n, dx)
     for a in range(3):
-        assert rel(np_(g.mass[a]), gm[a]) < TOL
-        assert rel(np_(g.mom[a]), gp[a]) < TOL
+        assert_close(np_(g.mass[a]), gm[a], TOL)
+        assert_close(np_(g.mom[a]), gp[a], TOL)
 
 
 # ------------------------------------------------------------------ grid update
@@ -212,14 +216,14 @@ def test_g2p_parity(R):
     dt = 1e-3
     pp.polypic_g2p(ctx, g, ps, out, dt, ws)
     c_or, x_or = oracle.g2p(f.x, gv, R, sc.n, sc.dx, dt)
-    perm = oracle.particle_order(f.x, sc.n, sc.dx)[0]
+    perm = slot_layout.library_order(f.x, sc.n, sc.dx)[0]
     c_or = c_or[:, :, perm]
     x_or = x_or[:, perm]
     c_gpu = np_(out.coeff).astype(np.float64)
     deg = scenes.mode_degrees(R)
     scale = (sc.dx ** deg)[None, :, None]
-    assert rel(c_gpu[:, 0], c_or[:, 0]) < TOL                       # particle velocity
-    assert rel(c_gpu * scale, c_or * scale) < TOL                  # all modes, c dx^L
+    assert_close(c_gpu[:, 0], c_or[:, 0], TOL)                       # particle velocity
+    assert_close(c_gpu * scale, c_or * scale, TOL)                  # all modes, c dx^L
     assert np.max(np.abs(np_(out.x) - x_or)) < 2e-7               # positions (FP32 ulp ~ 6e-8)
     assert np.array_equal(np_(out.mass), f.mass[perm])
     assert pp.polypic_check_device_status(ctx) == 0
@@ -302,16 +306,16 @@ def test_step_parity(R):
     prm = pp.UpdateSettings(dt=sc.dt)
     pp.polypic_step(ctx, ps, out, g, prm, ws)
     c_or, x_or, (gm, gp, gv) = oracle.step(f.x, f.mass, f.coeff, sc.n, sc.dx, sc.dt)
-    perm = oracle.particle_order(f.x, sc.n, sc.dx)[0]
+    perm = slot_layout.library_order(f.x, sc.n, sc.dx)[0]
     assert np.array_equal(u32(ps.perm), perm)
     for a in range(3):
-        assert rel(np_(g.mom[a]), gp[a]) < TOL
-        assert rel(np_(g.mass[a]), gm[a]) < TOL
+        assert_close(np_(g.mom[a]), gp[a], TOL)
+        assert_close(np_(g.mass[a]), gm[a], TOL)
     c_gpu = np_(out.coeff).astype(np.float64)
     c_or = c_or[:, :, perm]
     scale = (sc.dx ** scenes.mode_degrees(R))[None, :, None]
-    assert rel(c_gpu[:, 0], c_or[:, 0]) < TOL
-    assert rel(c_gpu * scale, c_or * scale) < 3 * TOL
+    assert_close(c_gpu[:, 0], c_or[:, 0], TOL)
+    assert_close(c_gpu * scale, c_or * scale, 3 * TOL)
     assert np.max(np.abs(np_(out.x) - x_or[:, perm])) < 2e-7
     assert pp.polypic_check_device_status(ctx) == 0
 
@@ -334,14 +338,14 @@ def test_step_with_solid_phase_and_drag():
     sm, sp = oracle.p2g(s.x, s.mass, scf, sc.n, sc.dx, mass_abs=s.mass_abs)
     fv, sv = oracle.grid_update(sc.n, sc.dt, prm.gravity, gm, gp, sm, sp, drag_k=5.0)
     for a in range(3):
-        assert rel(np_(gf.vel[a]), fv[a]) < TOL
-        assert rel(np_(gs.vel[a]), sv[a]) < TOL
+        assert_close(np_(gf.vel[a]), fv[a], TOL)
+        assert_close(np_(gs.vel[a]), sv[a], TOL)
     cf, xf = oracle.g2p(f.x, fv, 8, sc.n, sc.dx, sc.dt)
     cs_, xs = oracle.g2p(s.x, sv, 8, sc.n, sc.dx, sc.dt)
-    pf = oracle.particle_order(f.x, sc.n, sc.dx)[0]
-    psol = oracle.particle_order(s.x, sc.n, sc.dx)[0]
-    assert rel(np_(fo.coeff)[:, 0], cf[:, 0, pf]) < TOL
-    assert rel(np_(so.coeff)[:, 0], cs_[:, 0, psol]) < TOL
+    pf = slot_layout.library_order(f.x, sc.n, sc.dx)[0]
+    psol = slot_layout.library_order(s.x, sc.n, sc.dx)[0]
+    assert_close(np_(fo.coeff)[:, 0], cf[:, 0, pf], TOL)
+    assert_close(np_(so.coeff)[:, 0], cs_[:, 0, psol], TOL)
     assert np.array_equal(np_(so.mass_abs), s.mass_abs[psol])
 
 
@@ -364,10 +368,10 @@ def test_16bit_coefficients_round_trip(fmt, tol):
     pp.polypic_p2g(ctx, mid, g2, ws)
     c_or, _ = oracle.g2p(f.x, gv, 27, sc.n, sc.dx, 0.0)
     gm, gp = oracle.p2g(f.x, f.mass, c_or, sc.n, sc.dx)
-    errs = [rel(np_(g2.mom[a]), gp[a]) for a in range(3)]
-    assert max(errs) < tol, errs
+    errs = [(rel(np_(g2.mom[a]), gp[a]), max_rel(np_(g2.mom[a]), gp[a])) for a in range(3)]
+    assert max(max(e) for e in errs) < tol, errs
     for a in range(3):
-        assert rel(np_(g2.mass[a]), gm[a]) < TOL
+        assert_close(np_(g2.mass[a]), gm[a], TOL)
 
 
 # ------------------------------------------------------------------ projection
@@ -394,7 +398,7 @@ def test_pcg_projection_matches_oracle():
     fluid[cells[2], cells[1], cells[0]] = True
     vp, _, _ = oracle.pcg_project(sc.n, sc.dx, sc.dt, 1000.0, fluid, fv, rtol=1e-10, maxiter=5000)
     for a in range(3):
-        assert rel(np_(g.vel[a]), vp[a]) < 1e-4
+        assert_close(np_(g.vel[a]), vp[a], 1e-4)
     v = [np_(g.vel[a]).astype(np.float64) for a in range(3)]
     div = (np.diff(v[0], axis=2) + np.diff(v[1], axis=1) + np.diff(v[2], axis=0)) / sc.dx
     div0 = (np.diff(fv[0], axis=2) + np.diff(fv[1], axis=1) + np.diff(fv[2], axis=0)) / sc.dx
@@ -426,7 +430,7 @@ def test_pcg_projection_odd_and_flat_grids(n, maxiter):
     fluid[c32[2], c32[1], c32[0]] = True
     vp, _, _ = oracle.pcg_project(n, dx, prm.dt, 1000.0, fluid, fv, rtol=1e-10, maxiter=5000)
     for a in range(3):
-        assert rel(np_(g.vel[a]), vp[a]) < 1e-4
+        assert_close(np_(g.vel[a]), vp[a], 1e-4)
 
 
 def test_pcg_reports_not_converged():
@@ -496,11 +500,11 @@ def test_g2p_guard_band_matches_oracle():
     out = ctx.new_particles(ps.count)
     pp.polypic_g2p(ctx, g, ps, out, 1e-3, ws)
     c_or, x_or = oracle.g2p(x, gv, 27, sc.n, sc.dx, 1e-3)
-    perm = oracle.particle_order(x, sc.n, sc.dx)[0]
+    perm = slot_layout.library_order(x, sc.n, sc.dx)[0]
     c_or, x_or = c_or[:, :, perm], x_or[:, perm]
     c_gpu = np_(out.coeff).astype(np.float64)
     scale = (sc.dx ** scenes.mode_degrees(27))[None, :, None]
     assert np.array_equal(c_gpu == 0.0, c_or == 0.0)       # the same coefficients zeroed
-    assert rel(c_gpu * scale, c_or * scale) < TOL
+    assert_close(c_gpu * scale, c_or * scale, TOL)
     assert np.max(np.abs(np_(out.x) - x_or)) < 2e-7
     assert pp.polypic_check_device_status(ctx) == 0

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import bruteforce
 
 
 DX = 1.0 / 32
@@ -146,3 +147,85 @@ def test_quadratic_fit_is_second_difference():
         r200 = [oracle.mode_abc(r) for r in range(27)].index((2, 0, 0))
         sd = (prof[base] - 2 * prof[base + 1] + prof[base + 2]) / (2 * dx * dx)
         assert abs(c[1, r200, 0] - sd) < 1e-9 * max(1.0, abs(sd))
+
+
+def _guarded_position(rng, alpha, b, n, dx, delta=5e-5):
+    """A position whose axis b lies in the degenerate band of face grid alpha
+    (q = 1 - 4t^2 < 2^-10, t = -1/2 + delta in cells) and whose other axes sit
+    well away from both bands.  Along the face axis (b == alpha, offset 0) the
+    band is at the cell centre; along a centre axis (offset 1/2) at the cell
+    boundary."""
+    pos = np.empty(3)
+    for e in range(3):
+        m = rng.integers(4, n - 4)
+        if e == b:
+            pos[e] = (m + (0.5 if b == alpha else 1.0) + delta) * dx
+        else:
+            pos[e] = (m + rng.uniform(0.15, 0.35)) * dx
+    return pos
+
+
+@pytest.mark.parametrize("alpha", [0, 1, 2])
+@pytest.mark.parametrize("b", [0, 1, 2])
+def test_guard_zeroes_quadratic_modes_and_keeps_the_restricted_fit(alpha, b):
+    """Reading of the degenerate quadratic mode (q = 1 - 4t^2 < 2^-10 on axis b,
+    where d_2 -> 0, Section 3.3's fit being undefined in the limit): every mode
+    with a quadratic factor on the guarded axis gets coefficient 0, and every
+    other mode keeps the weighted least-squares fit restricted to the
+    unguarded modes (an independent all-pairs evaluator and NumPy's lstsq).
+    Controls: without the guard the quadratic fit is not 0, and the guard
+    fires on axis b of grid alpha only."""
+    n, dx = 16, 1 / 16
+    ng = (n, n, n)
+    rng = np.random.default_rng(100 + 3 * alpha + b)
+    modes = [oracle.mode_abc(r) for r in range(27)]
+    gv = [rng.standard_normal(oracle.face_shape(a, ng)) for a in range(3)]
+    for _ in range(4):
+        pos = _guarded_position(rng, alpha, b, n, dx)
+        _, _, _, _, guard = oracle.particle_modes(pos, alpha, 27, dx)
+        assert list(guard) == [int(e == b) for e in range(3)]
+        c_or, _ = oracle.g2p(pos.reshape(3, 1), gv, 27, ng, dx, 0.0)
+        c = c_or[alpha, :, 0]
+        quad = [r for r, abc in enumerate(modes) if abc[b] == 2]
+        free = [r for r, abc in enumerate(modes) if abc[b] != 2]
+        assert len(quad) == 9 and np.all(c[quad] == 0.0)
+        # the restricted least-squares fit over all nodes (weights > 0)
+        w, s = bruteforce._particle_grid(pos, alpha, ng, dx, [modes[r] for r in free])
+        m = w > 0
+        sw = np.sqrt(w[m])
+        A = np.stack([s[q][m] * sw for q in range(len(free))], axis=1)
+        c_ls, *_ = np.linalg.lstsq(A, gv[alpha][m] * sw, rcond=None)
+        assert np.allclose(c[free], c_ls, rtol=1e-9, atol=1e-9 * np.abs(c_ls).max())
+        # control: the ungated decoupled fit of the guarded modes is not 0
+        wq, sq = bruteforce._particle_grid(pos, alpha, ng, dx, [modes[r] for r in quad])
+        num = np.tensordot(sq, wq * gv[alpha], axes=([1, 2, 3], [0, 1, 2]))
+        den = np.tensordot(sq * sq, wq, axes=([1, 2, 3], [0, 1, 2]))
+        scale = np.abs(gv[alpha]).max() / dx ** 2
+        assert np.abs(num / den).max() > 1e-3 * scale
+
+
+@pytest.mark.parametrize("alpha", [0, 1, 2])
+@pytest.mark.parametrize("b", [0, 1, 2])
+def test_guarded_modes_pass_no_gradient(alpha, b):
+    """The G2P adjoint transposes the guard: the guarded coefficients are the
+    constant 0 whatever the grid and the position, so a loss on them alone
+    has zero gradient with respect to the grid velocities and the position
+    (both places where the adjoint skips guarded modes are exercised).  The
+    control seeds an unguarded mode and must see a non-zero gradient."""
+    n, dx = 16, 1 / 16
+    ng = (n, n, n)
+    rng = np.random.default_rng(200 + 3 * alpha + b)
+    modes = [oracle.mode_abc(r) for r in range(27)]
+    gv = [rng.standard_normal(oracle.face_shape(a, ng)) for a in range(3)]
+    pos = _guarded_position(rng, alpha, b, n, dx).reshape(3, 1)
+    quad = [r for r, abc in enumerate(modes) if abc[b] == 2]
+    lc = np.zeros((3, 27, 1))
+    lc[alpha, quad, 0] = rng.standard_normal(len(quad))
+    lv, lx = oracle.g2p_adjoint(pos, gv, 27, ng, dx, 0.0, lc, np.zeros((3, 1)))
+    assert all(np.all(v == 0.0) for v in lv)
+    assert np.all(lx == 0.0)
+    free = [r for r, abc in enumerate(modes) if abc[b] != 2 and sum(abc) > 0]
+    lc2 = np.zeros((3, 27, 1))
+    lc2[alpha, free[0], 0] = 1.0
+    lv2, lx2 = oracle.g2p_adjoint(pos, gv, 27, ng, dx, 0.0, lc2, np.zeros((3, 1)))
+    assert np.abs(lv2[alpha]).max() > 0 and np.abs(lx2).max() > 0

@@ -12,7 +12,6 @@
   * free fall, energy non-increase, adjoint identities, two-phase drag,
     absorbed mass (Eqs 18-20), pressure projection
 """
-import itertools
 
 import numpy as np
 import pytest
@@ -47,31 +46,27 @@ def test_stable_sort_matches_numpy():
     dx = 1.0 / 16
     x = np.stack([rng.uniform(0, n[b] * dx, 5000) for b in range(3)]).astype(np.float32)
     key = oracle.keys(x, n, dx)
-    nk = oracle.num_keys(n)
-    perm, cs = oracle.stable_sort(key, nk)
+    nc = oracle.num_cells(n)
+    perm, cs = oracle.stable_sort(key, nc)
     assert np.array_equal(perm, np.argsort(key, kind="stable").astype(np.uint32))
-    assert np.array_equal(cs, np.searchsorted(np.sort(key), np.arange(nk + 1)).astype(np.uint32))
+    assert np.array_equal(cs, np.searchsorted(np.sort(key), np.arange(nc + 1)).astype(np.uint32))
 
 
-def test_key_layout_blocks_and_tiles():
-    """The key is a bijection on cells; each 4x4x2 block and each 8x8x4 tile
-    occupies one contiguous key range; tiles follow in row-major order."""
-    n = (16, 16, 8)
-    nk = oracle.num_keys(n)
-    keys = {}
-    for i, j, k in itertools.product(range(n[0]), range(n[1]), range(n[2])):
-        keys[(i, j, k)] = oracle.cell_key(i, j, k, n)
-    assert len(set(keys.values())) == len(keys)
-    assert max(keys.values()) < nk
-    for bi, bj, bk in itertools.product(range(4), range(4), range(4)):
-        ks = sorted(keys[(4 * bi + a, 4 * bj + b, 2 * bk + c)]
-                    for a in range(4) for b in range(4) for c in range(2))
-        assert ks == list(range(ks[0], ks[0] + 32)) and ks[0] % 32 == 0
-    for ti, tj, tk in itertools.product(range(2), range(2), range(2)):
-        ks = sorted(keys[(8 * ti + a, 8 * tj + b, 4 * tk + c)]
-                    for a in range(8) for b in range(8) for c in range(4))
-        assert ks[0] == 256 * ((tk * 2 + tj) * 2 + ti)
-        assert ks == list(range(ks[0], ks[0] + 256))
+def test_key_is_the_plain_cell_index():
+    """The oracle's key is (k n_y + j) n_x + i of the FP32-decided cell, on a
+    grid whose axes all differ, against integer arithmetic done here."""
+    rng = np.random.default_rng(12)
+    n = (7, 5, 6)
+    dx = 1.0 / 7
+    ijk = np.stack([rng.integers(0, n[b], 400) for b in range(3)])
+    x = ((ijk + rng.uniform(0.05, 0.95, ijk.shape)) * dx).astype(np.float32)
+    key = oracle.keys(x, n, dx)
+    assert np.array_equal(key, (ijk[2] * n[1] + ijk[1]) * n[0] + ijk[0])
+    perm, cs, k2 = oracle.cell_sort(x, n, dx)
+    assert np.array_equal(k2, key)
+    for c in range(oracle.num_cells(n)):
+        members = np.flatnonzero(key == c)
+        assert np.array_equal(perm[cs[c]:cs[c + 1]], members)
 
 
 def test_key_uses_fp32_product():
@@ -80,7 +75,8 @@ def test_key_uses_fp32_product():
     x = np.array([[np.nextafter(np.float32(0.5), np.float32(0))], [0.3], [0.3]], np.float32)
     key = oracle.keys(x, n, dx)
     i = int(np.floor(np.float32(x[0, 0] * np.float32(32.0))))
-    assert key[0] == oracle.cell_key(i, 9, 9, n)
+    assert i == 15                          # the FP32 product rounds below 16
+    assert key[0] == (9 * 32 + 9) * 32 + i
 
 
 # --------------------------------------------------------------------- P2G
@@ -501,84 +497,6 @@ def test_pcg_projection_matches_direct_solve_and_is_divergence_free():
         if np.abs(div[fluid]).max() > 0 else (vp, None, None)
     for a in range(3):
         assert np.allclose(vp2[a], vp[a], rtol=0, atol=1e-8 * np.abs(vp[a]).max())
-
-
-def test_block_interleave_order():
-    """Rounds of the interleaved order list, per block, each key's particles in
-    stable order; it is a permutation that keeps every block's slot range."""
-    rng = np.random.default_rng(90)
-    n = (16, 8, 8)
-    dx = 1 / 16
-    x = np.stack([rng.uniform(1, n[b] - 1, 3000) * dx for b in range(3)]).astype(np.float32)
-    x[:, :400] = np.array([[5.5], [3.5], [2.5]]) * dx      # one crowded cell
-    nk = oracle.num_keys(n)
-    key = oracle.keys(x, n, dx)
-    perm, cs = oracle.stable_sort(key, nk)
-    out = oracle.block_interleave(perm, nk, cs)
-    assert np.array_equal(np.sort(out), np.arange(x.shape[1]))
-    for b in range(nk // 32):
-        lo, hi = cs[32 * b], cs[32 * b + 32]
-        seg = out[lo:hi]
-        assert np.array_equal(np.sort(seg), np.sort(perm[lo:hi]))
-        # each key's particles appear in increasing index order, and the r-th
-        # one of key k comes after the (r-1)-th one of every key of the block
-        for k in range(32 * b, 32 * b + 32):
-            mine = seg[key[seg] == k]
-            assert np.array_equal(mine, perm[cs[k]:cs[k + 1]])
-        kk = key[seg]
-        rank = np.zeros_like(kk)
-        for c in np.unique(kk):
-            rank[kk == c] = np.arange(np.sum(kk == c))
-        order = np.lexsort((kk, rank))
-        assert np.array_equal(order, np.arange(len(seg)))
-
-
-def test_tile_group_order():
-    """The grouped slot order of ordered phases, checked through properties
-    that define it: a permutation keeping every 256-key tile's slot range;
-    each cell's particles in stable order; cells first appearing in
-    (min(n, 31) descending, key ascending) order; ranks 32 g .. 32 g + 31
-    filling consecutive slots; and inside a group, (round, lane) strictly
-    increasing."""
-    rng = np.random.default_rng(91)
-    n = (16, 8, 8)
-    dx = 1 / 16
-    x = np.stack([rng.uniform(1, n[b] - 1, 3000) * dx for b in range(3)]).astype(np.float32)
-    x[:, :400] = np.array([[5.5], [3.5], [2.5]]) * dx      # crowded cells: both in
-    x[:, 400:440] = np.array([[2.5], [2.5], [2.5]]) * dx   # the top bucket, key order decides
-    x[:, 440:460] = np.array([[1.5], [1.5], [1.5]]) * dx   # 16..30 particles: ranked by count,
-    x[:, 460:485] = np.array([[6.5], [1.5], [1.5]]) * dx   # not by key (the higher key is fuller)
-    nk = oracle.num_keys(n)
-    key = oracle.keys(x, n, dx)
-    perm, cs = oracle.stable_sort(key, nk)
-    out = oracle.tile_group_order(perm, nk, cs)
-    assert np.array_equal(np.sort(out), np.arange(x.shape[1]))
-    pos_in_cell = np.empty(x.shape[1], np.int64)
-    for k in range(nk):
-        pos_in_cell[perm[cs[k]:cs[k + 1]]] = np.arange(cs[k + 1] - cs[k])
-    groups = 0
-    for t in range(nk // 256):
-        lo, hi = cs[256 * t], cs[256 * t + 256]
-        seg = out[lo:hi]
-        assert np.array_equal(np.sort(seg), np.sort(perm[lo:hi]))
-        kk = key[seg].astype(np.int64)
-        for k in np.unique(kk):                      # stable order inside each cell
-            assert np.array_equal(seg[kk == k], perm[cs[k]:cs[k + 1]])
-        _, first = np.unique(kk, return_index=True)
-        ranked = kk[np.sort(first)]                  # cells by first appearance
-        cnt = np.minimum(cs[ranked + 1] - cs[ranked], 31)
-        for a_, b_, ca, cb in zip(ranked[:-1], ranked[1:], cnt[:-1], cnt[1:]):
-            assert ca > cb or (ca == cb and a_ < b_)
-        rank = {int(k): i for i, k in enumerate(ranked)}
-        grp = np.array([rank[int(k)] // 32 for k in kk])
-        lane = np.array([rank[int(k)] % 32 for k in kk])
-        assert np.all(np.diff(grp) >= 0)             # groups fill consecutive slots
-        rnd = pos_in_cell[seg]
-        for g in np.unique(grp):
-            m = grp == g
-            assert np.all(np.diff(rnd[m] * 32 + lane[m]) > 0)   # round by round, lane by lane
-        groups += len(np.unique(grp))
-    assert groups >= 8                               # several tiles hold more than one group
 
 
 def test_affine_map_reduces_to_constant_map_at_zero_dt():
