@@ -1,5 +1,5 @@
 // g2p_fit.cuh -- the G2P fit from a staged velocity footprint (Eqs 6-8,
-// Section 3.3), shared by the G2P kernels of g2p.cu and ordered.cu.
+// Section 3.3), used by the G2P kernels of g2p.cu.
 //
 // The fit is the transpose of P2G's sum factorisation with per-axis weights
 //   G0_k = W_k,  G1_k = W_k z_k / mu2 = 4 F1_k,  G2_k = W_k g_k / d_2 = (1,-2,1)/2

@@ -1,8 +1,7 @@
 // p2g_kernel.cuh -- the per-particle pieces of the P2G transfer (Eqs 1-5,
-// 13, 15-19) shared by the tile kernels of p2g.cu (block-interleaved phases)
-// and p2g_ordered.cu (ordered phases): cp.async staging of a particle, the
-// sum-factorised accumulation into a lane's padded 4 x 3 x 3 footprint, and
-// the slot of a lane's particle in a round.
+// 13, 15-19) used by the tile kernel of p2g_tiles.cuh: cp.async staging of a
+// particle, the sum-factorised accumulation into a lane's padded 4 x 3 x 3
+// footprint, and the slot of a lane's particle in a round.
 #pragma once
 #include "p2g.cuh"
 

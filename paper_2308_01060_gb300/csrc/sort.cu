@@ -20,7 +20,6 @@
 //                  each key's r-th particle), so that a warp whose lanes own
 //                  the 32 cells reads one contiguous run of slots per round.
 #include "sort.cuh"
-#include "tile_order.cuh"
 
 namespace polypic {
 
@@ -260,38 +259,21 @@ __global__ void __launch_bounds__(256) k_cell_order(const uint32_t *__restrict__
     deal_rounds(in, k, s0, cs[k + 1] - s0, cs[b * 32], out, crowded, num_crowded);
 }
 
-// Grouped layout: one CTA per tile, warp g deals group g of the ranked cells.
-__global__ void __launch_bounds__(256) k_cell_order_groups(const uint32_t *__restrict__ in,
-                                                           const uint32_t *__restrict__ cs,
-                                                           uint32_t *__restrict__ out,
-                                                           uint32_t *__restrict__ crowded,
-                                                           uint32_t *__restrict__ num_crowded) {
-    __shared__ TileOrder o;
-    const uint32_t tile = blockIdx.x;
-    if (cs[tile * kTileCells] == cs[tile * kTileCells + kTileCells]) return;  // CTA-uniform
-    rank_tile<256>(cs, tile, o);
-    const uint32_t rk = threadIdx.x;  // rank = 32 g + lane
-    const uint32_t k = tile * kTileCells + o.cell[rk];
-    deal_rounds(in, k, cs[k], o.n[rk], o.gstart[threadIdx.x >> 5], out, crowded, num_crowded);
-}
-
 // Cells holding more than kSelectMax particles, one CTA per cell: a stable
 // LSD radix sort of the cell's indices (8-bit digits, ranked in chunks of 256
 // in order) between its range of `a` and of `b`, then the dealt slots.
 // Linear in the cell's population, so a crowded cell costs what its particles
 // cost.  Launched with a fixed grid; CTAs beyond the list exit at once.
-template <Layout L>
 __global__ void __launch_bounds__(256) k_crowded_cells(const uint32_t *__restrict__ crowded,
                                                        const uint32_t *__restrict__ num_crowded,
                                                        uint32_t *a, uint32_t *b,
                                                        const uint32_t *__restrict__ cs,
                                                        uint32_t *__restrict__ out, int value_bits) {
-    __shared__ TileOrder o;
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_wc[8][256];
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_n[32];
-    __shared__ uint32_t s_lane, s_setbase, s_rank;
+    __shared__ uint32_t s_lane, s_setbase;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t total_cells = *num_crowded;
@@ -340,23 +322,12 @@ __global__ void __launch_bounds__(256) k_crowded_cells(const uint32_t *__restric
             dst = t;
         }
         // the cell's lane set: its 32 counts, its lane and the set's first slot
-        if constexpr (L == Layout::kBlocks) {
+        {
             const uint32_t blk = k >> 5;
             if (tid < 32) s_n[tid] = cs[blk * 32 + tid + 1] - cs[blk * 32 + tid];
             if (tid == 0) {
                 s_lane = k & 31u;
                 s_setbase = cs[blk * 32];
-            }
-        } else {
-            const uint32_t tile = k / kTileCells;
-            rank_tile<256>(cs, tile, o);
-            if (o.cell[tid] == k - tile * kTileCells) s_rank = (uint32_t)tid;
-            __syncthreads();
-            const uint32_t grp = s_rank >> 5;
-            if (tid < 32) s_n[tid] = o.n[32 * grp + (uint32_t)tid];
-            if (tid == 0) {
-                s_lane = s_rank & 31u;
-                s_setbase = o.gstart[grp];
             }
         }
         __syncthreads();
@@ -404,32 +375,25 @@ bool take_sort_scratch(Workspace &ws, int64_t count, int64_t num_keys, SortScrat
 }
 
 cudaError_t finish_order(int64_t num_keys, int64_t count, const uint32_t *key,
-                         uint32_t *cell_start, uint32_t *perm, Layout layout,
-                         const SortScratch &S, cudaStream_t s) {
+                         uint32_t *cell_start, uint32_t *perm, const SortScratch &S,
+                         cudaStream_t s) {
     cudaError_t e = exclusive_scan(cell_start, cell_start, num_keys + 1, S.cscan, s);
     if (e != cudaSuccess) return e;
     const int pblocks = (int)((count + 255) / 256);
     k_scatter<<<pblocks, 256, 0, s>>>(count, key, S.rank, cell_start, S.arrival);
     const int64_t cap = crowded_capacity(count);
     const int cgrid = (int)(cap < 304 ? cap : 304);
-    if (layout == Layout::kBlocks) {
-        const uint32_t nblocks = (uint32_t)(num_keys / 32);
-        k_cell_order<<<(nblocks + 7) / 8, 256, 0, s>>>(S.arrival, cell_start, perm, nblocks,
-                                                       S.crowded, S.num_crowded);
-        k_crowded_cells<Layout::kBlocks><<<cgrid, 256, 0, s>>>(
-            S.crowded, S.num_crowded, S.arrival, S.radix, cell_start, perm, value_bits(count));
-    } else {
-        k_cell_order_groups<<<(unsigned)(num_keys / kTileCells), 256, 0, s>>>(
-            S.arrival, cell_start, perm, S.crowded, S.num_crowded);
-        k_crowded_cells<Layout::kGroups><<<cgrid, 256, 0, s>>>(
-            S.crowded, S.num_crowded, S.arrival, S.radix, cell_start, perm, value_bits(count));
-    }
+    const uint32_t nblocks = (uint32_t)(num_keys / 32);
+    k_cell_order<<<(nblocks + 7) / 8, 256, 0, s>>>(S.arrival, cell_start, perm, nblocks,
+                                                   S.crowded, S.num_crowded);
+    k_crowded_cells<<<cgrid, 256, 0, s>>>(S.crowded, S.num_crowded, S.arrival, S.radix,
+                                          cell_start, perm, value_bits(count));
     return cudaGetLastError();
 }
 
 cudaError_t sort_particles(const GridGeom &g, int64_t num_keys, int64_t count, const float *x,
                            const float *y, const float *z, uint32_t *key, uint32_t *perm,
-                           uint32_t *cell_start, uint32_t *status, Layout layout, Workspace &ws,
+                           uint32_t *cell_start, uint32_t *status, Workspace &ws,
                            cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(cell_start, 0, sizeof(uint32_t) * (num_keys + 1), s);
     if (e != cudaSuccess) return e;
@@ -440,7 +404,7 @@ cudaError_t sort_particles(const GridGeom &g, int64_t num_keys, int64_t count, c
     k_keys<<<(int)((count + 256 * kKeyRuns - 1) / (256 * kKeyRuns)), 256, 0, s>>>(
         count, x, y, z, g, key, S.rank, cell_start, S.num_crowded, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return finish_order(num_keys, count, key, cell_start, perm, layout, S, s);
+    return finish_order(num_keys, count, key, cell_start, perm, S, s);
 }
 
 }  // namespace polypic

@@ -17,12 +17,6 @@ size_t scan_scratch_words(int64_t L);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t L, uint32_t *scratch,
                            cudaStream_t s);
 
-// Slot layouts written by the sort.
-enum class Layout {
-    kBlocks,  // block-interleaved: round-robin over the 32 keys of each block
-    kGroups,  // count-ranked groups of 32 cells per tile (tile_order.cuh)
-};
-
 // Scratch of one sort, carved from the caller's workspace.
 struct SortScratch {
     uint32_t *key;          // key of each input particle (when the caller has no array)
@@ -37,16 +31,16 @@ size_t sort_scratch_bytes(int64_t count, int64_t num_keys);
 bool take_sort_scratch(Workspace &ws, int64_t count, int64_t num_keys, SortScratch &S);
 
 // From the per-key counts in cell_start (written by a key producer together
-// with key and S.rank): cell_start becomes the exclusive prefix, perm the slot
-// order in `layout` (perm[j] = input index of the particle in slot j).
+// with key and S.rank): cell_start becomes the exclusive prefix, perm the
+// block-interleaved slot order (perm[j] = input index of the particle in slot j).
 cudaError_t finish_order(int64_t num_keys, int64_t count, const uint32_t *key,
-                         uint32_t *cell_start, uint32_t *perm, Layout layout,
-                         const SortScratch &S, cudaStream_t s);
+                         uint32_t *cell_start, uint32_t *perm, const SortScratch &S,
+                         cudaStream_t s);
 
 // The whole sort of particles by the cell of their positions.
 cudaError_t sort_particles(const GridGeom &g, int64_t num_keys, int64_t count, const float *x,
                            const float *y, const float *z, uint32_t *key, uint32_t *perm,
-                           uint32_t *cell_start, uint32_t *status, Layout layout, Workspace &ws,
+                           uint32_t *cell_start, uint32_t *status, Workspace &ws,
                            cudaStream_t s);
 
 }  // namespace polypic

@@ -70,8 +70,7 @@ EXPORTS = [
     "polypic_create", "polypic_destroy", "polypic_num_keys", "polypic_cell_key",
     "polypic_grid_dims", "polypic_workspace_bytes", "polypic_sort", "polypic_p2g",
     "polypic_p2g_mapped", "polypic_p2g_noalloc",
-    "polypic_grid_update", "polypic_g2p", "polypic_step", "polypic_order",
-    "polypic_step_ordered", "polypic_g2p_adjoint",
+    "polypic_grid_update", "polypic_g2p", "polypic_step", "polypic_g2p_adjoint",
     "polypic_grid_update_adjoint", "polypic_p2g_adjoint", "polypic_check_device_status",
     "polypic_status_string",
 ]
@@ -105,9 +104,6 @@ def load_library(path: str = LIB_PATH):
                              ctypes.c_size_t, _vp]),
         "polypic_step": (st, [_vp, P(Particles), P(Particles), P(Particles), P(Particles),
                               P(Grid), P(Grid), P(UpdateParams), _vp, ctypes.c_size_t, _vp]),
-        "polypic_order": (st, [_vp, P(Particles), P(Particles), _vp, ctypes.c_size_t, _vp]),
-        "polypic_step_ordered": (st, [_vp, P(Particles), P(Particles), P(Grid), P(UpdateParams),
-                                      _vp, ctypes.c_size_t, _vp]),
         "polypic_g2p_adjoint": (st, [_vp, P(Grid), P(Particles), ctypes.c_float, P(Particles),
                                      P(Grid), P(Particles), ctypes.c_int32, _vp, ctypes.c_size_t,
                                      _vp]),
@@ -374,26 +370,6 @@ def polypic_step(ctx: Context, fluid_in: ParticleState, fluid_out: ParticleState
     ref = lambda s: ctypes.byref(s) if s is not None else None
     _check(load_library().polypic_step(ctx.handle, ref(fi), ref(fo), ref(si), ref(so), ref(cgf),
                                        ref(cgs), ref(up), wp, wb, _stream(stream)), "polypic_step")
-
-
-def polypic_order(ctx: Context, p_in: ParticleState, p_out: ParticleState, ws: torch.Tensor,
-                  stream=None):
-    """p_out <- the particles of p_in as an ordered phase (grouped slot order);
-    p_out.perm[j] is the index in p_in of the particle in slot j."""
-    ci, co = p_in.c_struct(), p_out.c_struct()
-    wp, wb = _ws(ws)
-    _check(load_library().polypic_order(ctx.handle, ctypes.byref(ci), ctypes.byref(co), wp, wb,
-                                        _stream(stream)), "polypic_order")
-
-
-def polypic_step_ordered(ctx: Context, p_in: ParticleState, p_out: ParticleState, g: GridState,
-                         params: UpdateSettings, ws: torch.Tensor, stream=None):
-    """One step of an ordered phase p_in into the next ordered phase p_out."""
-    ci, co, cg, up = p_in.c_struct(), p_out.c_struct(), g.c_struct(), params.c_struct()
-    wp, wb = _ws(ws)
-    _check(load_library().polypic_step_ordered(ctx.handle, ctypes.byref(ci), ctypes.byref(co),
-                                               ctypes.byref(cg), ctypes.byref(up), wp, wb,
-                                               _stream(stream)), "polypic_step_ordered")
 
 
 def polypic_g2p_adjoint(ctx: Context, g: GridState, p_in: ParticleState, dt: float,
