@@ -213,13 +213,16 @@ polypic_status polypic_p2g_mapped(polypic_ctx *ctx, const polypic_particles *p, 
  * enough for grids of at most 2048 key tiles, i.e.
  * ceil(n_x/8) * ceil(n_y/8) * ceil(n_z/4) <= 2048 (64^3 uses 1024); larger
  * grids return POLYPIC_ERR_WORKSPACE before anything is launched.  The call
- * allocates nothing itself.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call shares the one array and
- * it keeps the previous call's contents (every launch writes each entry it
- * later reads, so nothing needs clearing); calls that overlap on the GPU, on
- * any stream or context of the process, race on it and must be serialised by
- * the caller.  Inputs and outputs are as for polypic_p2g. */
+ * allocates nothing itself.  Every call made outside a stream capture looks
+ * the array's device address up in the current CUDA context
+ * (cudaGetSymbolAddress) and remembers it for that context; a call issued
+ * while `stream` is being captured uses the remembered address (CUDA error
+ * if there is none), so make one call on the context before capturing.
+ * Every call shares the one array and it keeps the previous call's contents
+ * (every launch writes each entry it later reads, so nothing needs
+ * clearing); calls that overlap on the GPU, on any stream or context of the
+ * process, race on it and must be serialised by the caller.  Inputs and
+ * outputs are as for polypic_p2g. */
 polypic_status polypic_p2g_noalloc(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
                                    void *stream);
 
@@ -259,47 +262,6 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
                             polypic_particles *solid_out, polypic_grid *gf, polypic_grid *gs,
                             const polypic_update_params *params, void *ws, size_t ws_bytes,
                             void *stream);
-
-/* ---- ordered phases ------------------------------------------------------ *
- * An implementation device (the paper has none): a phase whose arrays are
- * kept in their own slot order, so that P2G reads every round of a warp as
- * one contiguous run instead of following perm, and the lanes of a warp hold
- * cells of similar population.  The grouped slot order of an ordered phase:
- * take the stable (key, index) order; every tile of 256 consecutive keys
- * keeps its slot range [cell_start[256t], cell_start[256t + 256]); inside it
- * the tile's cells are ranked by particle count n -- min(n, 31) descending,
- * ties by key ascending -- and rank 32g + l is lane l of group g; groups
- * g = 0..7 follow each other, and inside a group round r = 0, 1, ... lists
- * the r-th particle of every lane whose cell holds more than r particles,
- * lanes ascending.  An ordered phase is described by its arrays (x, mass,
- * mass_abs, coeff, coeff_scale) in that order plus cell_start and key (the
- * key of each slot's particle); its perm is not read.                        */
-
-/* Writes the particles of `in` (any order) into `out` as an ordered phase:
- * out->perm[j] = index in `in` of the particle in slot j, out->cell_start as
- * polypic_sort, out->key[j] its key, and every array of `in` gathered into
- * slot order.  `out` must not alias `in`.  Latches OUT_OF_DOMAIN like
- * polypic_sort. */
-polypic_status polypic_order(polypic_ctx *ctx, const polypic_particles *in,
-                             polypic_particles *out, void *ws, size_t ws_bytes, void *stream);
-
-/* One transfer step of an ordered phase (fluid, or a solid phase with
- * mass_abs, alone): P2G from in's arrays as they lie (no sort), the grid
- * update (fused into P2G's reduction) or the update and projection, then
- * advection: x_p + dt v_p, clamped as in polypic_g2p, with v_p the
- * velocity-mode fit -- the sort of the advected positions into the next
- * order -- and G2P at the old positions written into that order.  `out`
- * receives the next ordered phase: out->perm[j] = index in `in` of the
- * particle in slot j (a particle's identity follows through perm), and
- * out->cell_start, out->key.  The values equal polypic_step's up to
- * rounding; only the order of the particles differs.  A particle that moved
- * more than one cell out of its new tile is fitted from the grid directly
- * (slower, same result).  `in` must come from polypic_order or from this
- * call; `out` must not alias `in`. */
-polypic_status polypic_step_ordered(polypic_ctx *ctx, const polypic_particles *in,
-                                    polypic_particles *out, polypic_grid *g,
-                                    const polypic_update_params *params, void *ws,
-                                    size_t ws_bytes, void *stream);
 
 /* ---- adjoints (constant map, single phase, no projection) ---------------- *
  * Contexts with POLYPIC_MAP_AFFINE (4 modes or more) or POLYPIC_APIC_GRAD_W get

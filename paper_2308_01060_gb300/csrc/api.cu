@@ -9,7 +9,6 @@
 
 #include "g2p.cuh"
 #include "grid.cuh"
-#include "ordered.cuh"
 #include "p2g.cuh"
 #include "pcg.cuh"
 #include "adjoint.cuh"
@@ -35,12 +34,9 @@ size_t required_ws(const polypic_ctx *c, int64_t nf, int64_t ns) {
     size_t e = c->cfg.coeff_format == POLYPIC_COEFF_F32
                    ? adjoint_scratch_bytes(n, c->cfg.num_modes) + b + 256
                    : 0;
-    // the ordered step: its sort and far list
-    size_t o = a + (size_t)n * sizeof(uint32_t) + 8 * 256;
     size_t m = a > b ? a : b;
     m = m > d ? m : d;
     m = m > e ? m : e;
-    m = m > o ? m : o;
     return m + 4096;
 }
 
@@ -87,8 +83,7 @@ polypic_status do_sort(polypic_ctx *c, polypic_particles *p, void *ws, size_t ws
     if (p->count > 0 && !p->key) return POLYPIC_ERR_INVALID_ARG;
     Workspace W{static_cast<char *>(ws), ws_bytes, 0};
     return from_cuda(sort_particles(c->geom, c->num_keys, p->count, p->x[0], p->x[1], p->x[2],
-                                    p->key, p->perm, p->cell_start, c->d_status, Layout::kBlocks,
-                                    W, s));
+                                    p->key, p->perm, p->cell_start, c->d_status, W, s));
 }
 
 // Eq 12's map changes the transfer (with one mode C = 0 and M = I).
@@ -96,9 +91,9 @@ bool mapped(const polypic_ctx *c) {
     return c->cfg.map == POLYPIC_MAP_AFFINE && c->cfg.num_modes >= 4;
 }
 
-polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *g, void *ws,
-                      size_t ws_bytes, cudaStream_t s, const polypic_update_params *fused = nullptr,
-                      bool ordered = false, float map_dt = 0.0f) {
+// The P2G launch arguments of phase p on context c, except the scratch (tile
+// regions and live flags), which the caller supplies.
+P2GArgs p2g_args(const polypic_ctx *c, const polypic_particles *p, float map_dt) {
     P2GArgs P{};
     P.affine = mapped(c);
     P.map_dt = map_dt;
@@ -120,13 +115,20 @@ polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *
     const bool phys = c->cfg.coeff_format == POLYPIC_COEFF_F32;
     P.s1 = phys ? P.dxpow[1] : 1.0f;
     P.s2 = phys ? P.dxpow[2] : 1.0f;
+    return P;
+}
+
+polypic_status do_p2g(polypic_ctx *c, const polypic_particles *p, polypic_grid *g, void *ws,
+                      size_t ws_bytes, cudaStream_t s, const polypic_update_params *fused = nullptr,
+                      float map_dt = 0.0f) {
+    P2GArgs P = p2g_args(c, p, map_dt);
     Workspace W{static_cast<char *>(ws), ws_bytes, 0};
     P.scratch = W.take<float>((size_t)(c->num_keys / 256) * kTileFloats);
     P.tile_live = W.take<uint8_t>((size_t)(c->num_keys / 256));
     if (W.overflow) return POLYPIC_ERR_WORKSPACE;
     return from_cuda(p2g(P, g->mass, g->mom, fused ? g->vel : nullptr, fused ? fused->dt : 0.0f,
                          fused ? fused->gravity : nullptr, c->cfg.num_modes, c->cfg.coeff_format,
-                         s, ordered));
+                         s));
 }
 
 polypic_status do_g2p(polypic_ctx *c, const polypic_grid *g, const polypic_particles *in,
@@ -169,18 +171,6 @@ polypic_status check_g2p_out(const polypic_ctx *c, const polypic_particles *in,
         for (int b = 0; b < 3; ++b)
             if (out->x[a] == in->x[b]) return POLYPIC_ERR_INVALID_ARG;
     if (out->mass == in->mass || out->coeff == in->coeff) return POLYPIC_ERR_INVALID_ARG;
-    return POLYPIC_OK;
-}
-
-// Output arrays of an ordered phase (the arrays of G2P's output plus the
-// order: perm, key, cell_start).
-polypic_status check_ordered_out(const polypic_ctx *c, const polypic_particles *in,
-                                 const polypic_particles *out) {
-    polypic_status s = check_g2p_out(c, in, out);
-    if (s != POLYPIC_OK) return s;
-    if (!out->cell_start) return POLYPIC_ERR_INVALID_ARG;
-    if (in->count > 0 && (!out->perm || !out->key)) return POLYPIC_ERR_INVALID_ARG;
-    if (out->cell_start == in->cell_start) return POLYPIC_ERR_INVALID_ARG;
     return POLYPIC_OK;
 }
 
@@ -329,7 +319,7 @@ polypic_status polypic_p2g_mapped(polypic_ctx *ctx, const polypic_particles *p, 
     if ((s = check_coeff(ctx, p)) != POLYPIC_OK) return s;
     if (!grid_ok(g, true, true, false)) return POLYPIC_ERR_INVALID_ARG;
     if ((s = check_ws(ctx, p->count, ws, ws_bytes)) != POLYPIC_OK) return s;
-    return do_p2g(ctx, p, g, ws, ws_bytes, as_stream(stream), nullptr, false, dt);
+    return do_p2g(ctx, p, g, ws, ws_bytes, as_stream(stream), nullptr, dt);
 }
 
 polypic_status polypic_p2g_noalloc(polypic_ctx *ctx, const polypic_particles *p, polypic_grid *g,
@@ -340,25 +330,9 @@ polypic_status polypic_p2g_noalloc(polypic_ctx *ctx, const polypic_particles *p,
     if ((s = check_coeff(ctx, p)) != POLYPIC_OK) return s;
     if (!grid_ok(g, true, true, false)) return POLYPIC_ERR_INVALID_ARG;
     if (ctx->num_keys / 256 > (int64_t)p2g_builtin_max_tiles()) return POLYPIC_ERR_WORKSPACE;
-    P2GArgs P{};
-    P.g = ctx->geom;
-    P.count = p->count;
-    P.x = p->x[0];
-    P.y = p->x[1];
-    P.z = p->x[2];
-    P.mass = p->mass;
-    P.mass_abs = p->mass_abs;
-    P.coeff = p->coeff;
-    P.scale = p->coeff_scale;
-    P.perm = p->perm;
-    P.cell_start = p->cell_start;
-    P.status = ctx->d_status;
-    P.nblocks = (uint32_t)(ctx->num_keys / 32);
-    for (int l = 0; l < 7; ++l) P.dxpow[l] = (float)std::pow(ctx->cfg.dx, (double)l);
-    const bool phys = ctx->cfg.coeff_format == POLYPIC_COEFF_F32;
-    P.s1 = phys ? P.dxpow[1] : 1.0f;
-    P.s2 = phys ? P.dxpow[2] : 1.0f;
-    if (p2g_builtin_scratch(&P.scratch, &P.tile_live) != cudaSuccess) return POLYPIC_ERR_CUDA;
+    P2GArgs P = p2g_args(ctx, p, 0.0f);
+    if (p2g_builtin_scratch(as_stream(stream), &P.scratch, &P.tile_live) != cudaSuccess)
+        return POLYPIC_ERR_CUDA;
     return from_cuda(p2g(P, g->mass, g->mom, nullptr, 0.0f, nullptr, ctx->cfg.num_modes,
                          ctx->cfg.coeff_format, as_stream(stream)));
 }
@@ -422,12 +396,12 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
     // a single phase without projection gets the grid update fused into P2G's reduce
     const bool fuse = !solid && !params->project;
     if ((s = do_sort(ctx, fluid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
-    if ((s = do_p2g(ctx, fluid_in, gf, ws, ws_bytes, st, fuse ? params : nullptr, false,
-                    params->dt)) != POLYPIC_OK)
+    if ((s = do_p2g(ctx, fluid_in, gf, ws, ws_bytes, st, fuse ? params : nullptr, params->dt)) !=
+        POLYPIC_OK)
         return s;
     if (solid) {
         if ((s = do_sort(ctx, solid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
-        if ((s = do_p2g(ctx, solid_in, gs, ws, ws_bytes, st, nullptr, false, params->dt)) !=
+        if ((s = do_p2g(ctx, solid_in, gs, ws, ws_bytes, st, nullptr, params->dt)) !=
             POLYPIC_OK)
             return s;
     }
@@ -437,127 +411,6 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
     if ((s = do_g2p(ctx, gf, fluid_in, fluid_out, params->dt, st)) != POLYPIC_OK) return s;
     if (solid && (s = do_g2p(ctx, gs, solid_in, solid_out, params->dt, st)) != POLYPIC_OK) return s;
     return POLYPIC_OK;
-}
-
-polypic_status polypic_order(polypic_ctx *ctx, const polypic_particles *in,
-                             polypic_particles *out, void *ws, size_t ws_bytes, void *stream) {
-    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
-    polypic_status s = check_positions(in);
-    if (s != POLYPIC_OK) return s;
-    if ((s = check_coeff(ctx, in)) != POLYPIC_OK) return s;
-    if ((s = check_ordered_out(ctx, in, out)) != POLYPIC_OK) return s;
-    if ((s = check_ws(ctx, in->count, ws, ws_bytes)) != POLYPIC_OK) return s;
-    cudaStream_t st = as_stream(stream);
-    Workspace W{static_cast<char *>(ws), ws_bytes, 0};
-    uint32_t *key = W.take<uint32_t>((size_t)in->count);
-    if (W.overflow) return POLYPIC_ERR_WORKSPACE;
-    cudaError_t e = sort_particles(ctx->geom, ctx->num_keys, in->count, in->x[0], in->x[1],
-                                   in->x[2], key, out->perm, out->cell_start, ctx->d_status,
-                                   Layout::kGroups, W, st);
-    if (e != cudaSuccess) return from_cuda(e);
-    GatherArgs G{};
-    G.count = in->count;
-    G.rows = 3 * ctx->cfg.num_modes;
-    G.elem = ctx->cfg.coeff_format == POLYPIC_COEFF_F32 ? 4 : 2;
-    G.perm = out->perm;
-    for (int a = 0; a < 3; ++a) {
-        G.x[a] = in->x[a];
-        G.ox[a] = out->x[a];
-    }
-    G.mass = in->mass;
-    G.mass_abs = in->mass_abs;
-    G.scale = in->coeff_scale;
-    G.coeff = in->coeff;
-    G.key = key;
-    G.omass = out->mass;
-    G.omass_abs = in->mass_abs ? out->mass_abs : nullptr;
-    G.oscale = ctx->cfg.coeff_format == POLYPIC_COEFF_F32 ? nullptr : out->coeff_scale;
-    G.ocoeff = out->coeff;
-    G.okey = out->key;
-    return from_cuda(gather_phase(G, st));
-}
-
-polypic_status polypic_step_ordered(polypic_ctx *ctx, const polypic_particles *in,
-                                    polypic_particles *out, polypic_grid *g,
-                                    const polypic_update_params *params, void *ws,
-                                    size_t ws_bytes, void *stream) {
-    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
-    // ordered phases fit with the truncation form and the constant map only
-    if (mapped(ctx) || ctx->cfg.apic_variant != POLYPIC_APIC_TRUNCATION)
-        return POLYPIC_ERR_UNSUPPORTED;
-    polypic_status s = check_positions(in);
-    if (s != POLYPIC_OK) return s;
-    if (!in->cell_start) return POLYPIC_ERR_INVALID_ARG;
-    if ((s = check_coeff(ctx, in)) != POLYPIC_OK) return s;
-    if ((s = check_ordered_out(ctx, in, out)) != POLYPIC_OK) return s;
-    if (!grid_ok(g, true, true, true)) return POLYPIC_ERR_INVALID_ARG;
-    if ((s = check_params(params)) != POLYPIC_OK) return s;
-    if ((s = check_ws(ctx, in->count, ws, ws_bytes)) != POLYPIC_OK) return s;
-    cudaStream_t st = as_stream(stream);
-    // P2G straight from the ordered arrays; the update fused into its reduce
-    // unless the step projects
-    if ((s = do_p2g(ctx, in, g, ws, ws_bytes, st, params->project ? nullptr : params, true)) !=
-        POLYPIC_OK)
-        return s;
-    if (params->project &&
-        (s = do_grid_update(ctx, g, nullptr, in, params, ws, ws_bytes, st)) != POLYPIC_OK)
-        return s;
-    // the P2G scratch is dead from here on (stream order): the rest reuses ws
-    cudaError_t e =
-        cudaMemsetAsync(out->cell_start, 0, sizeof(uint32_t) * (ctx->num_keys + 1), st);
-    if (e != cudaSuccess || in->count == 0) return from_cuda(e);
-    Workspace W{static_cast<char *>(ws), ws_bytes, 0};
-    SortScratch S;
-    if (!take_sort_scratch(W, in->count, ctx->num_keys, S)) return POLYPIC_ERR_WORKSPACE;
-    uint32_t *far = W.take<uint32_t>((size_t)in->count);
-    uint32_t *num_far = W.take<uint32_t>(1);
-    if (W.overflow) return POLYPIC_ERR_WORKSPACE;
-    const int64_t tiles = ctx->num_keys / 256;
-    AdvectArgs A{};
-    A.g = ctx->geom;
-    A.count = in->count;
-    A.dt = params->dt;
-    for (int a = 0; a < 3; ++a) A.vel[a] = g->vel[a];
-    A.x = in->x[0];
-    A.y = in->x[1];
-    A.z = in->x[2];
-    A.cell_start = in->cell_start;
-    A.key = S.key;
-    A.rank = S.rank;
-    A.counts = out->cell_start;
-    A.num_crowded = S.num_crowded;
-    A.num_far = num_far;
-    A.status = ctx->d_status;
-    if ((e = advect(A, tiles, st)) != cudaSuccess) return from_cuda(e);
-    if ((e = finish_order(ctx->num_keys, in->count, S.key, out->cell_start, out->perm,
-                          Layout::kGroups, S, st)) != cudaSuccess)
-        return from_cuda(e);
-    OrderedG2PArgs G{};
-    G.g = ctx->geom;
-    G.count = in->count;
-    G.dt = params->dt;
-    for (int a = 0; a < 3; ++a) G.vel[a] = g->vel[a];
-    G.x = in->x[0];
-    G.y = in->x[1];
-    G.z = in->x[2];
-    G.mass = in->mass;
-    G.mass_abs = in->mass_abs;
-    G.key_new = S.key;
-    G.perm = out->perm;
-    G.cell_start = out->cell_start;
-    G.ox = out->x[0];
-    G.oy = out->x[1];
-    G.oz = out->x[2];
-    G.omass = out->mass;
-    G.omass_abs = in->mass_abs ? out->mass_abs : nullptr;
-    G.ocoeff = out->coeff;
-    G.oscale = out->coeff_scale;
-    G.okey = out->key;
-    G.far = far;
-    G.num_far = num_far;
-    G.status = ctx->d_status;
-    for (int l = 0; l < 7; ++l) G.inv_dxpow[l] = (float)std::pow(ctx->cfg.dx, -(double)l);
-    return from_cuda(g2p_ordered(G, tiles, ctx->cfg.num_modes, ctx->cfg.coeff_format, st));
 }
 
 polypic_status polypic_g2p_adjoint(polypic_ctx *ctx, const polypic_grid *g,

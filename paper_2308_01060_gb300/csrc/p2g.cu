@@ -22,6 +22,8 @@
 //   * k_p2g_reduce (one CTA per tile, the nodes it owns on the three face
 //     grids) sums the at most 8 tile regions covering each node in ascending
 //     tile order and writes the grids.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "p2g_tiles.cuh"
@@ -168,34 +170,72 @@ __global__ void __launch_bounds__(256) k_p2g_reduce(GridGeom g, const uint8_t *_
 // device arrays that every GPU loading the library holds until the process
 // exits.  Host code must not pass these names to a kernel (on the host they
 // are stand-ins, not device addresses); p2g_builtin_scratch() looks the
-// device addresses up once per device with cudaGetSymbolAddress.
+// device addresses up with cudaGetSymbolAddress.  The address belongs to the
+// copy of the module loaded in the current CUDA context, so it is cached per
+// context (the driver's cuCtxGetCurrent) and looked up again on every call
+// made outside a stream capture, which also covers a context that was torn
+// down and recreated (cudaDeviceReset) under the same handle.  During a
+// capture only the cached address is used.
 constexpr int kBuiltinTiles = 2048;
 static __device__ __align__(256) float g_builtin_tiles[(size_t)kBuiltinTiles * kTileFloats];
 static __device__ __align__(256) uint8_t g_builtin_live[kBuiltinTiles];
 
 int p2g_builtin_max_tiles() { return kBuiltinTiles; }
 
-cudaError_t p2g_builtin_scratch(float **tiles, uint8_t **live) {
-    constexpr int kMaxDevices = 64;
+namespace {
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link-time
+// dependency on libcuda); nullptr if the driver does not provide it.
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    return fn;
+}
+
+struct BuiltinEntry {
+    CUcontext ctx;
+    float *tiles;
+    uint8_t *live;
+};
+}  // namespace
+
+cudaError_t p2g_builtin_scratch(cudaStream_t s, float **tiles, uint8_t **live) {
+    constexpr int kEntries = 64;
     static std::mutex mu;
-    static bool ready[kMaxDevices] = {};
-    static float *tile_ptr[kMaxDevices] = {};
-    static uint8_t *live_ptr[kMaxDevices] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static BuiltinEntry cache[kEntries] = {};
+    static int used = 0, next = 0;
+    // the runtime call first: it makes the device's context current
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    CUcontext ctx = nullptr;
+    const CtxGetCurrentFn get = ctx_get_current();
+    if (get && get(&ctx) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
     std::lock_guard<std::mutex> lock(mu);
-    if (!ready[dev]) {
+    int hit = -1;
+    for (int i = 0; i < used; ++i)
+        if (cache[i].ctx == ctx) hit = i;
+    if (cap == cudaStreamCaptureStatusNone || hit < 0 || !get) {
+        if (cap != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
         void *t = nullptr, *l = nullptr;
         if ((e = cudaGetSymbolAddress(&t, g_builtin_tiles)) != cudaSuccess) return e;
         if ((e = cudaGetSymbolAddress(&l, g_builtin_live)) != cudaSuccess) return e;
-        tile_ptr[dev] = static_cast<float *>(t);
-        live_ptr[dev] = static_cast<uint8_t *>(l);
-        ready[dev] = true;
+        if (hit < 0) {
+            hit = used < kEntries ? used++ : next;
+            next = (hit + 1) % kEntries;
+        }
+        cache[hit] = BuiltinEntry{ctx, static_cast<float *>(t), static_cast<uint8_t *>(l)};
     }
-    *tiles = tile_ptr[dev];
-    *live = live_ptr[dev];
+    *tiles = cache[hit].tiles;
+    *live = cache[hit].live;
     return cudaSuccess;
 }
 
@@ -226,13 +266,8 @@ cudaError_t p2g_adjoint_scatter(const P2GArgs &P, float *lv[3], bool accumulate,
 }
 
 cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], float dt,
-                const float gravity[3], int R, int fmt, cudaStream_t s, bool ordered) {
+                const float gravity[3], int R, int fmt, cudaStream_t s) {
     const int grid = (int)(P.nblocks / kP2GWarps);
-    if (ordered) {
-        const cudaError_t e = launch_p2g_ordered(P, R, fmt, grid, s);
-        if (e != cudaSuccess) return e;
-        return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
-    }
     cudaError_t e;
     if (P.affine) {  // Eq 12's affine map: FP32 coefficients, 4, 8 or 27 modes
         if (fmt != POLYPIC_COEFF_F32) return cudaErrorInvalidValue;

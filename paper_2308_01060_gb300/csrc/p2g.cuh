@@ -54,21 +54,17 @@ struct P2GArgs {
 size_t p2g_scratch_bytes(int64_t num_keys);
 
 // Built-in fixed-size scratch for polypic_p2g_noalloc: device addresses of the
-// tile regions and live flags on the current device (looked up on the first
-// call per device), and the number of tiles they hold.
-cudaError_t p2g_builtin_scratch(float **tiles, uint8_t **live);
+// tile regions and live flags in the current context (looked up again on
+// every call outside a capture of `s`, cached per context for calls during
+// one), and the number of tiles they hold.
+cudaError_t p2g_builtin_scratch(cudaStream_t s, float **tiles, uint8_t **live);
 int p2g_builtin_max_tiles();
 
 // Writes all faces of gm[3] (mass) and gp[3] (momentum); with gv non-NULL
 // also the single-phase grid update (v = mv/m + dt g, zero on wall faces).
-// `ordered`: the phase is in its own grouped slot order (perm unused, the
-// arrays read at the slot); otherwise block-interleaved, read through perm.
+// The phase is in block-interleaved slot order, read through perm.
 cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], float dt,
-                const float gravity[3], int R, int fmt, cudaStream_t s, bool ordered = false);
-
-// The tile kernel of ordered phases (p2g_ordered.cu): writes the tile
-// regions and live flags that the reduction of p2g() sums.
-cudaError_t launch_p2g_ordered(const P2GArgs &P, int R, int fmt, int ntiles, cudaStream_t s);
+                const float gravity[3], int R, int fmt, cudaStream_t s);
 
 // Adjoint of the G2P fit's grid dependence: lv_ia (+)= sum_p sum_r mu_pra
 // G_r(x_ia - x_p), the same deterministic scatter with the fit factors
