@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+    cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
            "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -66,6 +66,8 @@ def _load():
     lib = ctypes.CDLL(build())
     sig = {
         "or_mode_abc": (None, [_int, _I]),
+        "or_set_threads": (None, [_int]),
+        "or_get_threads": (_int, []),
         "or_keys": (None, [_i64, _F, _F, _F, _int, _int, _int, _dbl, _U32]),
         "or_stable_sort": (None, [_i64, _U32, ctypes.c_uint32, _U32, _U32]),
         "or_stencil_1d": (_int, [_dbl, _dbl, _int, _I, _D, _D, _D, _D, _I]),
@@ -128,6 +130,17 @@ def _check(rc, what):
 
 
 # ---------------------------------------------------------------- modes / keys
+
+def set_threads(n: int) -> None:
+    """Host threads of P2G and G2P (1, the default, runs the plain serial
+    loops; more split G2P by particle and give P2G private grids summed in
+    thread order)."""
+    _load().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().or_get_threads())
+
 
 def mode_abc(r: int) -> tuple:
     out = (ctypes.c_int * 3)()

@@ -45,12 +45,18 @@
  *     [1.5 dx, (n - 1.5) dx] per axis instead of deleting particles.
  *
  * Build: plain C99, -O2 -ffp-contract=off (no fused multiply-add, so the FP32
- * decisions round exactly as documented).  Callers pass flat arrays.
+ * decisions round exactly as documented), -fopenmp for the optional host
+ * threads of P2G and G2P (or_set_threads; one thread by default).  Callers
+ * pass flat arrays.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_OK 0
 #define OR_ERR_ARG (-1)
@@ -336,12 +342,57 @@ int or_particle_modes(double px, double py, double pz, int alpha, int R,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Host threads for P2G and G2P (1 = the plain serial loops).  With more
+ * threads, G2P splits the particles between them (each particle's fit is
+ * independent) and P2G gives every thread private grids that are summed in
+ * thread order afterwards, so the result does not depend on timing.       */
+static int g_threads = 1;
+
+void or_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+int or_get_threads(void) { return g_threads; }
+
+/* ------------------------------------------------------------------------ */
 /* P2G: Eqs 1, 4 (mass), Eq 13 (PolyPIC momentum), Eqs 15-18 (phase masses).
  *   m_ia  += mt_p w_ipa
  *   mv_ia += mt_p w_ipa sum_{r<R} c_pra s_r(z_ipa)
  * mt_p = mass[p] (+ mass_abs[p] for solids, Eq 18).  Grids are zeroed first.
  * coeff: [3][R][np].  Grid a has dims face_dims(a), x fastest.
  * Returns OR_ERR_DOMAIN if a particle lies outside [dx, (n-1) dx).          */
+/* The deposit of particle p into the grids gm, gp (the body of or_p2g). */
+static void p2g_particle(int64_t np, int64_t p, const double *x, const double *y,
+                         const double *z, const double *mass, const double *mass_abs,
+                         const double *coeff, int R, int nx, int ny, int nz, double dx,
+                         int map, double dt, double *const gm[3], double *const gp[3])
+{
+    double mt = mass[p] + (mass_abs ? mass_abs[p] : 0.0);
+    double M[3][3];
+    if (map == 1) affine_matrix(coeff, R, np, p, dt, M);
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        axis_stencil st[3];
+        particle_stencils(x[p], y[p], z[p], a, dx, st);
+        for (int kz = 0; kz < 3; ++kz)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx) {
+                    double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
+                    double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
+                    if (map == 1) {
+                        double zm[3];
+                        for (int i = 0; i < 3; ++i)
+                            zm[i] = M[i][0] * zz[0] + M[i][1] * zz[1] + M[i][2] * zz[2];
+                        zz[0] = zm[0]; zz[1] = zm[1]; zz[2] = zm[2];
+                    }
+                    double S = 0.0;
+                    for (int r = 0; r < R; ++r)
+                        S += coeff[((int64_t)a * R + r) * np + p] * mode_value(st, r, zz);
+                    int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
+                    size_t idx = ((size_t)iz * d[1] + iy) * d[0] + ix;
+                    gm[a][idx] += mt * w;
+                    gp[a][idx] += mt * w * S;
+                }
+    }
+}
+
 int or_p2g(int64_t np, const double *x, const double *y, const double *z,
            const double *mass, const double *mass_abs, const double *coeff, int R,
            int nx, int ny, int nz, double dx, int map, double dt,
@@ -359,35 +410,47 @@ int or_p2g(int64_t np, const double *x, const double *y, const double *z,
     for (int64_t p = 0; p < np; ++p)
         if (!in_domain(x[p], y[p], z[p], nx, ny, nz, dx)) return OR_ERR_DOMAIN;
 
-    for (int64_t p = 0; p < np; ++p) {
-        double mt = mass[p] + (mass_abs ? mass_abs[p] : 0.0);
-        double M[3][3];
-        if (map == 1) affine_matrix(coeff, R, np, p, dt, M);
+    if (g_threads <= 1) {
+        for (int64_t p = 0; p < np; ++p)
+            p2g_particle(np, p, x, y, z, mass, mass_abs, coeff, R, nx, ny, nz, dx, map, dt, gm, gp);
+        return OR_OK;
+    }
+    /* private grids per thread, summed in thread order */
+    int T = g_threads;
+    size_t cnt[3], tot = 0;
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        cnt[a] = (size_t)d[0] * d[1] * d[2];
+        tot += 2 * cnt[a];
+    }
+    double *priv = (double *)calloc((size_t)T * tot, sizeof(double));
+    if (!priv) return OR_ERR_ARG;
+#pragma omp parallel num_threads(T)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        double *base = priv + (size_t)t * tot;
+        double *pm[3], *pv[3];
         for (int a = 0; a < 3; ++a) {
-            int d[3]; face_dims(a, nx, ny, nz, d);
-            axis_stencil st[3];
-            particle_stencils(x[p], y[p], z[p], a, dx, st);
-            for (int kz = 0; kz < 3; ++kz)
-                for (int ky = 0; ky < 3; ++ky)
-                    for (int kx = 0; kx < 3; ++kx) {
-                        double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
-                        double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
-                        if (map == 1) {
-                            double zm[3];
-                            for (int i = 0; i < 3; ++i)
-                                zm[i] = M[i][0] * zz[0] + M[i][1] * zz[1] + M[i][2] * zz[2];
-                            zz[0] = zm[0]; zz[1] = zm[1]; zz[2] = zm[2];
-                        }
-                        double S = 0.0;
-                        for (int r = 0; r < R; ++r)
-                            S += coeff[((int64_t)a * R + r) * np + p] * mode_value(st, r, zz);
-                        int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
-                        size_t idx = ((size_t)iz * d[1] + iy) * d[0] + ix;
-                        gm[a][idx] += mt * w;
-                        gp[a][idx] += mt * w * S;
-                    }
+            pm[a] = base;
+            pv[a] = base + cnt[a];
+            base += 2 * cnt[a];
+        }
+#pragma omp for schedule(static)
+        for (int64_t p = 0; p < np; ++p)
+            p2g_particle(np, p, x, y, z, mass, mass_abs, coeff, R, nx, ny, nz, dx, map, dt, pm, pv);
+    }
+    for (int t = 0; t < T; ++t) {
+        double *base = priv + (size_t)t * tot;
+        for (int a = 0; a < 3; ++a) {
+            for (size_t i = 0; i < cnt[a]; ++i) gm[a][i] += base[i];
+            for (size_t i = 0; i < cnt[a]; ++i) gp[a][i] += base[cnt[a] + i];
+            base += 2 * cnt[a];
         }
     }
+    free(priv);
     return OR_OK;
 }
 
@@ -466,6 +529,7 @@ int or_g2p(int64_t np, const double *x, const double *y, const double *z,
     for (int64_t p = 0; p < np; ++p)
         if (!in_domain(x[p], y[p], z[p], nx, ny, nz, dx)) return OR_ERR_DOMAIN;
     int n3[3] = {nx, ny, nz};
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
     for (int64_t p = 0; p < np; ++p) {
         double pos[3] = {x[p], y[p], z[p]};
         double vp[3];

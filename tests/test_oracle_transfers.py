@@ -549,3 +549,25 @@ def test_affine_map_with_four_modes_is_a_transform_of_the_linear_coefficients():
     _, gt = oracle.p2g(x, mass, ct, n, dx)
     for a in range(3):
         assert np.abs(gp[a] - gt[a]).max() <= 1e-12 * np.abs(gt[a]).max()
+
+
+def test_host_threads_give_the_serial_result():
+    """The optional host threads (the all-core CPU baseline): G2P splits
+    independent particles, so its output is bit-identical; P2G sums private
+    grids in thread order, so it agrees to FP64 rounding."""
+    sc = scenes.parity_scene(n=16, R=27, seed=21, random_mode_init=True)
+    f = sc.fluid
+    assert oracle.get_threads() == 1
+    gm1, gp1 = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx)
+    gv = oracle.grid_update(sc.n, sc.dt, (0.0, -9.81, 0.0), gm1, gp1)
+    c1, x1 = oracle.g2p(f.x, gv, 27, sc.n, sc.dx, sc.dt)
+    try:
+        oracle.set_threads(4)
+        gm4, gp4 = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx)
+        c4, x4 = oracle.g2p(f.x, gv, 27, sc.n, sc.dx, sc.dt)
+    finally:
+        oracle.set_threads(1)
+    for a in range(3):
+        assert np.allclose(gm4[a], gm1[a], rtol=1e-13, atol=1e-13 * np.abs(gm1[a]).max())
+        assert np.allclose(gp4[a], gp1[a], rtol=1e-13, atol=1e-13 * np.abs(gp1[a]).max())
+    assert np.array_equal(c4, c1) and np.array_equal(x4, x1)
