@@ -599,6 +599,8 @@ int or_p2g_adjoint(int64_t np, const double *x, const double *y, const double *z
     double *lpos[3] = {lx, ly, lz};
     for (int64_t p = 0; p < np; ++p)
         if (!in_domain(x[p], y[p], z[p], nx, ny, nz, dx)) return OR_ERR_DOMAIN;
+    /* each particle writes only its own entries of lc and lx, ly, lz */
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
     for (int64_t p = 0; p < np; ++p) {
         double mt = mass[p] + (mass_abs ? mass_abs[p] : 0.0);
         for (int a = 0; a < 3; ++a) {
@@ -676,6 +678,89 @@ void or_grid_update_adjoint(int nx, int ny, int nz,
 /* G2P adjoint with the advection.  Given lc_out = dL/dc'_pra ([3][R][np]) and
  * lxo = dL/dx'_p, adds dL/dv~_ia to lv0..2 (the caller zeroes them) and adds
  * dL/dx_p to lx, ly, lz.  Clamped axes pass no gradient through the advection. */
+/* The adjoint of particle p's fit and advection (the body of or_g2p_adjoint):
+ * adds its grid-velocity adjoint to lv and writes its position adjoint. */
+static void g2p_adjoint_particle(int64_t np, int64_t p, const double *x, const double *y,
+                                 const double *z, const double *const gv[3], int R,
+                                 const int n3[3], double dx, double dt, const double *lc_out,
+                                 const double *const lpo[3], double *const lv[3],
+                                 double *const lpos[3])
+{
+    int nx = n3[0], ny = n3[1], nz = n3[2];
+    double pos[3] = {x[p], y[p], z[p]};
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        axis_stencil st[3];
+        particle_stencils(x[p], y[p], z[p], a, dx, st);
+        /* forward quantities: num_r, den_r and their x-derivatives */
+        double num[27], den[27], dnum[27][3], dden[27][3];
+        for (int r = 0; r < R; ++r) {
+            num[r] = den[r] = 0.0;
+            for (int b = 0; b < 3; ++b) dnum[r][b] = dden[r][b] = 0.0;
+        }
+        for (int kz = 0; kz < 3; ++kz)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx) {
+                    int k3[3] = {kx, ky, kz};
+                    double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
+                    double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
+                    int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
+                    double v = gv[a][((size_t)iz * d[1] + iy) * d[0] + ix];
+                    for (int r = 0; r < R; ++r) {
+                        double s = mode_value(st, r, zz);
+                        num[r] += w * s * v;
+                        den[r] += w * s * s;
+                        for (int b = 0; b < 3; ++b) {
+                            double dwb = 1.0, ds = 1.0;
+                            for (int e = 0; e < 3; ++e) {
+                                dwb *= (e == b) ? st[e].dw[k3[e]] : st[e].w[k3[e]];
+                                int deg = g_modes[r][e];
+                                ds *= (e == b) ? basis_df(&st[e], deg, zz[e], -1.0)
+                                               : basis_f(&st[e], deg, zz[e]);
+                            }
+                            dnum[r][b] += (dwb * s + w * ds) * v;
+                            dden[r][b] += dwb * s * s + 2.0 * w * s * ds;
+                        }
+                    }
+                }
+        /* adjoint seed on the output coefficients, plus advection */
+        double mu[27];
+        for (int r = 0; r < R; ++r) mu[r] = lc_out[((int64_t)a * R + r) * np + p];
+        double c0 = num[0] / den[0];
+        double lo = 1.5 * dx, hi = ((double)n3[a] - 1.5) * dx;
+        double xn = pos[a] + dt * c0;
+        if (xn >= lo && xn <= hi) {
+            mu[0] += dt * lpo[a][p];
+            lpos[a][p] += lpo[a][p];
+        }
+        for (int r = 0; r < R; ++r) {
+            int guarded = (g_modes[r][0] == 2 && st[0].guard) ||
+                          (g_modes[r][1] == 2 && st[1].guard) ||
+                          (g_modes[r][2] == 2 && st[2].guard);
+            if (guarded || mu[r] == 0.0) continue;
+            double c = num[r] / den[r];
+            for (int b = 0; b < 3; ++b)
+                lpos[b][p] += mu[r] * (dnum[r][b] - c * dden[r][b]) / den[r];
+        }
+        for (int kz = 0; kz < 3; ++kz)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx) {
+                    double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
+                    double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
+                    int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
+                    double acc = 0.0;
+                    for (int r = 0; r < R; ++r) {
+                        int guarded = (g_modes[r][0] == 2 && st[0].guard) ||
+                                      (g_modes[r][1] == 2 && st[1].guard) ||
+                                      (g_modes[r][2] == 2 && st[2].guard);
+                        if (guarded) continue;
+                        acc += mu[r] * w * mode_value(st, r, zz) / den[r];
+                    }
+                    lv[a][((size_t)iz * d[1] + iy) * d[0] + ix] += acc;
+                }
+    }
+}
+
 int or_g2p_adjoint(int64_t np, const double *x, const double *y, const double *z,
                    const double *gv0, const double *gv1, const double *gv2, int R,
                    int nx, int ny, int nz, double dx, double dt,
@@ -692,80 +777,41 @@ int or_g2p_adjoint(int64_t np, const double *x, const double *y, const double *z
     int n3[3] = {nx, ny, nz};
     for (int64_t p = 0; p < np; ++p)
         if (!in_domain(x[p], y[p], z[p], nx, ny, nz, dx)) return OR_ERR_DOMAIN;
-    for (int64_t p = 0; p < np; ++p) {
-        double pos[3] = {x[p], y[p], z[p]};
+    if (g_threads <= 1) {
+        for (int64_t p = 0; p < np; ++p)
+            g2p_adjoint_particle(np, p, x, y, z, gv, R, n3, dx, dt, lc_out, lpo, lv, lpos);
+        return OR_OK;
+    }
+    /* private grid adjoints per thread, added to lv in thread order */
+    int T = g_threads;
+    size_t cnt[3], tot = 0;
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        cnt[a] = (size_t)d[0] * d[1] * d[2];
+        tot += cnt[a];
+    }
+    double *priv = (double *)calloc((size_t)T * tot, sizeof(double));
+    if (!priv) return OR_ERR_ARG;
+#pragma omp parallel num_threads(T)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        double *base = priv + (size_t)t * tot;
+        double *pl[3] = {base, base + cnt[0], base + cnt[0] + cnt[1]};
+#pragma omp for schedule(static)
+        for (int64_t p = 0; p < np; ++p)
+            g2p_adjoint_particle(np, p, x, y, z, gv, R, n3, dx, dt, lc_out, lpo, pl, lpos);
+    }
+    for (int t = 0; t < T; ++t) {
+        double *base = priv + (size_t)t * tot;
         for (int a = 0; a < 3; ++a) {
-            int d[3]; face_dims(a, nx, ny, nz, d);
-            axis_stencil st[3];
-            particle_stencils(x[p], y[p], z[p], a, dx, st);
-            /* forward quantities: num_r, den_r and their x-derivatives */
-            double num[27], den[27], dnum[27][3], dden[27][3];
-            for (int r = 0; r < R; ++r) {
-                num[r] = den[r] = 0.0;
-                for (int b = 0; b < 3; ++b) dnum[r][b] = dden[r][b] = 0.0;
-            }
-            for (int kz = 0; kz < 3; ++kz)
-                for (int ky = 0; ky < 3; ++ky)
-                    for (int kx = 0; kx < 3; ++kx) {
-                        int k3[3] = {kx, ky, kz};
-                        double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
-                        double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
-                        int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
-                        double v = gv[a][((size_t)iz * d[1] + iy) * d[0] + ix];
-                        for (int r = 0; r < R; ++r) {
-                            double s = mode_value(st, r, zz);
-                            num[r] += w * s * v;
-                            den[r] += w * s * s;
-                            for (int b = 0; b < 3; ++b) {
-                                double dwb = 1.0, ds = 1.0;
-                                for (int e = 0; e < 3; ++e) {
-                                    dwb *= (e == b) ? st[e].dw[k3[e]] : st[e].w[k3[e]];
-                                    int deg = g_modes[r][e];
-                                    ds *= (e == b) ? basis_df(&st[e], deg, zz[e], -1.0)
-                                                   : basis_f(&st[e], deg, zz[e]);
-                                }
-                                dnum[r][b] += (dwb * s + w * ds) * v;
-                                dden[r][b] += dwb * s * s + 2.0 * w * s * ds;
-                            }
-                        }
-                    }
-            /* adjoint seed on the output coefficients, plus advection */
-            double mu[27];
-            for (int r = 0; r < R; ++r) mu[r] = lc_out[((int64_t)a * R + r) * np + p];
-            double c0 = num[0] / den[0];
-            double lo = 1.5 * dx, hi = ((double)n3[a] - 1.5) * dx;
-            double xn = pos[a] + dt * c0;
-            if (xn >= lo && xn <= hi) {
-                mu[0] += dt * lpo[a][p];
-                lpos[a][p] += lpo[a][p];
-            }
-            for (int r = 0; r < R; ++r) {
-                int guarded = (g_modes[r][0] == 2 && st[0].guard) ||
-                              (g_modes[r][1] == 2 && st[1].guard) ||
-                              (g_modes[r][2] == 2 && st[2].guard);
-                if (guarded || mu[r] == 0.0) continue;
-                double c = num[r] / den[r];
-                for (int b = 0; b < 3; ++b)
-                    lpos[b][p] += mu[r] * (dnum[r][b] - c * dden[r][b]) / den[r];
-            }
-            for (int kz = 0; kz < 3; ++kz)
-                for (int ky = 0; ky < 3; ++ky)
-                    for (int kx = 0; kx < 3; ++kx) {
-                        double w = st[0].w[kx] * st[1].w[ky] * st[2].w[kz];
-                        double zz[3] = {st[0].z[kx], st[1].z[ky], st[2].z[kz]};
-                        int ix = st[0].base + kx, iy = st[1].base + ky, iz = st[2].base + kz;
-                        double acc = 0.0;
-                        for (int r = 0; r < R; ++r) {
-                            int guarded = (g_modes[r][0] == 2 && st[0].guard) ||
-                                          (g_modes[r][1] == 2 && st[1].guard) ||
-                                          (g_modes[r][2] == 2 && st[2].guard);
-                            if (guarded) continue;
-                            acc += mu[r] * w * mode_value(st, r, zz) / den[r];
-                        }
-                        lv[a][((size_t)iz * d[1] + iy) * d[0] + ix] += acc;
-                    }
+            for (size_t i = 0; i < cnt[a]; ++i) lv[a][i] += base[i];
+            base += cnt[a];
         }
     }
+    free(priv);
     return OR_OK;
 }
 

@@ -552,22 +552,34 @@ def test_affine_map_with_four_modes_is_a_transform_of_the_linear_coefficients():
 
 
 def test_host_threads_give_the_serial_result():
-    """The optional host threads (the all-core CPU baseline): G2P splits
-    independent particles, so its output is bit-identical; P2G sums private
-    grids in thread order, so it agrees to FP64 rounding."""
+    """The optional host threads (the all-core CPU baseline and the adjoint
+    gate at full size): G2P and the P2G adjoint split independent particles,
+    so their outputs are bit-identical; P2G and the G2P adjoint's grid part
+    sum private grids in thread order, so they agree to FP64 rounding."""
     sc = scenes.parity_scene(n=16, R=27, seed=21, random_mode_init=True)
     f = sc.fluid
     assert oracle.get_threads() == 1
     gm1, gp1 = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx)
     gv = oracle.grid_update(sc.n, sc.dt, (0.0, -9.81, 0.0), gm1, gp1)
     c1, x1 = oracle.g2p(f.x, gv, 27, sc.n, sc.dx, sc.dt)
+    rng = np.random.default_rng(22)
+    lc = rng.standard_normal(c1.shape)
+    lxo = rng.standard_normal(x1.shape)
+    lv1, lx1 = oracle.g2p_adjoint(f.x, gv, 27, sc.n, sc.dx, sc.dt, lc, lxo)
+    lm = [rng.standard_normal(g.shape) for g in gm1]
+    lp = [rng.standard_normal(g.shape) for g in gm1]
+    la1, lxa1 = oracle.p2g_adjoint(f.x, f.mass, f.coeff, sc.n, sc.dx, lm, lp)
     try:
         oracle.set_threads(4)
         gm4, gp4 = oracle.p2g(f.x, f.mass, f.coeff, sc.n, sc.dx)
         c4, x4 = oracle.g2p(f.x, gv, 27, sc.n, sc.dx, sc.dt)
+        lv4, lx4 = oracle.g2p_adjoint(f.x, gv, 27, sc.n, sc.dx, sc.dt, lc, lxo)
+        la4, lxa4 = oracle.p2g_adjoint(f.x, f.mass, f.coeff, sc.n, sc.dx, lm, lp)
     finally:
         oracle.set_threads(1)
     for a in range(3):
         assert np.allclose(gm4[a], gm1[a], rtol=1e-13, atol=1e-13 * np.abs(gm1[a]).max())
         assert np.allclose(gp4[a], gp1[a], rtol=1e-13, atol=1e-13 * np.abs(gp1[a]).max())
+        assert np.allclose(lv4[a], lv1[a], rtol=1e-13, atol=1e-13 * np.abs(lv1[a]).max())
     assert np.array_equal(c4, c1) and np.array_equal(x4, x1)
+    assert np.array_equal(lx4, lx1) and np.array_equal(la4, la1) and np.array_equal(lxa4, lxa1)
