@@ -24,8 +24,13 @@
  *    (c, b, a).  num_modes = 1 (PIC), 4 (APIC), 8 (the paper's setting),
  *    27 (full PolyPIC) take prefixes of this order.
  *  - Particle arrays are structure-of-arrays in device memory owned by the
- *    caller.  Coefficients are laid out [3][num_modes][count]: element
- *    (a, r, p) at (a * num_modes + r) * count + p.
+ *    caller.  FP32 coefficients are laid out [3][num_modes][count]: element
+ *    (a, r, p) at (a * num_modes + r) * count + p.  The 16-bit formats pack
+ *    two modes per 32-bit word: [3][H][count] words, H = (num_modes + 1) / 2,
+ *    word (a, k, p) at (a * H + k) * count + p holding the code of mode 2k in
+ *    its low 16 bits and of mode 2k + 1 in its high 16 bits (0 when
+ *    2k + 1 = num_modes), so that one 4-byte load serves two modes of a
+ *    particle.  Coefficient arrays must be 4-byte aligned.
  *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
  *    default stream).  Arguments are validated on the host before anything
  *    is launched; a bad argument returns an error and launches nothing.  No
@@ -109,8 +114,9 @@ typedef struct polypic_config {
  *   x[3]        [count] float positions (in)
  *   mass        [count] float particle mass m_p (in)
  *   mass_abs    [count] float absorbed fluid mass, or NULL for fluid (Eq 18)
- *   coeff       [3][num_modes][count]: float for POLYPIC_COEFF_F32; for the
- *               16-bit formats uint16 codes of c_pra dx^L_r / s_p, where L_r
+ *   coeff       [3][num_modes][count] float for POLYPIC_COEFF_F32; for the
+ *               16-bit formats [3][(num_modes + 1) / 2][count] words of two
+ *               codes (see above), the codes of c_pra dx^L_r / s_p, where L_r
  *               is the total degree of mode r and s_p = max |c_pra dx^L_r|
  *   coeff_scale [count] float s_p (16-bit formats only, else NULL)
  *   key, perm   [count] uint32, written by polypic_sort (perm: slot order)

@@ -62,6 +62,8 @@ polypic_status check_sorted(const polypic_particles *p) {
 polypic_status check_coeff(const polypic_ctx *c, const polypic_particles *p) {
     if (p->count == 0) return POLYPIC_OK;
     if (!p->coeff || !p->mass) return POLYPIC_ERR_INVALID_ARG;
+    // FP32 values and the 16-bit formats' code pairs are 32-bit words
+    if (((uintptr_t)p->coeff & 3u) != 0) return POLYPIC_ERR_INVALID_ARG;
     if (c->cfg.coeff_format != POLYPIC_COEFF_F32 && !p->coeff_scale) return POLYPIC_ERR_INVALID_ARG;
     return POLYPIC_OK;
 }
@@ -165,6 +167,7 @@ polypic_status check_g2p_out(const polypic_ctx *c, const polypic_particles *in,
     if (in->count == 0) return POLYPIC_OK;
     if (!out->x[0] || !out->x[1] || !out->x[2] || !out->mass || !out->coeff)
         return POLYPIC_ERR_INVALID_ARG;
+    if (((uintptr_t)out->coeff & 3u) != 0) return POLYPIC_ERR_INVALID_ARG;
     if (c->cfg.coeff_format != POLYPIC_COEFF_F32 && !out->coeff_scale) return POLYPIC_ERR_INVALID_ARG;
     if (in->mass_abs && !out->mass_abs) return POLYPIC_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)

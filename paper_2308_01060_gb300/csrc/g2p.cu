@@ -13,8 +13,9 @@
 // so no denominator is formed; the guard zeroes G2 on a guarded axis.  The
 // FP32 output folds 1/dx and 1/dx^2 into the degree-1 and degree-2 factors and
 // so comes out in physical units; the 16-bit formats fit c dx^L, divide by the
-// per-particle scale s_p = max |c dx^L| and round to nearest even.  Outputs
-// are written in sorted slot order (coalesced).  With Eq 10's gradient form
+// per-particle scale s_p = max |c dx^L| and round to nearest even, two codes
+// (modes 2k and 2k + 1) per 32-bit word.  Outputs are written in sorted slot
+// order (coalesced).  With Eq 10's gradient form
 // (4 modes) the linear modes are sum_i dw_ipa/dx_p v~_ia instead of the fit.
 #include <type_traits>
 
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
             }
         };
         float vel[3];
-        T *out = ocoeff + j;  // row (a, r) starts (a R + r) * cnt elements in
+        T *out = ocoeff + j;  // FP32: row (a, r) starts (a R + r) * cnt elements in
         if constexpr (FMT == POLYPIC_COEFF_F32) {
             // each component's coefficients leave as soon as they are fitted,
             // spreading the stores over the particle's arithmetic
@@ -133,10 +134,18 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) s = fmaxf(s, fabsf(Chat[a][r]));
             const float inv = s > 0.0f ? 1.0f / s : 0.0f;
+            // word (a H + k, j), H = (R + 1) / 2: modes 2k (low half) and 2k + 1
+            constexpr int H = (R + 1) / 2;
+            uint32_t *ow = reinterpret_cast<uint32_t *>(A.ocoeff) + j;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int r = 0; r < R; ++r, out += cnt) *out = Codec<FMT>::encode(Chat[a][r] * inv);
+                for (int k = 0; k < H; ++k, ow += cnt) {
+                    const uint32_t lo = Codec<FMT>::bits(Codec<FMT>::encode(Chat[a][2 * k] * inv));
+                    const uint32_t hi = 2 * k + 1 < R
+                        ? Codec<FMT>::bits(Codec<FMT>::encode(Chat[a][2 * k + 1] * inv)) : 0u;
+                    *ow = lo | (hi << 16);
+                }
             A.oscale[j] = s;
 #pragma unroll
             for (int a = 0; a < 3; ++a) vel[a] = Chat[a][0];

@@ -43,13 +43,17 @@ template <int A> __host__ __device__ constexpr int deg_z(int du, int dv, int dw)
 // ---------------------------------------------------------------- staging
 // Each lane prefetches its next particles with cp.async (4-byte copies) into
 // a private multi-stage buffer laid out [stage][value][lane] (conflict-free):
-// x, y, z, m, m_abs, s_p, the particle index, then one 32-bit word per mode
-// (the coefficient, or for 16-bit formats the aligned word holding its code).
-// With Eq 12's affine map (AFF) six more words follow: the linear-mode
-// coefficients of the two other components (their C rows).
-template <int R, bool AFF = false> struct Stage {
+// x, y, z, m, m_abs, s_p, the particle index, then the coefficient words: one
+// per mode for FP32, one per pair of modes for the 16-bit formats (whose
+// words hold two codes).  With Eq 12's affine map (AFF) six more words
+// follow: the linear-mode coefficients of the two other components (their C
+// rows).
+__host__ __device__ constexpr int coeff_words(int R, int FMT) {
+    return FMT == POLYPIC_COEFF_F32 ? R : (R + 1) / 2;
+}
+template <int R, bool AFF = false, int FMT = POLYPIC_COEFF_F32> struct Stage {
     static constexpr int kX = 0, kY = 1, kZ = 2, kM = 3, kMabs = 4, kScale = 5, kIdx = 6, kC = 7;
-    static constexpr int kL = kC + R;
+    static constexpr int kL = kC + coeff_words(R, FMT);
     static constexpr int NV = kL + (AFF ? 6 : 0);
 };
 
@@ -67,7 +71,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 template <int R, int FMT, int A, bool ADJ, bool AFF = false>
 __device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, uint32_t slot,
                                                float *st, int lane) {
-    using S = Stage<R, AFF>;
+    using S = Stage<R, AFF, FMT>;
     cp_async4(st + S::kX * 32 + lane, P.x + p);
     cp_async4(st + S::kY * 32 + lane, P.y + p);
     cp_async4(st + S::kZ * 32 + lane, P.z + p);
@@ -99,22 +103,12 @@ __device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, uin
             }
         }
     } else {
+        // 16-bit codes: word (A H + k, p), H = (R + 1) / 2, holds modes 2k and 2k + 1
         cp_async4(st + S::kScale * 32 + lane, P.scale + p);
-        // byte offset of code (A R + r, p); its aligned 4-byte word holds it
-        const char *base = reinterpret_cast<const char *>(P.coeff);
-        int64_t b = 2 * ((int64_t)A * R * P.count + p);
-        const int64_t rstride = 2 * P.count;
+        constexpr int H = coeff_words(R, FMT);
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(P.coeff) + (int64_t)A * H * P.count + p;
 #pragma unroll
-        for (int r = 0; r < R; ++r, b += rstride) {
-            const int64_t w = b & ~(int64_t)3;
-            // only the array's last code can sit alone in a word at its end
-            if (A == 2 && r == R - 1 && w + 4 > (int64_t)6 * R * P.count) {
-                reinterpret_cast<uint32_t *>(st)[(S::kC + r) * 32 + lane] =
-                    *reinterpret_cast<const uint16_t *>(base + b);
-            } else {
-                cp_async4(st + (S::kC + r) * 32 + lane, base + w);
-            }
-        }
+        for (int k = 0; k < H; ++k, w += P.count) cp_async4(st + (S::kC + k) * 32 + lane, w);
     }
 }
 
@@ -273,7 +267,7 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
                                            const Stencil1D &fw, bool gu, bool gv, bool gw,
                                            float (&am)[4][3][3], float (&av)[4][3][3],
                                            float tu = 0.0f, float tv = 0.0f, float tw = 0.0f) {
-    using S = Stage<R, AFF>;
+    using S = Stage<R, AFF, FMT>;
     if constexpr (AFF && R > 4) {
         accumulate_mapped<R, A>(P, st, lane, mt, shift, tu, tv, tw, fu, fv, fw, am, av);
         return;
@@ -282,10 +276,6 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
     if constexpr (AFF) affine_linear<R, A>(st, lane, P.map_dt, cl);
     constexpr int D = axis_degrees(R);
     const float cscale = FMT == POLYPIC_COEFF_F32 ? 1.0f : st[S::kScale * 32 + lane];
-    // 16-bit codes: element e = (A R + r) count + p sits in the high half of
-    // its aligned word when e is odd; (A R + r) is a compile-time constant.
-    const uint32_t podd = reinterpret_cast<const uint32_t *>(st)[S::kIdx * 32 + lane] & 1u;
-    const uint32_t par_even_row = podd, par_odd_row = podd ^ (uint32_t)(P.count & 1);
     float Fu[D][3], Fv[D][3], Fw[D][3];
     if constexpr (ADJ) {
         fit_rows<D>(fu, gu, P.inv_dx, P.inv_dx2, Fu);
@@ -347,10 +337,10 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
                     } else if constexpr (FMT == POLYPIC_COEFF_F32) {
                         C[dv][dw] = st[(S::kC + r) * 32 + lane];
                     } else {
+                        // mode r is the low (r even) or high (r odd) half of word r / 2
                         const uint32_t word =
-                            reinterpret_cast<const uint32_t *>(st)[(S::kC + r) * 32 + lane];
-                        const uint32_t odd = ((A * R + r) & 1) ? par_odd_row : par_even_row;
-                        C[dv][dw] = Codec<FMT>::decode((uint16_t)(word >> (odd << 4)));
+                            reinterpret_cast<const uint32_t *>(st)[(S::kC + r / 2) * 32 + lane];
+                        C[dv][dw] = Codec<FMT>::decode((uint16_t)((r & 1) ? word >> 16 : word));
                     }
                 }
             }

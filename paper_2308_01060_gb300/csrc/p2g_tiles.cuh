@@ -26,10 +26,11 @@ __device__ __forceinline__ int region_index(int ix, int iy, int iz) {
     return (iz * Reg<A>::Y + iy) * Reg<A>::X + ix;
 }
 
-template <int R, bool AFF = false> constexpr int p2g_smem_bytes() {
-    return (kP2GWarps * kRegionFloats + kP2GWarps * kStages * Stage<R, AFF>::NV * 32) * 4;
+template <int R, bool AFF = false, int FMT = POLYPIC_COEFF_F32> constexpr int p2g_smem_bytes() {
+    return (kP2GWarps * kRegionFloats + kP2GWarps * kStages * Stage<R, AFF, FMT>::NV * 32) * 4;
 }
-static_assert(p2g_smem_bytes<27>() <= 227 * 1024, "P2G staging exceeds the shared memory of a CTA");
+static_assert(p2g_smem_bytes<27, true>() <= 227 * 1024,
+              "P2G staging exceeds the shared memory of a CTA");
 
 // The rounds of the three component passes form one stream (pass 0 rounds
 // 0 .. maxn-1, then pass 1, then pass 2) that flows through the stage ring
@@ -65,7 +66,7 @@ template <int R, int FMT, int A, bool ADJ, bool AFF>
 __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs, uint32_t n_c,
                                          uint32_t maxn, int ci, int cj, int ck, int gi, int gj,
                                          int gk, int lane, float *reg, float *stage, bool &bad) {
-    using S = Stage<R, AFF>;
+    using S = Stage<R, AFF, FMT>;
     const bool interior = gi >= 1 && gi <= P.g.n[0] - 2 && gj >= 1 && gj <= P.g.n[1] - 2 &&
                           gk >= 1 && gk <= P.g.n[2] - 2;
     float am[4][3][3], av[4][3][3];
@@ -146,7 +147,7 @@ __device__ __forceinline__ void p2g_block(const P2GArgs &P, uint32_t bs, uint32_
     q.pn = n_c > 0 ? P.perm[q.sn] : 0u;
 #pragma unroll
     for (int k = 0; k < kStages; ++k)
-        pipe_issue<R, FMT, ADJ, AFF>(P, q, bs, n_c, maxn, lt, stage + k * Stage<R, AFF>::NV * 32,
+        pipe_issue<R, FMT, ADJ, AFF>(P, q, bs, n_c, maxn, lt, stage + k * Stage<R, AFF, FMT>::NV * 32,
                                      lane);
     p2g_pass<R, FMT, 0, ADJ, AFF>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
     p2g_pass<R, FMT, 1, ADJ, AFF>(P, q, bs, n_c, maxn, ci, cj, ck, gi, gj, gk, lane, reg, stage, bad);
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 || (AFF && R > 4) ? 1
     const uint32_t bs = P.cell_start[b * 32];
     const uint32_t maxn = __reduce_max_sync(0xffffffffu, n_c);
     float *reg = s_reg + warp * kRegionFloats;
-    float *stage = s_stage + warp * kStages * Stage<R, AFF>::NV * 32;
+    float *stage = s_stage + warp * kStages * Stage<R, AFF, FMT>::NV * 32;
     if (lane == 0) s_empty[warp] = maxn == 0;
     if (maxn > 0) {
         for (int i = lane; i < kRegionFloats; i += 32) reg[i] = 0.0f;
@@ -224,16 +225,13 @@ __global__ void __launch_bounds__(kP2GWarps * 32, (R == 27 || (AFF && R > 4) ? 1
 
 template <int R, int FMT, bool ADJ, bool AFF = false>
 cudaError_t launch_tiles(const P2GArgs &P, int grid, cudaStream_t s) {
-    const int smem = p2g_smem_bytes<R, AFF>();
-    static int configured_device = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (configured_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_p2g_tiles<R, FMT, ADJ, AFF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured_device = dev;
-    }
+    const int smem = p2g_smem_bytes<R, AFF, FMT>();
+    // the attribute is a property of the kernel in the current context; it is
+    // set on every launch (a cheap host call), which keeps no state shared
+    // between host threads or devices
+    const cudaError_t e = cudaFuncSetAttribute(k_p2g_tiles<R, FMT, ADJ, AFF>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
     k_p2g_tiles<R, FMT, ADJ, AFF><<<grid, kP2GWarps * 32, smem, s>>>(P);
     return cudaGetLastError();
 }

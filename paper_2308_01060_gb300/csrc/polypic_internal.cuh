@@ -200,12 +200,14 @@ template <> struct Codec<POLYPIC_COEFF_BF16> {
         return __bfloat162float(__ushort_as_bfloat16(bits));
     }
     __device__ static __nv_bfloat16 encode(float v) { return __float2bfloat16_rn(v); }
+    __device__ static uint32_t bits(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
 };
 template <> struct Codec<POLYPIC_COEFF_F16> {
     using T = __half;
     __device__ static float load(const __half *p) { return __half2float(*p); }
     __device__ static float decode(uint16_t bits) { return __half2float(__ushort_as_half(bits)); }
     __device__ static __half encode(float v) { return __float2half_rn(v); }
+    __device__ static uint32_t bits(__half v) { return __half_as_ushort(v); }
 };
 
 // ---------------------------------------------------------------- launch helpers

@@ -144,7 +144,9 @@ def _stream(stream) -> _vp:
 @dataclass
 class ParticleState:
     """One phase of particles on the GPU.  x: (3, P) float32; coeff: (3, R, P)
-    float32, or bfloat16 / float16 codes with scale (P,) for the 16-bit formats;
+    float32, or for the 16-bit formats bfloat16 / float16 codes shaped
+    (3, (R + 1) // 2, P, 2) (mode 2k of particle p at [a, k, p, 0], mode 2k + 1
+    at [a, k, p, 1]: the library's word layout) with scale (P,);
     key, perm: (P,) int32 holding uint32; cell_start: (K + 1,) int32."""
     x: torch.Tensor
     mass: torch.Tensor
@@ -233,6 +235,7 @@ class Context:
         self.dx = float(dx)
         self.num_modes = int(num_modes)
         self.coeff_format = coeff_format
+        self.variant = bool(map_affine or apic_grad_w)
         self.num_keys = int(L.polypic_num_keys(h))
 
     @property
@@ -261,6 +264,11 @@ class Context:
         return torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
 
     # -------------------------------------------------------------- allocation helpers
+    def coeff_shape(self, count: int):
+        """Shape of a phase's coefficient tensor (see ParticleState)."""
+        R = self.num_modes
+        return (3, R, count) if self.coeff_format == "f32" else (3, (R + 1) // 2, count, 2)
+
     def coeff_dtype(self):
         return {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[self.coeff_format]
 
@@ -269,7 +277,7 @@ class Context:
         return ParticleState(
             x=torch.empty((3, count), dtype=torch.float32, device=device),
             mass=torch.empty(count, dtype=torch.float32, device=device),
-            coeff=torch.zeros((3, R, count), dtype=self.coeff_dtype(), device=device),
+            coeff=torch.zeros(self.coeff_shape(count), dtype=self.coeff_dtype(), device=device),
             key=torch.empty(count, dtype=torch.int32, device=device),
             perm=torch.empty(count, dtype=torch.int32, device=device),
             cell_start=torch.empty(self.num_keys + 1, dtype=torch.int32, device=device),
@@ -411,8 +419,9 @@ def polypic_check_device_status(ctx: Context, stream=None) -> int:
 # ------------------------------------------------------------------ conveniences
 
 def upload_particles(ctx: Context, x, mass, coeff=None, mass_abs=None, device="cuda") -> ParticleState:
-    """Copy host arrays (NumPy or torch) into a new ParticleState (FP32 coefficients
-    are copied as given; for 16-bit contexts the caller encodes first)."""
+    """Copy host arrays (NumPy or torch) into a new ParticleState (FP32
+    coefficients are copied as given; 16-bit contexts start from zero codes
+    and get theirs from G2P)."""
     P = int(x.shape[1])
     ps = ctx.new_particles(P, solid=mass_abs is not None, device=device)
     ps.x.copy_(torch.as_tensor(x, dtype=torch.float32))
@@ -420,5 +429,7 @@ def upload_particles(ctx: Context, x, mass, coeff=None, mass_abs=None, device="c
     if mass_abs is not None:
         ps.mass_abs.copy_(torch.as_tensor(mass_abs, dtype=torch.float32))
     if coeff is not None:
-        ps.coeff.copy_(torch.as_tensor(coeff, dtype=torch.float32).to(ps.coeff.dtype))
+        if ctx.coeff_format != "f32":
+            raise ValueError("upload_particles: 16-bit contexts take their codes from G2P")
+        ps.coeff.copy_(torch.as_tensor(coeff, dtype=torch.float32))
     return ps

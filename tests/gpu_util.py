@@ -29,6 +29,23 @@ def max_rel(a, b):
     return float(np.abs(a - b).max() / (m if m > 0 else 1.0))
 
 
+def codes(ps, R):
+    """The 16-bit codes of a phase as a (3, R, P) float32 tensor in mode order
+    (the library stores modes 2k and 2k + 1 as the halves of one word)."""
+    c = ps.coeff
+    H = c.shape[1]
+    return c.permute(0, 1, 3, 2).reshape(3, 2 * H, c.shape[2])[:, :R].float()
+
+
+def decoded(ps, R, dx):
+    """Physical coefficients (3, R, P) float64 of a 16-bit phase:
+    code * s_p / dx^L_r."""
+    from paper_2308_01060_gb300 import scenes
+    dxl = dx ** scenes.mode_degrees(R).astype(np.float64)
+    return (np_(codes(ps, R)).astype(np.float64) * np_(ps.scale).astype(np.float64)[None, None, :]
+            / dxl[None, :, None])
+
+
 def upload(ctx, ps_host, device="cuda"):
     """scenes.ParticleSet -> pp.ParticleState (FP32 coefficients or zeros)."""
     coeff = ps_host.coeff

@@ -26,7 +26,7 @@ import oracle
 import slot_layout
 from paper_2308_01060_gb300 import polypic as pp
 from paper_2308_01060_gb300 import scenes
-from gpu_util import max_rel, np_, rel, u32, upload
+from gpu_util import codes, max_rel, np_, rel, u32, upload
 
 pytestmark = pytest.mark.gpu
 
@@ -210,7 +210,7 @@ def test_full_size_bf16_conservation(dam_break):
     pp.polypic_p2g(ctx, a, g, ws)
     torch.cuda.synchronize()
     mass = np_(a.mass).astype(np.float64)
-    c0 = np_(a.coeff[:, 0].float()).astype(np.float64) * np_(a.scale).astype(np.float64)[None]
+    c0 = np_(codes(a, 27)[:, 0]).astype(np.float64) * np_(a.scale).astype(np.float64)[None]
     for k in range(3):
         assert abs(np_(g.mass[k]).astype(np.float64).sum() / mass.sum() - 1.0) < 1e-5
         p_tot = float(np.sum(mass * c0[k]))

@@ -250,19 +250,21 @@ def test_g2p_flags_non_finite_velocity():
     assert pp.polypic_check_device_status(ctx) == 0       # reading clears the latch
 
 
-def _offset_particles(ctx, count, shift):
-    """Output arrays whose first element sits `shift` elements past an
-    allocation start, so that rows begin at every 16-byte phase."""
-    def buf(shape, dtype):
+def _offset_particles(ctx, count, shift, coeff_shift=None):
+    """Output arrays whose first element sits `shift` 4-byte words past an
+    allocation start, so that rows begin at every 16-byte phase (the 16-bit
+    codes are stored in 4-byte pairs; coeff_shift, in codes, overrides)."""
+    def buf(shape, dtype, sh):
         n = int(np.prod(shape))
-        return torch.zeros(n + shift, dtype=dtype, device="cuda")[shift:].view(shape)
+        return torch.zeros(n + sh, dtype=dtype, device="cuda")[sh:].view(shape)
 
     ref = ctx.new_particles(count)
+    cs = coeff_shift if coeff_shift is not None else shift * (4 // ref.coeff.element_size())
     return pp.ParticleState(
-        x=buf((3, count), torch.float32), mass=buf((count,), torch.float32),
-        coeff=buf(tuple(ref.coeff.shape), ref.coeff.dtype), key=ref.key, perm=ref.perm,
+        x=buf((3, count), torch.float32, shift), mass=buf((count,), torch.float32, shift),
+        coeff=buf(tuple(ref.coeff.shape), ref.coeff.dtype, cs), key=ref.key, perm=ref.perm,
         cell_start=ref.cell_start,
-        scale=None if ref.scale is None else buf((count,), torch.float32))
+        scale=None if ref.scale is None else buf((count,), torch.float32, shift))
 
 
 @pytest.mark.parametrize("fmt", ["f32", "bf16"])
@@ -289,6 +291,10 @@ def test_g2p_output_alignment_does_not_change_results(fmt, shift):
                        ref.coeff.view(torch.int16) if fmt != "f32" else ref.coeff)
     if fmt != "f32":
         assert torch.equal(out.scale, ref.scale)
+        # code pairs that do not start on a 4-byte boundary are refused
+        bad = _offset_particles(ctx, ps.count, shift, coeff_shift=1)
+        with pytest.raises(pp.PolyPICError, match="INVALID_ARG|invalid"):
+            pp.polypic_g2p(ctx, g, ps, bad, 1e-3, ws)
     assert pp.polypic_check_device_status(ctx) == 0
 
 

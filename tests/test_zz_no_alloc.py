@@ -19,8 +19,8 @@ import pytest
 import oracle
 from paper_2308_01060_gb300 import polypic as pp
 from paper_2308_01060_gb300 import scenes
-from gpu_util import (assert_close, grid_from_host, np_, random_grid_velocity, sorted_particles,
-                      upload)
+from gpu_util import (assert_close, decoded, grid_from_host, np_, random_grid_velocity,
+                      sorted_particles)
 
 TOL = 1e-5
 N = 32
@@ -59,11 +59,7 @@ def _state(ctx, fmt, f, seed):
     ps = ctx.new_particles(ps0.count)
     pp.polypic_g2p(ctx, g, ps0, ps, 0.0, ws)        # dt = 0: positions unchanged
     pp.polypic_sort(ctx, ps, ws)
-    codes = np_(ps.coeff.float()).astype(np.float64)
-    scale = np_(ps.scale).astype(np.float64)
-    dxl = ctx.dx ** scenes.mode_degrees(R).astype(np.float64)
-    coeff = codes * scale[None, None, :] / dxl[None, :, None]
-    return ps, ws, coeff, np_(ps.x), np_(ps.mass)
+    return ps, ws, decoded(ps, R, ctx.dx), np_(ps.x), np_(ps.mass)
 
 
 @pytest.mark.gpu
