@@ -112,6 +112,45 @@ __device__ __forceinline__ void stage_particle(const P2GArgs &P, uint32_t p, uin
     }
 }
 
+// A lane's footprint on face grid A: 4 x 3 x 3 nodes (d along the face axis,
+// the lowest node cell - 1; kv, kw along the other two axes), mass and
+// momentum.  The kw = 0, 1 entries are float2 pairs so that packed FP32 FMAs
+// update both at once; each lane of a packed FMA rounds as fmaf does, so the
+// sums carry the same bits as scalar FMAs in the same order.
+struct Foot {
+    float2 m2[4][3], v2[4][3];  // kw = 0 (x), kw = 1 (y)
+    float m1[4][3], v1[4][3];   // kw = 2
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int kv = 0; kv < 3; ++kv) {
+                m2[d][kv] = v2[d][kv] = make_float2(0.0f, 0.0f);
+                m1[d][kv] = v1[d][kv] = 0.0f;
+            }
+    }
+    __device__ __forceinline__ float m(int d, int kv, int kw) const {
+        return kw == 0 ? m2[d][kv].x : (kw == 1 ? m2[d][kv].y : m1[d][kv]);
+    }
+    __device__ __forceinline__ float v(int d, int kv, int kw) const {
+        return kw == 0 ? v2[d][kv].x : (kw == 1 ? v2[d][kv].y : v1[d][kv]);
+    }
+    __device__ __forceinline__ void add(int d, int kv, int kw, float dm, float dv) {
+        if (kw == 0) {
+            m2[d][kv].x += dm;
+            v2[d][kv].x += dv;
+        } else if (kw == 1) {
+            m2[d][kv].y += dm;
+            v2[d][kv].y += dv;
+        } else {
+            m1[d][kv] += dm;
+            v1[d][kv] += dv;
+        }
+    }
+};
+
+__device__ __forceinline__ float2 bcast(float x) { return make_float2(x, x); }
+
 // One particle's contribution to the lane's padded footprint on grid A.
 // fu: stencil along A (face offset), fv / fw: the other two axes (centre).
 // Fit factors of the G2P least-squares fit in physical units (the adjoint
@@ -195,7 +234,7 @@ __device__ __forceinline__ void accumulate_mapped(const P2GArgs &P, const float 
                                                   float mt, int shift, float tu, float tv,
                                                   float tw, const Stencil1D &fu,
                                                   const Stencil1D &fv, const Stencil1D &fw,
-                                                  float (&am)[4][3][3], float (&av)[4][3][3]) {
+                                                  Foot &F) {
     using S = Stage<R, true>;
     constexpr int D = axis_degrees(R);
     float M[3][3];
@@ -254,22 +293,19 @@ __device__ __forceinline__ void accumulate_mapped(const P2GArgs &P, const float 
                 // rows are static indices (the footprint stays in registers)
                 const float w = mt * fu.W[ku] * fv.W[kv] * fw.W[kw];
                 const float wS = w * Sn;
-                am[ku][kv][kw] += shift ? 0.0f : w;
-                am[ku + 1][kv][kw] += shift ? w : 0.0f;
-                av[ku][kv][kw] += shift ? 0.0f : wS;
-                av[ku + 1][kv][kw] += shift ? wS : 0.0f;
+                F.add(ku, kv, kw, shift ? 0.0f : w, shift ? 0.0f : wS);
+                F.add(ku + 1, kv, kw, shift ? w : 0.0f, shift ? wS : 0.0f);
             }
 }
 
 template <int R, int FMT, int A, bool ADJ, bool AFF = false>
 __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, int lane, float mt,
                                            int shift, const Stencil1D &fu, const Stencil1D &fv,
-                                           const Stencil1D &fw, bool gu, bool gv, bool gw,
-                                           float (&am)[4][3][3], float (&av)[4][3][3],
+                                           const Stencil1D &fw, bool gu, bool gv, bool gw, Foot &F,
                                            float tu = 0.0f, float tv = 0.0f, float tw = 0.0f) {
     using S = Stage<R, AFF, FMT>;
     if constexpr (AFF && R > 4) {
-        accumulate_mapped<R, A>(P, st, lane, mt, shift, tu, tv, tw, fu, fv, fw, am, av);
+        accumulate_mapped<R, A>(P, st, lane, mt, shift, tu, tv, tw, fu, fv, fw, F);
         return;
     }
     float cl[3] = {0.0f, 0.0f, 0.0f};
@@ -308,18 +344,24 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
             w2 = mt * W0[2];
         }
         const float Wm[4] = {shift ? 0.0f : w0, shift ? w0 : w1, shift ? w1 : w2, shift ? w2 : 0.0f};
+        const float2 fw0 = make_float2(Fw[0][0], Fw[0][1]);
 #pragma unroll
-        for (int kv = 0; kv < 3; ++kv)
+        for (int kv = 0; kv < 3; ++kv) {
+            const float2 wvw = __fmul2_rn(bcast(Fv[0][kv]), fw0);
+            const float wvw2 = Fv[0][kv] * Fw[0][2];
 #pragma unroll
-            for (int kw = 0; kw < 3; ++kw) {
-                const float wvw = Fv[0][kv] * Fw[0][kw];
-#pragma unroll
-                for (int d = 0; d < 4; ++d) am[d][kv][kw] = fmaf(Wm[d], wvw, am[d][kv][kw]);
+            for (int d = 0; d < 4; ++d) {
+                F.m2[d][kv] = __ffma2_rn(bcast(Wm[d]), wvw, F.m2[d][kv]);
+                F.m1[d][kv] = fmaf(Wm[d], wvw2, F.m1[d][kv]);
             }
+        }
     }
     (void)W0;
     // momentum, streamed over the degree du along u: contract w, then v, then
-    // u into the padded footprint
+    // u into the padded footprint (kw = 0, 1 as packed pairs, kw = 2 scalar)
+    float2 fw2[D];
+#pragma unroll
+    for (int dw = 0; dw < D; ++dw) fw2[dw] = make_float2(Fw[dw][0], Fw[dw][1]);
 #pragma unroll
     for (int du = 0; du < D; ++du) {
         float C[D][D];
@@ -344,30 +386,38 @@ __device__ __forceinline__ void accumulate(const P2GArgs &P, const float *st, in
                     }
                 }
             }
-        float T1[D][3];
+        float2 T1p[D];
+        float T1s[D];
 #pragma unroll
-        for (int dv = 0; dv < D; ++dv)
+        for (int dv = 0; dv < D; ++dv) {
+            float2 sp = make_float2(0.0f, 0.0f);
+            float ss = 0.0f;
 #pragma unroll
-            for (int kw = 0; kw < 3; ++kw) {
-                float s = 0.0f;
-#pragma unroll
-                for (int dw = 0; dw < D; ++dw)
-                    if (has_mode(R, deg_x<A>(du, dv, dw), deg_y<A>(du, dv, dw), deg_z<A>(du, dv, dw)))
-                        s = fmaf(C[dv][dw], Fw[dw][kw], s);
-                T1[dv][kw] = s;
-            }
+            for (int dw = 0; dw < D; ++dw)
+                if (has_mode(R, deg_x<A>(du, dv, dw), deg_y<A>(du, dv, dw), deg_z<A>(du, dv, dw))) {
+                    sp = __ffma2_rn(bcast(C[dv][dw]), fw2[dw], sp);
+                    ss = fmaf(C[dv][dw], Fw[dw][2], ss);
+                }
+            T1p[dv] = sp;
+            T1s[dv] = ss;
+        }
         const float f0 = Fu[du][0], f1 = Fu[du][1], f2 = Fu[du][2];
         const float Gu[4] = {shift ? 0.0f : f0, shift ? f0 : f1, shift ? f1 : f2, shift ? f2 : 0.0f};
 #pragma unroll
-        for (int kv = 0; kv < 3; ++kv)
+        for (int kv = 0; kv < 3; ++kv) {
+            float2 tp = make_float2(0.0f, 0.0f);
+            float ts = 0.0f;
 #pragma unroll
-            for (int kw = 0; kw < 3; ++kw) {
-                float t2 = 0.0f;
-#pragma unroll
-                for (int dv = 0; dv < D; ++dv) t2 = fmaf(T1[dv][kw], Fv[dv][kv], t2);
-#pragma unroll
-                for (int d = 0; d < 4; ++d) av[d][kv][kw] = fmaf(t2, Gu[d], av[d][kv][kw]);
+            for (int dv = 0; dv < D; ++dv) {
+                tp = __ffma2_rn(T1p[dv], bcast(Fv[dv][kv]), tp);
+                ts = fmaf(T1s[dv], Fv[dv][kv], ts);
             }
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                F.v2[d][kv] = __ffma2_rn(tp, bcast(Gu[d]), F.v2[d][kv]);
+                F.v1[d][kv] = fmaf(ts, Gu[d], F.v1[d][kv]);
+            }
+        }
     }
 }
 

@@ -69,13 +69,8 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
     using S = Stage<R, AFF, FMT>;
     const bool interior = gi >= 1 && gi <= P.g.n[0] - 2 && gj >= 1 && gj <= P.g.n[1] - 2 &&
                           gk >= 1 && gk <= P.g.n[2] - 2;
-    float am[4][3][3], av[4][3][3];
-#pragma unroll
-    for (int d = 0; d < 4; ++d)
-#pragma unroll
-        for (int kv = 0; kv < 3; ++kv)
-#pragma unroll
-            for (int kw = 0; kw < 3; ++kw) am[d][kv][kw] = av[d][kv][kw] = 0.0f;
+    Foot F;
+    F.zero();
     const unsigned lt = (1u << lane) - 1u;
     for (uint32_t r = 0; r < maxn; ++r) {
         float *st = stage + q.ring * S::NV * 32;
@@ -101,7 +96,7 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
                 const int shift = au.base - (cu - 1);
                 accumulate<R, FMT, A, ADJ, AFF>(P, st, lane, mt, shift, stencil_1d_scaled(au.t, P.s1, P.s2),
                                            stencil_1d_scaled(av_.t, P.s1, P.s2), stencil_1d_scaled(aw.t, P.s1, P.s2), au.guard,
-                                           av_.guard, aw.guard, am, av, au.t, av_.t, aw.t);
+                                           av_.guard, aw.guard, F, au.t, av_.t, aw.t);
             } else {
                 bad = true;
             }
@@ -127,8 +122,8 @@ __device__ __forceinline__ void p2g_pass(const P2GArgs &P, Pipe &q, uint32_t bs,
                 const int iy = A == 0 ? nv : (A == 1 ? nu : nw);
                 const int iz = A == 2 ? nu : nw;
                 const int idx = region_index<A>(ix, iy, iz);
-                rm[idx] += am[d][kv][kw];
-                rv[idx] += av[d][kv][kw];
+                rm[idx] += F.m(d, kv, kw);
+                rv[idx] += F.v(d, kv, kw);
                 __syncwarp();
             }
 }
