@@ -90,16 +90,19 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_tiles(G2PArgs A) {
             constexpr int a = decltype(acomp)::value;
             if (ok) {
                 if constexpr (a == 0)
-                    g2p_component<R, 0, Tile<0>::X, Tile<0>::Y, GRADW>(
+                    g2p_component<R, 0, Tile<0>::X, Tile<0>::Y, GRADW,
+                                  FMT != POLYPIC_COEFF_F32>(
                         s_tile, af0.base - ox, ac1.base - oy, ac2.base - oz, sf0, af0.guard, sc1,
                         ac1.guard, sc2, ac2.guard, inv1, inv2, C, af0.t, ac1.t, ac2.t);
                 else if constexpr (a == 1)
-                    g2p_component<R, 1, Tile<1>::X, Tile<1>::Y, GRADW>(
+                    g2p_component<R, 1, Tile<1>::X, Tile<1>::Y, GRADW,
+                                  FMT != POLYPIC_COEFF_F32>(
                         s_tile + kVelTileOff1, ac0.base - ox, af1.base - oy, ac2.base - oz, sc0,
                         ac0.guard, sf1, af1.guard, sc2, ac2.guard, inv1, inv2, C, ac0.t, af1.t,
                         ac2.t);
                 else
-                    g2p_component<R, 2, Tile<2>::X, Tile<2>::Y, GRADW>(
+                    g2p_component<R, 2, Tile<2>::X, Tile<2>::Y, GRADW,
+                                  FMT != POLYPIC_COEFF_F32>(
                         s_tile + kVelTileOff2, ac0.base - ox, ac1.base - oy, af2.base - oz, sc0,
                         ac0.guard, sc1, ac1.guard, sf2, af2.guard, inv1, inv2, C, ac0.t, ac1.t,
                         af2.t);

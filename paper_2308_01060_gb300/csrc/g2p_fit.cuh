@@ -50,6 +50,8 @@ __device__ __forceinline__ void stage_velocity(const GridGeom &g, const float *c
     stage(2, S::template D<2>::X, S::template D<2>::Y, S::template D<2>::Z, S::kOff2);
 }
 
+__device__ __forceinline__ float2 gbc(float x) { return make_float2(x, x); }
+
 // inv1 = 1/dx, inv2 = 1/dx^2 give physical coefficients; 1 and 1 give c dx^L.
 template <int D>
 __device__ __forceinline__ void fit_factors(const Stencil1D &s, bool guard, float inv1,
@@ -85,7 +87,10 @@ __device__ __forceinline__ void grad_w_factors(float t, float inv1, float (&G)[D
 // t: the staged values of face grid A, rows of TX nodes, planes of TY rows;
 // (lx, ly, lz): the stencil's lowest node in it.  GRADW (4 modes): the
 // linear modes take Eq 10's weight gradients; (tx, ty, tz) are the axes' t.
-template <int R, int A, int TX, int TY, bool GRADW = false>
+// PACK: the x and y contractions run two rows at a time through packed FP32
+// FMAs, with the same bits as the scalar form (faster where the fit, not the
+// coefficient stores, bounds the kernel: the 16-bit formats).
+template <int R, int A, int TX, int TY, bool GRADW = false, bool PACK = false>
 __device__ __forceinline__ void g2p_component(const float *t, int lx, int ly, int lz,
                                               const Stencil1D &sx, bool gx, const Stencil1D &sy,
                                               bool gy, const Stencil1D &sz, bool gz, float inv1,
@@ -101,28 +106,63 @@ __device__ __forceinline__ void g2p_component(const float *t, int lx, int ly, in
         grad_w_factors<D>(ty, inv1, Gy);
         grad_w_factors<D>(tz, inv1, Gz);
     }
-    // contract x
-    float U1[D][3][3];
+    float U2[D][D][3];
+    if constexpr (!PACK) {
+        // contract x
+        float U1[D][3][3];
 #pragma unroll
-    for (int kz = 0; kz < 3; ++kz)
+        for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+                const float *row = t + ((lz + kz) * TY + (ly + ky)) * TX + lx;
+                const float v0 = row[0], v1 = row[1], v2 = row[2];
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    U1[a][ky][kz] = fmaf(Gx[a][0], v0, fmaf(Gx[a][1], v1, Gx[a][2] * v2));
+            }
+        // contract y
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+#pragma unroll
+                for (int kz = 0; kz < 3; ++kz)
+                    U2[a][b][kz] = fmaf(Gy[b][0], U1[a][0][kz],
+                                        fmaf(Gy[b][1], U1[a][1][kz], Gy[b][2] * U1[a][2][kz]));
+    } else {
+        // contract x, then y; the rows kz = 0, 1 travel as float2 pairs through
+        // packed FP32 FMAs (each lane rounds as fmaf does, in the same order, so
+        // the values carry the same bits as scalar FMAs), the row kz = 2 scalar
+        float2 U1p[D][3];
+        float U1s[D][3];
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky) {
-            const float *row = t + ((lz + kz) * TY + (ly + ky)) * TX + lx;
-            const float v0 = row[0], v1 = row[1], v2 = row[2];
+            const float *r0 = t + ((lz + 0) * TY + (ly + ky)) * TX + lx;
+            const float *r1 = t + ((lz + 1) * TY + (ly + ky)) * TX + lx;
+            const float *r2 = t + ((lz + 2) * TY + (ly + ky)) * TX + lx;
+            const float2 v0 = make_float2(r0[0], r1[0]), v1 = make_float2(r0[1], r1[1]),
+                         v2 = make_float2(r0[2], r1[2]);
+            const float w0 = r2[0], w1 = r2[1], w2 = r2[2];
 #pragma unroll
-            for (int a = 0; a < D; ++a)
-                U1[a][ky][kz] = fmaf(Gx[a][0], v0, fmaf(Gx[a][1], v1, Gx[a][2] * v2));
+            for (int a = 0; a < D; ++a) {
+                U1p[a][ky] = __ffma2_rn(gbc(Gx[a][0]), v0,
+                                        __ffma2_rn(gbc(Gx[a][1]), v1, __fmul2_rn(gbc(Gx[a][2]), v2)));
+                U1s[a][ky] = fmaf(Gx[a][0], w0, fmaf(Gx[a][1], w1, Gx[a][2] * w2));
+            }
         }
-    // contract y
-    float U2[D][D][3];
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+        for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int b = 0; b < D; ++b)
-#pragma unroll
-            for (int kz = 0; kz < 3; ++kz)
-                U2[a][b][kz] = fmaf(Gy[b][0], U1[a][0][kz],
-                                    fmaf(Gy[b][1], U1[a][1][kz], Gy[b][2] * U1[a][2][kz]));
+            for (int b = 0; b < D; ++b) {
+                const float2 p = __ffma2_rn(
+                    gbc(Gy[b][0]), U1p[a][0],
+                    __ffma2_rn(gbc(Gy[b][1]), U1p[a][1], __fmul2_rn(gbc(Gy[b][2]), U1p[a][2])));
+                U2[a][b][0] = p.x;
+                U2[a][b][1] = p.y;
+                U2[a][b][2] = fmaf(Gy[b][0], U1s[a][0],
+                                   fmaf(Gy[b][1], U1s[a][1], Gy[b][2] * U1s[a][2]));
+            }
+    }
     // contract z
 #pragma unroll
     for (int a = 0; a < D; ++a)
