@@ -46,13 +46,18 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="grid cells per axis (default 128)")
+    ap.add_argument("--preroll", type=int, default=200,
+                    help="dam-break steps with pressure projection run (untimed) before the "
+                         "timed steps, so that they start from the sustained state")
     ap.add_argument("--variants", default="graph,apic4,apic4_gradw,apic4_affine,affine27,bf16,f16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--e2e-lanes", type=int, default=3,
                     help="streams (each with its own device buffers) the e2e steps rotate over")
-    ap.add_argument("--rows", default="coupled,update,projection,adjoint",
+    ap.add_argument("--large-steps", type=int, default=100,
+                    help="steps of the 256^3 fluid + fabric row per coefficient format")
+    ap.add_argument("--rows", default="coupled,update,projection,adjoint,large",
                     help="the other rows of the path, each timed on its own workload")
     return ap.parse_args()
 
@@ -149,7 +154,7 @@ class ClockSampler:
 # read, 13.8 MB written); P2G traffic grows in proportion to the particles, so
 # it scales to the 128^3 launch.  It must go back to None whenever the kernel
 # changes after that capture.
-P2G_TILES_DRAM_BYTES_PER_PARTICLE = (537.172736e6 + 13.766912e6) / 1557376
+P2G_TILES_DRAM_BYTES_PER_PARTICLE = None
 
 
 def algorithmic_bytes(R: int, fmt: str):
@@ -179,15 +184,75 @@ def make_state(pp, ctx, scene, device):
     return a, b
 
 
+def preroll(pp, torch, scene, steps, device):
+    """The dam break run `steps` steps from rest WITH the pressure projection
+    (multigrid-preconditioned CG, FP64 reductions), FP32 coefficients, 27
+    modes: the sustained state every timed figure starts from (the particles
+    have fallen and spread, and cells hold uneven counts)."""
+    ctx = pp.Context(scene.n, scene.dx, 27)
+    a, b = make_state(pp, ctx, scene, device)
+    g = ctx.new_grid(device=device)
+    ws = ctx.workspace(a.count, device=device)
+    prj = pp.UpdateSettings(dt=scene.dt, project=True, pcg_maxiter=2000)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pp.polypic_step(ctx, a, b, g, prj, ws, stream=stream)
+        a, b = b, a
+    torch.cuda.synchronize()
+    st = pp.polypic_check_device_status(ctx)
+    if st != 0:
+        raise RuntimeError(f"device status {pp.STATUS_NAMES.get(st)} during the pre-roll")
+    out = {"x": a.x.clone(), "mass": a.mass.clone(), "coeff": a.coeff.clone(),
+           "vel": [v.clone() for v in g.vel], "steps": steps,
+           "seconds": round(time.perf_counter() - t0, 2),
+           "stability": state_stats(pp, torch, a, scene.dt, scene.dx, steps)}
+    del ctx, a, b, g, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def state_from(pp, ctx, pre, device):
+    """(src, dst) particle states of context ctx at the pre-rolled positions:
+    the pre-rolled FP32 27-mode coefficients as they are, or, for another mode
+    count, format or variant, the coefficients G2P fits (dt = 0, positions
+    unchanged) from the pre-rolled grid velocity."""
+    src = pp.upload_particles(ctx, pre["x"], pre["mass"], None, device=device)
+    dst = ctx.new_particles(src.count, device=device)
+    if ctx.num_modes == 27 and ctx.coeff_format == "f32" and not ctx.variant:
+        src.coeff.copy_(pre["coeff"])
+        return src, dst
+    ws = ctx.workspace(src.count, device=device)
+    g = ctx.new_grid(device=device)
+    for a in range(3):
+        g.vel[a].copy_(pre["vel"][a])
+    pp.polypic_sort(ctx, src, ws)
+    pp.polypic_g2p(ctx, g, src, dst, 0.0, ws)
+    del ws, g
+    return dst, src
+
+
+def round_efficiency(cell_start) -> float:
+    """Particles over 32 x the fullest cell, summed over the 32-key blocks:
+    the share of lane rounds a one-lane-per-cell P2G would keep busy (a
+    property of the state; the library's schedule balances it)."""
+    cs = cell_start.cpu().numpy().view(np.uint32).astype(np.int64)
+    cnt = np.diff(cs).reshape(-1, 32)
+    mx = cnt.max(axis=1)
+    live = mx > 0
+    return round(float(cnt.sum() / max(1, (32 * mx[live]).sum())), 4)
+
+
 def state_stats(pp, torch, ps, dt, dx, steps_run):
     """Stability of a state (reported, not gated: the paper found 27 fluid
     modes unstable in coupled runs): the particle velocity c_p0 (decoded for
     16-bit codes), its largest magnitude, the CFL number max |v| dt / dx, the
     kinetic energy per particle and whether every coefficient is finite."""
     c = ps.coeff.float()
-    v = c[:, 0, :]
     if ps.scale is not None and ps.coeff.dtype != torch.float32:
-        v = v * ps.scale[None, :]
+        v = c[:, 0, :, 0] * ps.scale[None, :]      # mode 0: the low half of word 0
+    else:
+        v = c[:, 0, :]
     speed = torch.sqrt((v.double() ** 2).sum(dim=0))
     vmax = float(speed.max().item()) if speed.numel() else 0.0
     ke = float((0.5 * ps.mass.double() * speed ** 2).mean().item()) if speed.numel() else 0.0
@@ -196,13 +261,13 @@ def state_stats(pp, torch, ps, dt, dx, steps_run):
             "finite": bool(torch.isfinite(c).all().item())}
 
 
-def run_variant(pp, torch, scene, R, fmt, steps, warmup, device, **ctx_opts):
-    """Times `steps` calls of polypic_step (the whole path, as a user runs it),
-    then `steps` steps made of the individual calls (sort, P2G, grid update,
-    G2P) with events between them for the per-phase split.  ctx_opts: the
-    context's map_affine / apic_grad_w variants."""
+def run_variant(pp, torch, scene, pre, R, fmt, steps, warmup, device, **ctx_opts):
+    """Times `steps` calls of polypic_step (the whole path, as a user runs it)
+    from the pre-rolled state, then `steps` steps made of the individual calls
+    (sort, P2G, grid update, G2P) with events between them for the per-phase
+    split.  ctx_opts: the context's map_affine / apic_grad_w variants."""
     ctx = pp.Context(scene.n, scene.dx, R, coeff_format=fmt, **ctx_opts)
-    src, dst = make_state(pp, ctx, scene, device)
+    src, dst = state_from(pp, ctx, pre, device)
     g = ctx.new_grid(device=device)
     ws = ctx.workspace(src.count, device=device)
     prm = pp.UpdateSettings(dt=scene.dt)
@@ -251,7 +316,9 @@ def run_variant(pp, torch, scene, R, fmt, steps, warmup, device, **ctx_opts):
     st = pp.polypic_check_device_status(ctx)
     return {"ctx": ctx, "count": src.count, "total_ms": total_ms,
             "phase_ms": (ph / steps).tolist(), "status": pp.STATUS_NAMES.get(st),
-            "stability": state_stats(pp, torch, src, scene.dt, scene.dx, warmup + 2 * steps)}
+            "round_efficiency": round_efficiency(src.cell_start),
+            "stability": state_stats(pp, torch, src, scene.dt, scene.dx,
+                                     pre["steps"] + warmup + 2 * steps)}
 
 
 class L2Flush:
@@ -285,7 +352,7 @@ def face_nodes(n):
     return sum((n[0] + (a == 0)) * (n[1] + (a == 1)) * (n[2] + (a == 2)) for a in range(3))
 
 
-def run_rows(pp, torch, scenes, device, hbm, which, iters=10, warmup=3):
+def run_rows(pp, torch, scenes, device, hbm, which, iters=10, warmup=3, large_steps=100):
     """The rows of the path outside the headline step, each on the workload
     it is defined on: the coupled fluid + fabric step (splash scene, 128^3),
     the grid update and the pressure projection (dam break, 128^3), and the
@@ -426,18 +493,137 @@ def run_rows(pp, torch, scenes, device, hbm, which, iters=10, warmup=3):
         out["status"] = pp.STATUS_NAMES.get(pp.polypic_check_device_status(ctx))
         rows["A8_adjoints"] = out
         del ctx, ps, ws, g, bar_out, bar_grid, bar_mid, bar_in
+    if "large" in which:
+        rows["cfg_large_fluid_fabric_256"] = run_large(pp, torch, scenes, device,
+                                                       steps=large_steps, timed=10)
     del flush
     torch.cuda.empty_cache()
     return rows
 
 
-def run_graph(pp, torch, scene, R, steps, warmup, device):
+def field_on_grid(torch, scene, ctx, device):
+    """The large scene's vortical field sampled at the face positions of the
+    three face grids (device tensors in the library's grid layout)."""
+    out = []
+    dx = scene.dx
+    for a in range(3):
+        d = ctx.grid_dims(a)
+        off = [0.0 if b == a else 0.5 for b in range(3)]
+        ax = [(torch.arange(d[b], device=device, dtype=torch.float64) + off[b]) * dx
+              for b in range(3)]
+        zz, yy, xx = torch.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        v = torch.zeros_like(xx)
+        for k, amp, ph in scene.meta["field"]:
+            v += float(amp[a]) * torch.sin(2 * np.pi * (float(k[0]) * xx + float(k[1]) * yy
+                                                          + float(k[2]) * zz) + ph)
+        out.append(v.float().contiguous())
+        del xx, yy, zz, v
+    return out
+
+
+def run_large(pp, torch, scenes, device, steps, timed):
+    """Large fluid + fabric at 256^3: ~64M fluid particles (the lower half-box
+    at 8 per cell, a vortical initial field) and a 1024^2-vertex sheet (3.1M
+    vertex and element particles), 27 modes, dt 2.5e-4, FP32 coefficients
+    against BF16 and FP16 per-particle-scaled codes.  Each format fits its
+    initial modes from the same grid field, then runs `steps` steps of both
+    phases with the pressure projection (FP64 reductions) and drag; the last
+    `timed` steps are made of the individual calls with CUDA events, and the
+    transfer time per step (the sorts, P2Gs and G2Ps of both phases; the grid
+    update and projection are reported apart) gives the throughput.  The 16-bit
+    forms' grid momentum is compared, on the first P2G, with the FP32 form's
+    (itself within 1e-5 of the FP64 oracle at smaller sizes)."""
+    sc = scenes.large_scene()
+    f, sol = sc.fluid, sc.solid
+    timed = max(1, min(timed, steps))
+    stream = torch.cuda.current_stream()
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"256^3 half box, {f.n} fluid particles (8/cell, vortical field of 4 "
+                       f"solenoidal modes, 0.5 m/s) + {sol.n} sheet particles "
+                       f"(1024^2 vertices at y = 0.75), 27 modes, dt 2.5e-4, drag K 5, "
+                       f"projection every step", "steps": steps, "timed_steps": timed}
+    ref_mom = None
+    for fmt in ("f32", "bf16", "f16"):
+        ctx = pp.Context(sc.n, sc.dx, 27, coeff_format=fmt)
+        vel = field_on_grid(torch, sc, ctx, device)
+        g0 = ctx.new_grid(device=device)
+        for a in range(3):
+            g0.vel[a].copy_(vel[a])
+        del vel
+        ws = ctx.workspace(f.n, sol.n, device=device)
+        fa = pp.upload_particles(ctx, f.x, f.mass, None, device=device)
+        fb = ctx.new_particles(f.n, device=device)
+        sa = pp.upload_particles(ctx, sol.x, sol.mass, None, mass_abs=sol.mass_abs, device=device)
+        sb = ctx.new_particles(sol.n, solid=True, device=device)
+        pp.polypic_sort(ctx, fa, ws)
+        pp.polypic_g2p(ctx, g0, fa, fb, 0.0, ws)
+        pp.polypic_sort(ctx, sa, ws)
+        pp.polypic_g2p(ctx, g0, sa, sb, 0.0, ws)
+        fa, fb, sa, sb = fb, fa, sb, sa
+        gf, gs = g0, ctx.new_grid(device=device)
+        # first P2G: the grid-momentum error of the 16-bit forms against FP32
+        pp.polypic_sort(ctx, fa, ws)
+        pp.polypic_p2g(ctx, fa, gf, ws)
+        torch.cuda.synchronize()
+        if fmt == "f32":
+            ref_mom = [m.clone() for m in gf.mom]
+            err = None
+        else:
+            num = sum(float(((gf.mom[a].double() - ref_mom[a].double()) ** 2).sum()) for a in range(3))
+            den = sum(float((ref_mom[a].double() ** 2).sum()) for a in range(3))
+            mx = max(float((gf.mom[a] - ref_mom[a]).abs().max()) for a in range(3))
+            mref = max(float(ref_mom[a].abs().max()) for a in range(3))
+            err = {"norm_rel": num ** 0.5 / den ** 0.5, "max_rel": mx / mref}
+        prm = pp.UpdateSettings(dt=sc.dt, project=True, drag_k=5.0, pcg_maxiter=2000)
+        t_tr, t_upd = 0.0, 0.0
+        for k in range(steps):
+            ev = [E() for _ in range(8)]
+            ev[0].record(stream)
+            pp.polypic_sort(ctx, fa, ws, stream)
+            pp.polypic_p2g(ctx, fa, gf, ws, stream)
+            ev[1].record(stream)
+            pp.polypic_sort(ctx, sa, ws, stream)
+            pp.polypic_p2g(ctx, sa, gs, ws, stream)
+            ev[2].record(stream)
+            pp.polypic_grid_update(ctx, gf, prm, solid=gs, fluid_particles=fa, ws=ws,
+                                   stream=stream)
+            ev[3].record(stream)
+            pp.polypic_g2p(ctx, gf, fa, fb, sc.dt, ws, stream)
+            ev[4].record(stream)
+            pp.polypic_g2p(ctx, gs, sa, sb, sc.dt, ws, stream)
+            ev[5].record(stream)
+            fa, fb, sa, sb = fb, fa, sb, sa
+            if k >= steps - timed:
+                torch.cuda.synchronize()
+                t_tr += (ev[0].elapsed_time(ev[1]) + ev[1].elapsed_time(ev[2])
+                         + ev[3].elapsed_time(ev[4]) + ev[4].elapsed_time(ev[5]))
+                t_upd += ev[2].elapsed_time(ev[3])
+        torch.cuda.synchronize()
+        st = pp.polypic_check_device_status(ctx)
+        ms = t_tr / timed
+        out[fmt] = {"ms_transfers_per_step": round(ms, 3),
+                    "ms_update_and_projection_per_step": round(t_upd / timed, 3),
+                    "value": round((f.n + sol.n) / (ms * 1e-3) / 1e6, 1), "unit": UNIT,
+                    "grid_momentum_error_vs_f32": err,
+                    "stability": state_stats(pp, torch, fa, sc.dt, sc.dx, steps),
+                    "status": pp.STATUS_NAMES.get(st)}
+        del ctx, fa, fb, sa, sb, gf, gs, g0, ws
+        torch.cuda.empty_cache()
+    for fmt in ("bf16", "f16"):
+        out[fmt]["speedup_vs_f32"] = round(out["f32"]["ms_transfers_per_step"]
+                                           / out[fmt]["ms_transfers_per_step"], 3)
+    del ref_mom
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_graph(pp, torch, scene, pre, R, steps, warmup, device):
     """polypic_step replayed from CUDA graphs: the two ping-pong steps (a -> b,
     b -> a) are each captured once (the step makes no host synchronisation
     without the projection) and replayed `steps` times, which removes the
     launch gaps between its kernels."""
     ctx = pp.Context(scene.n, scene.dx, R)
-    a, b = make_state(pp, ctx, scene, device)
+    a, b = state_from(pp, ctx, pre, device)
     g = ctx.new_grid(device=device)
     ws = ctx.workspace(a.count, device=device)
     prm = pp.UpdateSettings(dt=scene.dt)
@@ -467,7 +653,7 @@ def run_graph(pp, torch, scene, R, steps, warmup, device):
             "status": pp.STATUS_NAMES.get(st)}
 
 
-def run_e2e(pp, torch, scene, R, steps, device, lanes=2):
+def run_e2e(pp, torch, scene, pre, R, steps, device, lanes=2):
     """Through the C ABI with host buffers: every step copies the particle
     state in from pinned host memory, runs polypic_step, and copies the new
     state back out.  Steps alternate between `lanes` streams, each with its
@@ -476,16 +662,16 @@ def run_e2e(pp, torch, scene, R, steps, device, lanes=2):
     moves its full input and output across the host link inside the timed
     region."""
     ctx = pp.Context(scene.n, scene.dx, R)
-    f = scene.fluid
-    P = f.n
+    P = int(pre["x"].shape[1])
     prm = pp.UpdateSettings(dt=scene.dt)
-    h_x = torch.from_numpy(f.x).pin_memory()
-    h_m = torch.from_numpy(f.mass).pin_memory()
-    h_c = torch.zeros((3, R, P), dtype=torch.float32).pin_memory()
+    h_x = pre["x"].cpu().pin_memory()
+    h_m = pre["mass"].cpu().pin_memory()
+    h_c = pre["coeff"].cpu().pin_memory()
     L = []
     for _ in range(lanes):
-        dev_in, dev_out = make_state(pp, ctx, scene, device)
-        L.append({"s": torch.cuda.Stream(device=device), "in": dev_in, "out": dev_out,
+        L.append({"s": torch.cuda.Stream(device=device),
+                  "in": ctx.new_particles(P, device=device),
+                  "out": ctx.new_particles(P, device=device),
                   "g": ctx.new_grid(device=device), "ws": ctx.workspace(P, device=device),
                   "xo": torch.empty((3, P), dtype=torch.float32).pin_memory(),
                   "co": torch.empty((3, R, P), dtype=torch.float32).pin_memory()})
@@ -524,25 +710,40 @@ def run_e2e(pp, torch, scene, R, steps, device, lanes=2):
 
 
 def cpu_baseline(scene, R, target_s=12.0):
-    """FP64 CPU oracle (single thread, as it stands) on a bounded sample of the
-    same workload: the first S particles of the scene on the full grid, one
-    step each; S grows until the run takes a few seconds."""
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same
+    workload: the first S particles of the scene on the full grid, one step
+    each (P2G, grid update, G2P); S grows until a run takes a few seconds.
+    Timed on all host cores (OpenMP: G2P split by particle, P2G on private
+    grids summed in thread order) and on one thread."""
     import oracle
     f = scene.fluid
-    S = 2000
-    while True:
-        x = f.x[:, :S]
-        m = f.mass[:S]
-        c = np.zeros((3, R, S))
-        t0 = time.perf_counter()
-        oracle.step(x, m, c, scene.n, scene.dx, scene.dt)
-        el = time.perf_counter() - t0
-        if el > target_s / 3 or S >= f.n:
-            break
-        S = min(f.n, int(S * max(2.0, (target_s / 3) / max(el, 1e-3))))
-    return {"value": S / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{S} of {f.n} particles, one full step (P2G, grid update, G2P) on the "
-                      f"{scene.n[0]}^3 grid, FP64, single thread", "seconds": el}
+    cores = os.cpu_count() or 1
+
+    def timed(threads, S0):
+        oracle.set_threads(threads)
+        S = S0
+        try:
+            while True:
+                x = f.x[:, :S]
+                m = f.mass[:S]
+                c = np.zeros((3, R, S))
+                t0 = time.perf_counter()
+                oracle.step(x, m, c, scene.n, scene.dx, scene.dt)
+                el = time.perf_counter() - t0
+                if el > target_s / 4 or S >= f.n:
+                    return S, el
+                S = min(f.n, int(S * max(2.0, (target_s / 4) / max(el, 1e-3))))
+        finally:
+            oracle.set_threads(1)
+
+    S1, e1 = timed(1, 2000)
+    Sn, en = timed(cores, 4000 * cores)
+    return {"value": Sn / en / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{Sn} of {f.n} particles of the initial dam break, one full step "
+                      f"(P2G, grid update, G2P) on the {scene.n[0]}^3 grid, FP64, "
+                      f"{cores} OpenMP threads", "seconds": round(en, 3),
+            "single_thread": {"value": S1 / e1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": f"{S1} particles, one step", "seconds": round(e1, 3)}}
 
 
 # ---------------------------------------------------------------- arms
@@ -556,7 +757,9 @@ def reference_arm(args):
     oracle.build()
     scene = scenes.dam_break_scene(n=args.n, R=27)
     f = scene.fluid
-    S = 20000
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    S = 10000 * cores
     x = f.x[:, :S]
     m = f.mass[:S]
     c = np.zeros((3, 27, S))
@@ -574,8 +777,9 @@ def reference_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"dam_break_{args.n}^3, 27 modes, dt 5e-4",
                        "sample_particles_per_step": S},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{S} of {f.n} particles per step on the full grid"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{S} of {f.n} particles of the initial dam break per "
+                                       f"step on the full grid, {cores} OpenMP threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -604,13 +808,16 @@ def our_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # the sustained state: the dam break stepped with projection (untimed)
+    pre = preroll(pp, torch, scene, args.preroll, device)
+
     # headline: 27 modes, FP32 coefficients
     barrier()
     sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
     sampler.start()
     t_wall = time.perf_counter()
-    main = run_variant(pp, torch, scene, 27, "f32", args.steps, args.warmup, device)
+    main = run_variant(pp, torch, scene, pre, 27, "f32", args.steps, args.warmup, device)
     barrier()
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
@@ -629,7 +836,7 @@ def our_arm(args):
         "frac": round(dom_gbs / hbm, 4),
         "traffic": (round(P * P2G_TILES_DRAM_BYTES_PER_PARTICLE / 1e9, 4)
                     if dominant == "p2g" and P2G_TILES_DRAM_BYTES_PER_PARTICLE else None),
-        "traffic_unit": "GB per launch (k_p2g_tiles only, scaled from the 96^3 capture)",
+        "traffic_unit": "GB per launch (k_p2g_tiles only, scaled from a 96^3 capture)",
         "kernel": "polypic_p2g call (k_p2g_tiles + k_p2g_reduce)" if dominant == "p2g"
         else "polypic_g2p (k_g2p_tiles)",
         "algorithmic_bytes_per_particle": p2g_b if dominant == "p2g" else g2p_b,
@@ -648,13 +855,13 @@ def our_arm(args):
     }
     for v in [s for s in args.variants.split(",") if s]:
         if v == "graph":
-            r = run_graph(pp, torch, scene, 27, args.steps, args.warmup, device)
+            r = run_graph(pp, torch, scene, pre, 27, args.steps, args.warmup, device)
             variants[v] = {"modes": 27, "coeff_format": "f32",
                            "note": "the same polypic_step calls, replayed from two CUDA graphs",
                            **r, "speedup_vs_f32_step": round(ms_step / r["ms_per_step"], 3)}
             continue
         R, fmt, opts = variant_defs[v]
-        r = run_variant(pp, torch, scene, R, fmt, args.steps, args.warmup, device, **opts)
+        r = run_variant(pp, torch, scene, pre, R, fmt, args.steps, args.warmup, device, **opts)
         pb, gb = algorithmic_bytes(R, fmt)
         vph = r["phase_ms"]
         variants[v] = {
@@ -670,12 +877,12 @@ def our_arm(args):
         }
         del r
 
-    rows = run_rows(pp, torch, scenes, device, hbm, [r for r in args.rows.split(",") if r]) \
-        if args.rows else {}
+    rows = run_rows(pp, torch, scenes, device, hbm, [r for r in args.rows.split(",") if r],
+                    large_steps=args.large_steps) if args.rows else {}
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(pp, torch, scene, 27, args.e2e_steps, device, lanes=args.e2e_lanes)
+        e2e = run_e2e(pp, torch, scene, pre, 27, args.e2e_steps, device, lanes=args.e2e_lanes)
         e2e["ms_per_step"], e2e["value"] = job_throughput(torch, e2e["ms_per_step"], P, 1, world,
                                                           device)
 
@@ -691,7 +898,11 @@ def our_arm(args):
             "data": "synthetic",
             "config": {
                 "workload": f"dam_break_{args.n}^3: {args.n // 2}x{args.n}x{args.n // 2}-cell block, "
-                            f"8 particles/cell, 27 modes, FP32 coefficients, dt 5e-4",
+                            f"8 particles/cell, 27 modes, FP32 coefficients, dt 5e-4, timed "
+                            f"after {args.preroll} steps with pressure projection",
+                "preroll": {"steps": args.preroll, "seconds": pre["seconds"],
+                            "stability": pre["stability"]},
+                "round_efficiency": main["round_efficiency"],
                 "particles_per_gpu": P, "grid": list(scene.n), "modes": 27,
                 "step": "polypic_step: sort + P2G (grid update fused) + G2P/advect",
                 "l2": f"inputs larger than L2 ({P * (16 + 324) / 1e9:.2f} GB of particle state "

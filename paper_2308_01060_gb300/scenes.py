@@ -264,3 +264,43 @@ def face_positions(alpha: int, n, dx: float):
     off = [0.0 if b == alpha else 0.5 for b in range(3)]
     k, j, i = np.meshgrid(np.arange(d[2]), np.arange(d[1]), np.arange(d[0]), indexing="ij")
     return ((i + off[0]) * dx, (j + off[1]) * dx, (k + off[2]) * dx)
+
+
+def vortical_modes(seed: int = 0, count: int = 4, amp: float = 0.5):
+    """`count` solenoidal Fourier modes u(x) = a sin(2 pi k.x + phi) with integer
+    wave vectors k (components 1..3), a random unit direction orthogonal to k
+    scaled so that the sum has amplitude ~amp: each mode is divergence free
+    because a . k = 0.  Returns a list of (k, a, phi)."""
+    rng = np.random.default_rng(seed)
+    modes = []
+    for _ in range(count):
+        k = rng.integers(1, 4, size=3).astype(np.float64)
+        r = rng.standard_normal(3)
+        a = r - k * (r @ k) / (k @ k)
+        a *= amp / (np.linalg.norm(a) * np.sqrt(count))
+        modes.append((k, a, float(rng.uniform(0, 2 * np.pi))))
+    return modes
+
+
+def large_scene(n: int = 256, seed: int = 0, sheet_verts: int = 1024, dt: float = 2.5e-4,
+                steps: int = 100, amp: float = 0.5) -> Scene:
+    """Large fluid + fabric: the lower half-box (y < 1/2) at 8 particles per
+    cell inside the 2-cell margin (about 64M particles on 256^3), whose
+    initial velocity is the vortical field of `vortical_modes` (the caller
+    samples it on the grid and fits the particles' modes from it), plus a
+    horizontal sheet of sheet_verts^2 vertices, side 0.8, at height 0.75
+    (above the fluid; the height is a stated choice)."""
+    dx = 1.0 / n
+    rng = np.random.default_rng(seed)
+    cells = box_cells((n, n, n), (0, 0, 0), (n, n // 2, n))
+    x = seed_cells(cells, 8, dx, rng)
+    P = x.shape[1]
+    mass = np.full(P, RHO_WATER * dx ** 3 / 8, dtype=np.float32)
+    fluid = ParticleSet(x=x, mass=mass, coeff=None, num_modes=27)
+    sx, smass, nv = sheet_particles(sheet_verts, 0.8, 0.75)
+    solid = ParticleSet(x=sx, mass=smass, coeff=None, num_modes=27,
+                        mass_abs=np.zeros(sx.shape[1], dtype=np.float32))
+    return Scene(name=f"large_fluid_fabric_{n}^3", n=(n, n, n), dx=dx, dt=dt, steps=steps,
+                 fluid=fluid, solid=solid,
+                 meta={"seed": seed, "ppc": 8, "sheet_vertices": nv,
+                       "field": vortical_modes(seed, 4, amp)})
