@@ -53,6 +53,7 @@ _D = ctypes.POINTER(ctypes.c_double)
 _F = ctypes.POINTER(ctypes.c_float)
 _U32 = ctypes.POINTER(ctypes.c_uint32)
 _U8 = ctypes.POINTER(ctypes.c_uint8)
+_PA = ctypes.c_void_p   # a C array of three double pointers (see _ptr3)
 _I = ctypes.POINTER(ctypes.c_int)
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
@@ -80,7 +81,9 @@ def _load():
                           _int, _D, _D, _D, _D]),
         "or_p2g_adjoint": (_int, [_i64, _D, _D, _D, _D, _D, _D, _int, _int, _int, _int, _dbl]
                            + [_D] * 10),
-        "or_grid_update_adjoint": (None, [_int, _int, _int] + [_D] * 15),
+        "or_grid_update_adjoint": (_int, [_int, _int, _int, _dbl, _dbl, _dbl, _dbl, _dbl, _PA,
+                                          _PA, _PA, _PA, _U8, _dbl, _int, _PA, _PA, _PA, _PA,
+                                          _PA, _PA]),
         "or_g2p_adjoint": (_int, [_i64, _D, _D, _D, _D, _D, _D, _int, _int, _int, _int, _dbl,
                                   _dbl] + [_D] * 10),
         "or_pcg_project": (_int, [_int, _int, _int, _dbl, _dbl, _dbl, _U8, _D, _D, _D, _D,
@@ -293,17 +296,41 @@ def p2g_adjoint(x, mass, coeff, n, dx, lm, lp, mass_abs=None):
     return lc, lx
 
 
-def grid_update_adjoint(n, fm, fp, lv):
-    D = ctypes.c_double
+def _ptr3(arrs):
+    """Three FP64 arrays as a C array of three pointers (None stays NULL)."""
+    if arrs is None:
+        return None
+    return (ctypes.c_void_p * 3)(*[a.ctypes.data for a in arrs])
+
+
+def grid_update_adjoint(n, fm, fp, lv, dt=0.0, gravity=(0.0, -9.81, 0.0), sm=None, sp=None,
+                        lsv=None, drag_k=0.0, fluid=None, rtol=1e-12, maxiter=5000):
+    """Adjoint of grid_update (then pcg_project on the fluid velocity when the
+    fluid-cell mask `fluid` (n_z, n_y, n_x) is given).  lv (and lsv with a
+    solid grid sm, sp): dL/dv~.  Returns (lm, lp), or (lm, lp, lsm, lsp) with a
+    solid grid."""
     fm = [_f64(a) for a in fm]
     fp = [_f64(a) for a in fp]
     lv = [_f64(a) for a in lv]
     lm = [np.zeros_like(a) for a in fm]
     lp = [np.zeros_like(a) for a in fm]
-    _load().or_grid_update_adjoint(int(n[0]), int(n[1]), int(n[2]), *[_p(a, D) for a in fm],
-                                   *[_p(a, D) for a in fp], *[_p(a, D) for a in lv],
-                                   *[_p(a, D) for a in lm], *[_p(a, D) for a in lp])
-    return lm, lp
+    solid = sm is not None
+    if solid:
+        sm = [_f64(a) for a in sm]
+        sp = [_f64(a) for a in sp]
+        lsv = [_f64(a) for a in lsv] if lsv is not None else [np.zeros_like(a) for a in sm]
+        lsm = [np.zeros_like(a) for a in sm]
+        lsp = [np.zeros_like(a) for a in sm]
+    else:
+        lsv = lsm = lsp = None
+    fl = None if fluid is None else np.ascontiguousarray(fluid, dtype=np.uint8)
+    rc = _load().or_grid_update_adjoint(
+        int(n[0]), int(n[1]), int(n[2]), float(dt), float(gravity[0]), float(gravity[1]),
+        float(gravity[2]), float(drag_k), _ptr3(fm), _ptr3(fp), _ptr3(sm), _ptr3(sp),
+        _p(fl, ctypes.c_uint8), float(rtol), int(maxiter), _ptr3(lv), _ptr3(lsv), _ptr3(lm),
+        _ptr3(lp), _ptr3(lsm), _ptr3(lsp))
+    _check(rc, "grid_update_adjoint")
+    return (lm, lp, lsm, lsp) if solid else (lm, lp)
 
 
 def g2p_adjoint(x, gv, R, n, dx, dt, lc_out, lx_out):

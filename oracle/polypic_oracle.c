@@ -647,34 +647,6 @@ int or_p2g_adjoint(int64_t np, const double *x, const double *y, const double *z
     return OR_OK;
 }
 
-/* Grid-update adjoint (single phase, no drag): given lv_a = dL/dv~_ia,
- * writes lm_a = dL/dm_ia and lp_a = dL/d(mv)_ia.  Wall faces and faces with
- * m = 0 pass no gradient.                                                    */
-void or_grid_update_adjoint(int nx, int ny, int nz,
-                            const double *fm0, const double *fm1, const double *fm2,
-                            const double *fp0, const double *fp1, const double *fp2,
-                            const double *lv0, const double *lv1, const double *lv2,
-                            double *lm0, double *lm1, double *lm2,
-                            double *lp0, double *lp1, double *lp2)
-{
-    const double *fm[3] = {fm0, fm1, fm2}, *fp[3] = {fp0, fp1, fp2}, *lv[3] = {lv0, lv1, lv2};
-    double *lm[3] = {lm0, lm1, lm2}, *lp[3] = {lp0, lp1, lp2};
-    for (int a = 0; a < 3; ++a) {
-        int d[3]; face_dims(a, nx, ny, nz, d);
-        for (int k = 0; k < d[2]; ++k)
-            for (int j = 0; j < d[1]; ++j)
-                for (int i = 0; i < d[0]; ++i) {
-                    size_t idx = ((size_t)k * d[1] + j) * d[0] + i;
-                    int ia = (a == 0) ? i : (a == 1) ? j : k;
-                    int wall = (ia == 0 || ia == d[a] - 1);
-                    double m = fm[a][idx];
-                    if (wall || !(m > 0.0)) { lm[a][idx] = 0.0; lp[a][idx] = 0.0; continue; }
-                    lp[a][idx] = lv[a][idx] / m;
-                    lm[a][idx] = -lv[a][idx] * fp[a][idx] / (m * m);
-                }
-    }
-}
-
 /* G2P adjoint with the advection.  Given lc_out = dL/dc'_pra ([3][R][np]) and
  * lxo = dL/dx'_p, adds dL/dv~_ia to lv0..2 (the caller zeroes them) and adds
  * dL/dx_p to lx, ly, lz.  Clamped axes pass no gradient through the advection. */
@@ -824,57 +796,52 @@ int or_g2p_adjoint(int64_t np, const double *x, const double *y, const double *z
  * CG to ||r|| <= rtol ||b||; then v_a -= dt/(rho dx) (p_right - p_left) on
  * every non-wall face with a fluid cell on at least one side.  Returns the
  * iteration count, or OR_ERR_NOT_CONVERGED.                                */
-int or_pcg_project(int nx, int ny, int nz, double dx, double dt, double rho,
-                   const uint8_t *fluid, double *v0, double *v1, double *v2,
-                   double *pressure, double rtol, int maxiter)
-{
-    double *v[3] = {v0, v1, v2};
-    int n3[3] = {nx, ny, nz};
-    size_t nc = (size_t)nx * ny * nz;
-    double *b = calloc(nc, sizeof(double)), *r = calloc(nc, sizeof(double));
-    double *zv = calloc(nc, sizeof(double)), *pd = calloc(nc, sizeof(double));
-    double *Ap = calloc(nc, sizeof(double)), *diag = calloc(nc, sizeof(double));
 #define CIDX(i, j, k) (((size_t)(k) * ny + (j)) * nx + (i))
+
+/* diag[c] = number of non-wall neighbours of fluid cell c (0 elsewhere). */
+static void laplacian_diag(int nx, int ny, int nz, const uint8_t *fluid, double *diag)
+{
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 size_t c = CIDX(i, j, k);
-                pressure[c] = 0.0;
+                diag[c] = 0.0;
                 if (!fluid[c]) continue;
-                int ijk[3] = {i, j, k};
-                double div = 0.0;
-                int nn = 0;
-                for (int a = 0; a < 3; ++a) {
-                    int d[3]; face_dims(a, nx, ny, nz, d);
-                    int lo[3] = {i, j, k}, hi[3] = {i, j, k};
-                    hi[a] += 1;
-                    double vl = v[a][((size_t)lo[2] * d[1] + lo[1]) * d[0] + lo[0]];
-                    double vh = v[a][((size_t)hi[2] * d[1] + hi[1]) * d[0] + hi[0]];
-                    div += (vh - vl) / dx;
-                    if (ijk[a] > 0) nn++;
-                    if (ijk[a] < n3[a] - 1) nn++;
-                }
-                b[c] = -(rho * dx * dx / dt) * div;
-                diag[c] = (double)nn;
+                diag[c] = (double)((i > 0) + (i < nx - 1) + (j > 0) + (j < ny - 1) + (k > 0) +
+                                   (k < nz - 1));
             }
-    /* A p for fluid cells */
-#define APPLY(src, dst)                                                          \
-    for (int k = 0; k < nz; ++k)                                                 \
-        for (int j = 0; j < ny; ++j)                                             \
-            for (int i = 0; i < nx; ++i) {                                       \
-                size_t c = CIDX(i, j, k);                                        \
-                if (!fluid[c]) { dst[c] = 0.0; continue; }                       \
-                double s = diag[c] * src[c];                                     \
-                if (i > 0 && fluid[CIDX(i - 1, j, k)]) s -= src[CIDX(i - 1, j, k)]; \
-                if (i < nx - 1 && fluid[CIDX(i + 1, j, k)]) s -= src[CIDX(i + 1, j, k)]; \
-                if (j > 0 && fluid[CIDX(i, j - 1, k)]) s -= src[CIDX(i, j - 1, k)]; \
-                if (j < ny - 1 && fluid[CIDX(i, j + 1, k)]) s -= src[CIDX(i, j + 1, k)]; \
-                if (k > 0 && fluid[CIDX(i, j, k - 1)]) s -= src[CIDX(i, j, k - 1)]; \
-                if (k < nz - 1 && fluid[CIDX(i, j, k + 1)]) s -= src[CIDX(i, j, k + 1)]; \
-                dst[c] = s;                                                      \
+}
+
+/* dst = A src on fluid cells: diag p_c minus the fluid neighbours' p. */
+static void laplacian_apply(int nx, int ny, int nz, const uint8_t *fluid, const double *diag,
+                            const double *src, double *dst)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = CIDX(i, j, k);
+                if (!fluid[c]) { dst[c] = 0.0; continue; }
+                double s = diag[c] * src[c];
+                if (i > 0 && fluid[CIDX(i - 1, j, k)]) s -= src[CIDX(i - 1, j, k)];
+                if (i < nx - 1 && fluid[CIDX(i + 1, j, k)]) s -= src[CIDX(i + 1, j, k)];
+                if (j > 0 && fluid[CIDX(i, j - 1, k)]) s -= src[CIDX(i, j - 1, k)];
+                if (j < ny - 1 && fluid[CIDX(i, j + 1, k)]) s -= src[CIDX(i, j + 1, k)];
+                if (k > 0 && fluid[CIDX(i, j, k - 1)]) s -= src[CIDX(i, j, k - 1)];
+                if (k < nz - 1 && fluid[CIDX(i, j, k + 1)]) s -= src[CIDX(i, j, k + 1)];
+                dst[c] = s;
             }
+}
+
+/* Jacobi-preconditioned CG for A x = b on the fluid cells, x from 0, to
+ * ||r|| <= rtol ||b||.  Returns the iteration count (-1: not converged). */
+static int jacobi_pcg(int nx, int ny, int nz, const uint8_t *fluid, const double *diag,
+                      const double *b, double *x, double rtol, int maxiter)
+{
+    size_t nc = (size_t)nx * ny * nz;
+    double *r = calloc(nc, sizeof(double)), *zv = calloc(nc, sizeof(double));
+    double *pd = calloc(nc, sizeof(double)), *Ap = calloc(nc, sizeof(double));
     double bnorm = 0.0;
-    for (size_t c = 0; c < nc; ++c) { r[c] = b[c]; bnorm += b[c] * b[c]; }
+    for (size_t c = 0; c < nc; ++c) { x[c] = 0.0; r[c] = b[c]; bnorm += b[c] * b[c]; }
     bnorm = sqrt(bnorm);
     int it = 0, converged = bnorm == 0.0;
     double rz = 0.0;
@@ -884,13 +851,13 @@ int or_pcg_project(int nx, int ny, int nz, double dx, double dt, double rho,
         rz += r[c] * zv[c];
     }
     while (!converged && it < maxiter) {
-        APPLY(pd, Ap);
+        laplacian_apply(nx, ny, nz, fluid, diag, pd, Ap);
         double pAp = 0.0;
         for (size_t c = 0; c < nc; ++c) pAp += pd[c] * Ap[c];
         double alpha = rz / pAp;
         double rn = 0.0;
         for (size_t c = 0; c < nc; ++c) {
-            pressure[c] += alpha * pd[c];
+            x[c] += alpha * pd[c];
             r[c] -= alpha * Ap[c];
             rn += r[c] * r[c];
         }
@@ -905,6 +872,36 @@ int or_pcg_project(int nx, int ny, int nz, double dx, double dt, double rho,
         rz = rz_new;
         for (size_t c = 0; c < nc; ++c) pd[c] = zv[c] + beta * pd[c];
     }
+    free(r); free(zv); free(pd); free(Ap);
+    return converged ? it : -1;
+}
+
+int or_pcg_project(int nx, int ny, int nz, double dx, double dt, double rho,
+                   const uint8_t *fluid, double *v0, double *v1, double *v2,
+                   double *pressure, double rtol, int maxiter)
+{
+    double *v[3] = {v0, v1, v2};
+    int n3[3] = {nx, ny, nz};
+    size_t nc = (size_t)nx * ny * nz;
+    double *b = calloc(nc, sizeof(double)), *diag = calloc(nc, sizeof(double));
+    laplacian_diag(nx, ny, nz, fluid, diag);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = CIDX(i, j, k);
+                if (!fluid[c]) continue;
+                double div = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    int d[3]; face_dims(a, nx, ny, nz, d);
+                    int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                    hi[a] += 1;
+                    double vl = v[a][((size_t)lo[2] * d[1] + lo[1]) * d[0] + lo[0]];
+                    double vh = v[a][((size_t)hi[2] * d[1] + hi[1]) * d[0] + hi[0]];
+                    div += (vh - vl) / dx;
+                }
+                b[c] = -(rho * dx * dx / dt) * div;
+            }
+    int it = jacobi_pcg(nx, ny, nz, fluid, diag, b, pressure, rtol, maxiter);
     /* velocity update on interior faces touching a fluid cell */
     for (int a = 0; a < 3; ++a) {
         int d[3]; face_dims(a, nx, ny, nz, d);
@@ -921,8 +918,146 @@ int or_pcg_project(int nx, int ny, int nz, double dx, double dt, double rho,
                         dt / (rho * dx) * (pressure[ch] - pressure[cl]);
                 }
     }
-#undef APPLY
-#undef CIDX
-    free(b); free(r); free(zv); free(pd); free(Ap); free(diag);
-    return converged ? it : OR_ERR_NOT_CONVERGED;
+    free(b); free(diag);
+    return it >= 0 ? it : OR_ERR_NOT_CONVERGED;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the whole grid update (or_grid_update, then or_pcg_project on
+ * the fluid velocity when `fluid` is given), each step's transpose written
+ * out, last step first.  Given lfv = dL/dv~_f (and lsv = dL/dv~_s with a
+ * solid grid), writes lfm = dL/dm_f, lfp = dL/d(mv)_f (and lsm, lsp).
+ *   projection  v' = v + dx G A^-1 D v, with (G p)_f = p_ch - p_cl on the
+ *               interior faces touching fluid and (D v)_c = div_c above, so
+ *               v^ = v^' + dx D^T A^-1 G^T v^': s = G^T v^' on the fluid
+ *               cells, A q = s (Jacobi-PCG, rtol), v^_f += q_cl - q_ch (dx
+ *               times D^T q, whose entries are +-1/dx; q = 0 off the fluid
+ *               cells; every face, walls included);
+ *   walls       v^ = 0 on the wall faces;
+ *   drag        per face holding both masses (drag_k > 0): the transposed
+ *               Jacobian of (v_f, v_s) -> (v_f', v_s') and its derivatives
+ *               in m_f and m_s (through the mean, the weights m/(m_f+m_s) and
+ *               the factor 1/(1 + dt K (1/m_f + 1/m_s)));
+ *   gravity     identity;
+ *   division    v = mv/m where m > 0: (mv)^ = v^/m, m^ += -v^ mv/m^2; faces
+ *               with m = 0 pass nothing.
+ * Returns OR_OK, or OR_ERR_NOT_CONVERGED if the adjoint solve did not.      */
+int or_grid_update_adjoint(int nx, int ny, int nz, double dt, double gx, double gy, double gz,
+                           double drag_k, const double *const *fm,
+                           const double *const *fp, const double *const *sm,
+                           const double *const *sp, const uint8_t *fluid, double rtol,
+                           int maxiter, const double *const *lfv, const double *const *lsv,
+                           double *const *lfm, double *const *lfp, double *const *lsm,
+                           double *const *lsp)
+{
+    int n3[3] = {nx, ny, nz};
+    double g[3] = {gx, gy, gz};
+    int solid = sm != NULL;
+    int rc = OR_OK;
+    double *lf[3];
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        size_t cnt = (size_t)d[0] * d[1] * d[2];
+        lf[a] = malloc(cnt * sizeof(double));
+        memcpy(lf[a], lfv[a], cnt * sizeof(double));
+    }
+    if (fluid) {
+        size_t nc = (size_t)nx * ny * nz;
+        double *s = calloc(nc, sizeof(double)), *q = calloc(nc, sizeof(double));
+        double *diag = calloc(nc, sizeof(double));
+        laplacian_diag(nx, ny, nz, fluid, diag);
+        /* s = G^T v^': +v^' on a face whose upper cell is c, -v^' on one whose
+         * lower cell is c, interior faces only */
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    size_t c = CIDX(i, j, k);
+                    if (!fluid[c]) continue;
+                    int ijk[3] = {i, j, k};
+                    double acc = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        int d[3]; face_dims(a, nx, ny, nz, d);
+                        int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                        hi[a] += 1;
+                        if (ijk[a] > 0) acc += lf[a][((size_t)lo[2] * d[1] + lo[1]) * d[0] + lo[0]];
+                        if (ijk[a] + 1 < n3[a]) acc -= lf[a][((size_t)hi[2] * d[1] + hi[1]) * d[0] + hi[0]];
+                    }
+                    s[c] = acc;
+                }
+        if (jacobi_pcg(nx, ny, nz, fluid, diag, s, q, rtol, maxiter) < 0) rc = OR_ERR_NOT_CONVERGED;
+        /* v^ += dx D^T q: face f gets (q_cl - q_ch)/dx from the two cells it bounds */
+        for (int a = 0; a < 3; ++a) {
+            int d[3]; face_dims(a, nx, ny, nz, d);
+            for (int k = 0; k < d[2]; ++k)
+                for (int j = 0; j < d[1]; ++j)
+                    for (int i = 0; i < d[0]; ++i) {
+                        int f[3] = {i, j, k};
+                        double ql = 0.0, qh = 0.0;
+                        if (f[a] > 0) {
+                            int lo[3] = {i, j, k};
+                            lo[a] -= 1;
+                            size_t cl = CIDX(lo[0], lo[1], lo[2]);
+                            if (fluid[cl]) ql = q[cl];
+                        }
+                        if (f[a] < n3[a]) {
+                            size_t ch = CIDX(i, j, k);
+                            if (fluid[ch]) qh = q[ch];
+                        }
+                        lf[a][((size_t)k * d[1] + j) * d[0] + i] += ql - qh;
+                    }
+        }
+        free(s); free(q); free(diag);
+    }
+    for (int a = 0; a < 3; ++a) {
+        int d[3]; face_dims(a, nx, ny, nz, d);
+        for (int k = 0; k < d[2]; ++k)
+            for (int j = 0; j < d[1]; ++j)
+                for (int i = 0; i < d[0]; ++i) {
+                    size_t idx = ((size_t)k * d[1] + j) * d[0] + i;
+                    int ia = (a == 0) ? i : (a == 1) ? j : k;
+                    int wall = (ia == 0 || ia == d[a] - 1);
+                    double lvf = wall ? 0.0 : lf[a][idx];
+                    double lvs = (solid && !wall) ? lsv[a][idx] : 0.0;
+                    double mf = fm[a][idx], ms = solid ? sm[a][idx] : 0.0;
+                    double dmf = 0.0, dms = 0.0;   /* mass adjoints from the drag */
+                    if (solid && drag_k > 0.0 && mf > 0.0 && ms > 0.0) {
+                        double vf = fp[a][idx] / mf + dt * g[a];
+                        double vs = sp[a][idx] / ms + dt * g[a];
+                        double M = mf + ms, wa = ms / M, wb = mf / M;
+                        double Dd = 1.0 + dt * drag_k * (1.0 / mf + 1.0 / ms);
+                        double u = (vf - vs) / Dd, mean = wb * vf + wa * vs;
+                        /* d(mean)/dm, d(wa)/dm, d(wb)/dm, du/dm */
+                        double mean_f = (vf - mean) / M, mean_s = (vs - mean) / M;
+                        double wa_f = -ms / (M * M), wa_s = mf / (M * M);
+                        double wb_f = ms / (M * M), wb_s = -mf / (M * M);
+                        double u_f = u * dt * drag_k / (Dd * mf * mf);
+                        double u_s = u * dt * drag_k / (Dd * ms * ms);
+                        dmf = lvf * (mean_f + wa_f * u + wa * u_f) + lvs * (mean_f - wb_f * u - wb * u_f);
+                        dms = lvf * (mean_s + wa_s * u + wa * u_s) + lvs * (mean_s - wb_s * u - wb * u_s);
+                        double lf_new = lvf * (wb + wa / Dd) + lvs * (wb - wb / Dd);
+                        double ls_new = lvf * (wa - wa / Dd) + lvs * (wa + wb / Dd);
+                        lvf = lf_new;
+                        lvs = ls_new;
+                    }
+                    if (mf > 0.0) {
+                        lfp[a][idx] = lvf / mf;
+                        lfm[a][idx] = dmf - lvf * fp[a][idx] / (mf * mf);
+                    } else {
+                        lfp[a][idx] = 0.0;
+                        lfm[a][idx] = 0.0;
+                    }
+                    if (solid) {
+                        if (ms > 0.0) {
+                            lsp[a][idx] = lvs / ms;
+                            lsm[a][idx] = dms - lvs * sp[a][idx] / (ms * ms);
+                        } else {
+                            lsp[a][idx] = 0.0;
+                            lsm[a][idx] = 0.0;
+                        }
+                    }
+                }
+        free(lf[a]);
+    }
+    return rc;
+}
+#undef CIDX
