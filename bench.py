@@ -154,7 +154,7 @@ class ClockSampler:
 # read, 13.8 MB written); P2G traffic grows in proportion to the particles, so
 # it scales to the 128^3 launch.  It must go back to None whenever the kernel
 # changes after that capture.
-P2G_TILES_DRAM_BYTES_PER_PARTICLE = None
+P2G_TILES_DRAM_BYTES_PER_PARTICLE = (537.27232e6 + 13.886464e6) / 1557376
 
 
 def algorithmic_bytes(R: int, fmt: str):
