@@ -269,7 +269,7 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
                             const polypic_update_params *params, void *ws, size_t ws_bytes,
                             void *stream);
 
-/* ---- adjoints (constant map, single phase, no projection) ---------------- *
+/* ---- adjoints (constant map) ---------------------------------------------- *
  * Contexts with POLYPIC_MAP_AFFINE (4 modes or more) or POLYPIC_APIC_GRAD_W get
  * UNSUPPORTED from the G2P adjoint, and with the affine map from the P2G
  * adjoint.
@@ -290,12 +290,37 @@ polypic_status polypic_g2p_adjoint(polypic_ctx *ctx, const polypic_grid *g,
                                    polypic_particles *bar_in, int32_t flags, void *ws,
                                    size_t ws_bytes, void *stream);
 
-/* Adjoint of polypic_grid_update (single phase, no drag, no projection):
- * given bar_out->vel, writes bar_in->mass and bar_in->mom from g->mass and
- * g->mom.  Wall faces and faces with m = 0 pass no gradient. */
-polypic_status polypic_grid_update_adjoint(polypic_ctx *ctx, const polypic_grid *g,
+/* Adjoint of polypic_grid_update with the same params (the update is
+ * delegated to the host simulator by the paper; this is the transpose of its
+ * stated minimal form), last step first:
+ *   projection (params->project): (P W)^T = P W -- walls then the projection
+ *     form an orthogonal projector onto the discretely divergence-free
+ *     fields of the fluid cells, so the wall-zeroed bar_fluid_out->vel is
+ *     projected exactly as the forward projects a velocity (same fluid cells
+ *     from fluid_particles->cell_start, same CG to params->pcg_rtol; needs
+ *     the workspace; NOT_CONVERGED as for the forward);
+ *   walls: no gradient on the wall faces;
+ *   drag (solid grid, drag_k > 0, faces holding both masses): the
+ *     transposed Jacobian of (v_f, v_s) -> (v_f', v_s') and the drag's
+ *     derivatives in m_f and m_s (through the mean, the weights m/(m_f+m_s)
+ *     and the factor 1/(1 + dt K (1/m_f + 1/m_s)));
+ *   gravity: identity;
+ *   v = mv/m: bar(mv) = bar v / m, bar m = (drag term) - bar v mv / m^2 on
+ *     faces with m > 0; faces with m = 0 pass no gradient.
+ * fluid / solid hold the forward's inputs (mass, mom).  Writes
+ * bar_fluid_in->mass and ->mom (and bar_solid_in's with a solid grid) from
+ * bar_fluid_out->vel (and bar_solid_out->vel).  solid, bar_solid_out and
+ * bar_solid_in are all NULL or all set; fluid_particles and ws may be NULL
+ * without the projection.  bar_fluid_in may be the same grid as
+ * bar_fluid_out (its mass and mom are written, its vel only read), and
+ * likewise for the solid. */
+polypic_status polypic_grid_update_adjoint(polypic_ctx *ctx, const polypic_grid *fluid,
+                                           const polypic_grid *solid,
+                                           const polypic_particles *fluid_particles,
                                            const polypic_update_params *params,
-                                           const polypic_grid *bar_out, polypic_grid *bar_in,
+                                           const polypic_grid *bar_fluid_out,
+                                           const polypic_grid *bar_solid_out,
+                                           polypic_grid *bar_fluid_in, polypic_grid *bar_solid_in,
                                            void *ws, size_t ws_bytes, void *stream);
 
 /* Adjoint of polypic_p2g at the state `in`: given bar_grid->mass and

@@ -25,6 +25,16 @@ bool valid_modes(int r) { return r == 1 || r == 4 || r == 8 || r == 27; }
 
 int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 
+int64_t face_count(const GridGeom &g, int a) {
+    return (int64_t)(g.n[0] + (a == 0)) * (g.n[1] + (a == 1)) * (g.n[2] + (a == 2));
+}
+
+size_t face_bytes(const GridGeom &g) {
+    size_t t = 0;
+    for (int a = 0; a < 3; ++a) t += (size_t)face_count(g, a) * sizeof(float);
+    return t;
+}
+
 size_t required_ws(const polypic_ctx *c, int64_t nf, int64_t ns) {
     int64_t n = max64(nf, ns);
     size_t a = sort_scratch_bytes(n, c->num_keys);
@@ -34,8 +44,11 @@ size_t required_ws(const polypic_ctx *c, int64_t nf, int64_t ns) {
     size_t e = c->cfg.coeff_format == POLYPIC_COEFF_F32
                    ? adjoint_scratch_bytes(n, c->cfg.num_modes) + b + 256
                    : 0;
+    // the grid-update adjoint with the projection: three face arrays, then
+    // the projection's scratch
+    size_t f = d + face_bytes(c->geom) + 4 * 256;
     size_t m = a > b ? a : b;
-    m = m > d ? m : d;
+    m = m > f ? m : f;
     m = m > e ? m : e;
     return m + 4096;
 }
@@ -444,29 +457,63 @@ polypic_status polypic_g2p_adjoint(polypic_ctx *ctx, const polypic_grid *g,
                                  as_stream(stream)));
 }
 
-polypic_status polypic_grid_update_adjoint(polypic_ctx *ctx, const polypic_grid *g,
+polypic_status polypic_grid_update_adjoint(polypic_ctx *ctx, const polypic_grid *fluid,
+                                           const polypic_grid *solid,
+                                           const polypic_particles *fluid_particles,
                                            const polypic_update_params *params,
-                                           const polypic_grid *bar_out, polypic_grid *bar_in,
+                                           const polypic_grid *bar_fluid_out,
+                                           const polypic_grid *bar_solid_out,
+                                           polypic_grid *bar_fluid_in, polypic_grid *bar_solid_in,
                                            void *ws, size_t ws_bytes, void *stream) {
-    (void)ws;
-    (void)ws_bytes;
     if (!ctx) return POLYPIC_ERR_INVALID_ARG;
     polypic_status s = check_params(params);
     if (s != POLYPIC_OK) return s;
-    if (params->project || params->drag_k != 0.0f) return POLYPIC_ERR_UNSUPPORTED;
-    if (!grid_ok(g, true, true, false) || !grid_ok(bar_out, false, false, true) ||
-        !grid_ok(bar_in, true, true, false))
+    if (!grid_ok(fluid, true, true, false) || !grid_ok(bar_fluid_out, false, false, true) ||
+        !grid_ok(bar_fluid_in, true, true, false))
         return POLYPIC_ERR_INVALID_ARG;
+    const bool two = solid != nullptr;
+    if (two != (bar_solid_out != nullptr) || two != (bar_solid_in != nullptr))
+        return POLYPIC_ERR_INVALID_ARG;
+    if (two && (!grid_ok(solid, true, true, false) || !grid_ok(bar_solid_out, false, false, true) ||
+                !grid_ok(bar_solid_in, true, true, false)))
+        return POLYPIC_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
     GridAdjointArgs U{};
     U.g = ctx->geom;
+    U.dt = params->dt;
+    U.drag_k = params->drag_k;
     for (int a = 0; a < 3; ++a) {
-        U.fm[a] = g->mass[a];
-        U.fp[a] = g->mom[a];
-        U.lv[a] = bar_out->vel[a];
-        U.lm[a] = bar_in->mass[a];
-        U.lp[a] = bar_in->mom[a];
+        U.gravity[a] = params->gravity[a];
+        U.fm[a] = fluid->mass[a];
+        U.fp[a] = fluid->mom[a];
+        U.lv[a] = bar_fluid_out->vel[a];
+        U.lm[a] = bar_fluid_in->mass[a];
+        U.lp[a] = bar_fluid_in->mom[a];
+        U.sm[a] = two ? solid->mass[a] : nullptr;
+        U.sp[a] = two ? solid->mom[a] : nullptr;
+        U.lsv[a] = two ? bar_solid_out->vel[a] : nullptr;
+        U.lsm[a] = two ? bar_solid_in->mass[a] : nullptr;
+        U.lsp[a] = two ? bar_solid_in->mom[a] : nullptr;
     }
-    return from_cuda(grid_update_adjoint(U, as_stream(stream)));
+    if (params->project) {
+        // (P W)^T = P W: the walls-then-projection map is an orthogonal
+        // projector, so its transpose is the forward projection applied to
+        // the wall-zeroed adjoint (same fluid cells, any dt and rho)
+        if (!fluid_particles || !fluid_particles->cell_start) return POLYPIC_ERR_INVALID_ARG;
+        if (!ws || ((uintptr_t)ws & 255u) != 0 || ws_bytes < required_ws(ctx, 0, 0))
+            return POLYPIC_ERR_WORKSPACE;
+        Workspace W{static_cast<char *>(ws), ws_bytes, 0};
+        float *lam[3];
+        for (int a = 0; a < 3; ++a) lam[a] = W.take<float>((size_t)face_count(ctx->geom, a));
+        if (W.overflow) return POLYPIC_ERR_WORKSPACE;
+        if (wall_zeroed_copy(ctx->geom, bar_fluid_out->vel, lam, st) != cudaSuccess)
+            return POLYPIC_ERR_CUDA;
+        s = pcg_project(ctx->geom, ctx->num_keys, fluid_particles->cell_start, lam, params->dt,
+                        params->rho, params->pcg_maxiter, params->pcg_rtol, ctx->d_status, W, st);
+        if (s != POLYPIC_OK) return s;
+        for (int a = 0; a < 3; ++a) U.lv[a] = lam[a];
+    }
+    return from_cuda(grid_update_adjoint(U, st));
 }
 
 polypic_status polypic_p2g_adjoint(polypic_ctx *ctx, const polypic_particles *in,

@@ -18,11 +18,19 @@ struct GridUpdateArgs {
 
 struct GridAdjointArgs {
     GridGeom g;
-    const float *fm[3], *fp[3], *lv[3];
+    float dt;
+    float gravity[3];
+    float drag_k;
+    const float *fm[3], *fp[3], *lv[3];   // lv: dL/dv~ of the fluid (projected already)
     float *lm[3], *lp[3];
+    const float *sm[3], *sp[3], *lsv[3];  // all NULL without a solid grid
+    float *lsm[3], *lsp[3];
 };
 
 cudaError_t grid_update(const GridUpdateArgs &U, cudaStream_t s);
 cudaError_t grid_update_adjoint(const GridAdjointArgs &U, cudaStream_t s);
+// dst = src with the wall faces i_a in {0, n_a} zeroed (all three face grids)
+cudaError_t wall_zeroed_copy(const GridGeom &g, const float *const src[3], float *const dst[3],
+                             cudaStream_t s);
 
 }  // namespace polypic

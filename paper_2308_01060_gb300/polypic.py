@@ -107,7 +107,8 @@ def load_library(path: str = LIB_PATH):
         "polypic_g2p_adjoint": (st, [_vp, P(Grid), P(Particles), ctypes.c_float, P(Particles),
                                      P(Grid), P(Particles), ctypes.c_int32, _vp, ctypes.c_size_t,
                                      _vp]),
-        "polypic_grid_update_adjoint": (st, [_vp, P(Grid), P(UpdateParams), P(Grid), P(Grid), _vp,
+        "polypic_grid_update_adjoint": (st, [_vp, P(Grid), P(Grid), P(Particles), P(UpdateParams),
+                                             P(Grid), P(Grid), P(Grid), P(Grid), _vp,
                                              ctypes.c_size_t, _vp]),
         "polypic_p2g_adjoint": (st, [_vp, P(Particles), P(Grid), P(Particles), ctypes.c_int32, _vp,
                                      ctypes.c_size_t, _vp]),
@@ -393,12 +394,21 @@ def polypic_g2p_adjoint(ctx: Context, g: GridState, p_in: ParticleState, dt: flo
 
 
 def polypic_grid_update_adjoint(ctx: Context, g: GridState, params: UpdateSettings,
-                                bar_out: GridState, bar_in: GridState, stream=None):
+                                bar_out: GridState, bar_in: GridState,
+                                solid: Optional[GridState] = None,
+                                bar_solid_out: Optional[GridState] = None,
+                                bar_solid_in: Optional[GridState] = None,
+                                fluid_particles: Optional[ParticleState] = None,
+                                ws: Optional[torch.Tensor] = None, stream=None):
+    ref = lambda x: ctypes.byref(x) if x is not None else None
+    cs = lambda x: x.c_struct() if x is not None else None
     cg, bo, bi = g.c_struct(), bar_out.c_struct(), bar_in.c_struct()
     up = params.c_struct()
+    wp, wb = _ws(ws) if ws is not None else (None, 0)
     _check(load_library().polypic_grid_update_adjoint(
-        ctx.handle, ctypes.byref(cg), ctypes.byref(up), ctypes.byref(bo), ctypes.byref(bi), None,
-        0, _stream(stream)), "polypic_grid_update_adjoint")
+        ctx.handle, ctypes.byref(cg), ref(cs(solid)), ref(cs(fluid_particles)), ctypes.byref(up),
+        ctypes.byref(bo), ref(cs(bar_solid_out)), ctypes.byref(bi), ref(cs(bar_solid_in)), wp, wb,
+        _stream(stream)), "polypic_grid_update_adjoint")
 
 
 def polypic_p2g_adjoint(ctx: Context, p_in: ParticleState, bar_grid: GridState,
