@@ -86,6 +86,10 @@ def _load():
                                           _PA, _PA]),
         "or_g2p_adjoint": (_int, [_i64, _D, _D, _D, _D, _D, _D, _int, _int, _int, _int, _dbl,
                                   _dbl] + [_D] * 10),
+        "or_fabric_forces": (None, [_i64, _D, _D, _D, _D, _D, _D, _int, _U32, _int, _dbl, _dbl,
+                                    _dbl, _dbl, _dbl, _dbl]),
+        "or_absorb": (None, [_i64, _F, _F, _F, _D, _i64, _F, _F, _F, _D, _D, _int, _int, _int,
+                             _dbl, _dbl, _dbl, _dbl, _dbl]),
         "or_pcg_project": (_int, [_int, _int, _int, _dbl, _dbl, _dbl, _U8, _D, _D, _D, _D,
                                   _dbl, _int]),
     }
@@ -374,3 +378,39 @@ def step(x, mass, coeff, n, dx, dt, gravity=(0.0, -9.81, 0.0), mass_abs=None):
     gv = grid_update(n, dt, gravity, gm, gp)
     c_new, x_new = g2p(x, gv, R, n, dx, dt)
     return c_new, x_new, (gm, gp, gv)
+
+
+def fabric_forces(x, mass, coeff, vertex_id, m, h, k_stretch, k_shear, k_bend, damping, dt,
+                  mass_abs=None):
+    """Mass-spring stand-in on the sheet's vertex lattice: returns the
+    coefficients with mode 0 (the velocity) of every vertex advanced by
+    dt f / (m + m_abs).  vertex_id: lattice id per particle (>= m^2: no
+    springs)."""
+    D = ctypes.c_double
+    x = _f64(x)
+    mass = _f64(mass)
+    mabs = None if mass_abs is None else _f64(mass_abs)
+    c = _f64(coeff).copy()
+    ids = np.ascontiguousarray(vertex_id, dtype=np.uint32)
+    P = x.shape[1]
+    _load().or_fabric_forces(P, _p(x[0], D), _p(x[1], D), _p(x[2], D), _p(mass, D),
+                             _p(mabs, D), _p(c, D), int(c.shape[1]), _p(ids, ctypes.c_uint32),
+                             int(m), float(h), float(k_stretch), float(k_shear), float(k_bend),
+                             float(damping), float(dt))
+    return c
+
+
+def absorb(xf32, fmass, xs32, smass, mass_abs, n, dx, dt, rate, capacity, max_fraction):
+    """Absorption stand-in per cell: returns (fluid masses, solid m_abs)."""
+    D = ctypes.c_double
+    xf32 = _f32(xf32)
+    xs32 = _f32(xs32)
+    fm = _f64(fmass).copy()
+    ma = _f64(mass_abs).copy()
+    sm = _f64(smass)
+    F = ctypes.c_float
+    _load().or_absorb(xf32.shape[1], _p(xf32[0], F), _p(xf32[1], F), _p(xf32[2], F), _p(fm, D),
+                      xs32.shape[1], _p(xs32[0], F), _p(xs32[1], F), _p(xs32[2], F), _p(sm, D),
+                      _p(ma, D), int(n[0]), int(n[1]), int(n[2]), float(dx), float(dt),
+                      float(rate), float(capacity), float(max_fraction))
+    return fm, ma

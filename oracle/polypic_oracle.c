@@ -1061,3 +1061,99 @@ int or_grid_update_adjoint(int nx, int ny, int nz, double dt, double gx, double 
     return rc;
 }
 #undef CIDX
+/* ------------------------------------------------------------------------ */
+/* Fabric stand-in (the paper takes the cloth mechanics from Fei et al.,
+ * Sections 3.4 and 4, and gives no force model): a mass-spring lattice on the
+ * sheet's vertex particles.  Vertex (i, k) of an m x m lattice has id k m + i;
+ * ids >= m^2 (element particles) carry no springs.  Springs join each vertex
+ * to its lattice neighbours at offsets (+-1, 0), (0, +-1) [stretch, rest h],
+ * (+-1, +-1) [shear, rest h sqrt 2] and (+-2, 0), (0, +-2) [bend, rest 2h].
+ * The force of the spring to neighbour j on vertex i, with d = x_j - x_i,
+ * L = |d|, e = d / L:   f = k (L - L0) e + c ((v_j - v_i) . e) e.
+ * The velocity of vertex i (mode 0 of its coefficients) then takes one
+ * explicit step  v_i += dt sum f / (m_i + m_abs,i); every velocity is read
+ * before any is written.  x, v in particle order, id[p] the lattice id.    */
+void or_fabric_forces(int64_t np, const double *x, const double *y, const double *z,
+                      const double *mass, const double *mass_abs, double *coeff, int R,
+                      const uint32_t *id, int m, double h, double k_stretch, double k_shear,
+                      double k_bend, double damping, double dt)
+{
+    int64_t nv = (int64_t)m * m;
+    int64_t *slot = malloc((size_t)nv * sizeof(int64_t));
+    double *dv = calloc((size_t)np * 3, sizeof(double));
+    for (int64_t v = 0; v < nv; ++v) slot[v] = -1;
+    for (int64_t p = 0; p < np; ++p)
+        if (id[p] < (uint32_t)nv) slot[id[p]] = p;
+    const int off[12][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {1, -1}, {-1, 1},
+                            {-1, -1}, {2, 0}, {-2, 0}, {0, 2}, {0, -2}};
+    const double *pos[3] = {x, y, z};
+    for (int64_t p = 0; p < np; ++p) {
+        if (id[p] >= (uint32_t)nv) continue;
+        int i = (int)(id[p] % (uint32_t)m), k = (int)(id[p] / (uint32_t)m);
+        double f[3] = {0.0, 0.0, 0.0};
+        for (int s = 0; s < 12; ++s) {
+            int i2 = i + off[s][0], k2 = k + off[s][1];
+            if (i2 < 0 || i2 >= m || k2 < 0 || k2 >= m) continue;
+            int64_t q = slot[(int64_t)k2 * m + i2];
+            if (q < 0) continue;
+            double kk = s < 4 ? k_stretch : s < 8 ? k_shear : k_bend;
+            double L0 = s < 4 ? h : s < 8 ? h * sqrt(2.0) : 2.0 * h;
+            double d[3], L = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                d[a] = pos[a][q] - pos[a][p];
+                L += d[a] * d[a];
+            }
+            L = sqrt(L);
+            if (!(L > 0.0)) continue;
+            double rv = 0.0;
+            for (int a = 0; a < 3; ++a)
+                rv += (coeff[((size_t)a * R) * np + q] - coeff[((size_t)a * R) * np + p]) * d[a] / L;
+            for (int a = 0; a < 3; ++a) f[a] += (kk * (L - L0) + damping * rv) * d[a] / L;
+        }
+        double mt = mass[p] + (mass_abs ? mass_abs[p] : 0.0);
+        for (int a = 0; a < 3; ++a) dv[(size_t)a * np + p] = dt * f[a] / mt;
+    }
+    for (int64_t p = 0; p < np; ++p)
+        for (int a = 0; a < 3; ++a) coeff[((size_t)a * R) * np + p] += dv[(size_t)a * np + p];
+    free(slot);
+    free(dv);
+}
+
+/* Absorption stand-in (the paper takes m_abs as given, Eqs 18-20; its
+ * dynamics are Fei et al.'s porous flow): per cell, with M_f the fluid mass
+ * of the cell's fluid particles, each solid particle p in the cell asks for
+ * d_p = min(rate dt m_s,p, max(0, capacity m_s,p - m_abs,p)); the cell gives
+ * D = min(sum d_p, max_fraction M_f); solid particle p gains d_p D / sum d
+ * and fluid particle q loses m_q D / M_f, so the cell's total mass is kept.
+ * Cells are decided in FP32 as for the sort (fx, fy, fz: FP32 positions).  */
+void or_absorb(int64_t nf, const float *fx, const float *fy, const float *fz, double *fmass,
+               int64_t ns, const float *sx, const float *sy, const float *sz,
+               const double *smass, double *mass_abs, int nx, int ny, int nz, double dx,
+               double dt, double rate, double capacity, double max_fraction)
+{
+    size_t nc = (size_t)nx * ny * nz;
+    double *Mf = calloc(nc, sizeof(double)), *Dd = calloc(nc, sizeof(double));
+    uint32_t *kf = malloc((size_t)(nf > 0 ? nf : 1) * sizeof(uint32_t));
+    uint32_t *ks = malloc((size_t)(ns > 0 ? ns : 1) * sizeof(uint32_t));
+    or_keys(nf, fx, fy, fz, nx, ny, nz, dx, kf);
+    or_keys(ns, sx, sy, sz, nx, ny, nz, dx, ks);
+    for (int64_t q = 0; q < nf; ++q) Mf[kf[q]] += fmass[q];
+    double *d = malloc((size_t)(ns > 0 ? ns : 1) * sizeof(double));
+    for (int64_t p = 0; p < ns; ++p) {
+        double room = capacity * smass[p] - mass_abs[p];
+        double want = rate * dt * smass[p];
+        d[p] = room > 0.0 ? (want < room ? want : room) : 0.0;
+        Dd[ks[p]] += d[p];
+    }
+    for (int64_t p = 0; p < ns; ++p) {
+        size_t c = ks[p];
+        double D = Dd[c] < max_fraction * Mf[c] ? Dd[c] : max_fraction * Mf[c];
+        if (D > 0.0) mass_abs[p] += d[p] * D / Dd[c];
+    }
+    for (int64_t q = 0; q < nf; ++q) {
+        size_t c = kf[q];
+        double D = Dd[c] < max_fraction * Mf[c] ? Dd[c] : max_fraction * Mf[c];
+        if (D > 0.0) fmass[q] -= fmass[q] * D / Mf[c];
+    }
+    free(Mf); free(Dd); free(kf); free(ks); free(d);
+}
