@@ -120,7 +120,9 @@ typedef struct polypic_config {
  *               is the total degree of mode r and s_p = max |c_pra dx^L_r|
  *   coeff_scale [count] float s_p (16-bit formats only, else NULL)
  *   key, perm   [count] uint32, written by polypic_sort (perm: slot order)
- *   cell_start  [polypic_num_keys() + 1] uint32, written by polypic_sort   */
+ *   cell_start  [polypic_num_keys() + 1] uint32, written by polypic_sort
+ *   id          [count] uint32 or NULL: a label carried with each particle by
+ *               polypic_step_coupled (the sheet's lattice ids)              */
 typedef struct polypic_particles {
     int64_t count;
     float *x[3];
@@ -131,6 +133,7 @@ typedef struct polypic_particles {
     uint32_t *key;
     uint32_t *perm;
     uint32_t *cell_start;
+    uint32_t *id;
 } polypic_particles;
 
 /* The three face grids of one phase (device memory, caller-owned). */
@@ -149,6 +152,27 @@ typedef struct polypic_update_params {
     int32_t pcg_maxiter;
     double pcg_rtol;
 } polypic_update_params;
+
+/* Stand-ins for the fabric mechanics and the absorption, which the paper
+ * takes from Fei et al. (Sections 3.4 and 4; Eqs 18-20 take m_abs as given).
+ *   verts_per_side  m: the sheet's vertex particles carry lattice ids k m + i
+ *                   (ids >= m^2: element particles, no springs)
+ *   rest_length     h, the lattice spacing at rest
+ *   k_stretch, k_shear, k_bend  spring constants (N/m) of the springs to the
+ *                   neighbours at (+-1, 0), (0, +-1); (+-1, +-1); (+-2, 0),
+ *                   (0, +-2), rest lengths h, h sqrt 2, 2h
+ *   damping         c (kg/s) of the dampers along the same springs
+ *   absorb_rate     rate (1/s) at which a solid particle takes fluid mass,
+ *                   relative to its own mass m_s; 0 disables absorption
+ *   absorb_capacity the most m_abs a solid particle holds, relative to m_s
+ *   absorb_max_fraction  the most of a cell's fluid mass taken in one step */
+typedef struct polypic_fabric_params {
+    int32_t verts_per_side;
+    float rest_length;
+    float k_stretch, k_shear, k_bend;
+    float damping;
+    float absorb_rate, absorb_capacity, absorb_max_fraction;
+} polypic_fabric_params;
 
 /* ---- context ------------------------------------------------------------ */
 
@@ -268,6 +292,40 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
                             polypic_particles *solid_out, polypic_grid *gf, polypic_grid *gs,
                             const polypic_update_params *params, void *ws, size_t ws_bytes,
                             void *stream);
+
+/* Fabric forces (stand-in): for every vertex particle of `solid` (id <
+ * m^2), with d = x_j - x_i, L = |d|, e = d / L over the lattice neighbours
+ * present, f = sum k (L - L0) e + c ((v_j - v_i) . e) e, and the velocity
+ * (mode 0 of the coefficients, FP32 contexts only: UNSUPPORTED otherwise)
+ * takes v_i += dt f / (m_i + m_abs,i), in place; all velocities are read
+ * before any is written.  Needs solid->id and the workspace; the arrays may
+ * be in any order (ids are unique). */
+polypic_status polypic_fabric_forces(polypic_ctx *ctx, polypic_particles *solid,
+                                     const polypic_fabric_params *fabric, float dt, void *ws,
+                                     size_t ws_bytes, void *stream);
+
+/* Absorption (stand-in), per cell, both phases sorted (polypic_sort): with
+ * M_f the mass of the cell's fluid particles, each solid particle asks
+ * d_p = min(rate dt m_s, max(0, capacity m_s - m_abs)), the cell gives
+ * D = min(sum d_p, max_fraction M_f); solid particle p gains d_p D / sum d
+ * (in solid->mass_abs), each fluid particle loses m_q D / M_f (in
+ * fluid->mass).  The cell's total mass is kept; sums run in slot order
+ * (deterministic).  In place. */
+polypic_status polypic_absorb(polypic_ctx *ctx, polypic_particles *fluid,
+                              polypic_particles *solid, const polypic_fabric_params *fabric,
+                              float dt, void *stream);
+
+/* polypic_step for a fluid and a fabric sheet with the stand-ins: sort both
+ * phases, absorption, fabric forces (both in place on the input states), P2G
+ * of both, the grid update (drag, projection), G2P of both, and the lattice
+ * ids carried to solid_out->id through the solid's slot order.  Requires a
+ * solid phase with ids (solid_in->id, solid_out->id). */
+polypic_status polypic_step_coupled(polypic_ctx *ctx, polypic_particles *fluid_in,
+                                    polypic_particles *fluid_out, polypic_particles *solid_in,
+                                    polypic_particles *solid_out, polypic_grid *gf,
+                                    polypic_grid *gs, const polypic_update_params *params,
+                                    const polypic_fabric_params *fabric, void *ws,
+                                    size_t ws_bytes, void *stream);
 
 /* ---- adjoints (constant map) ---------------------------------------------- *
  * Contexts with POLYPIC_MAP_AFFINE (4 modes or more) or POLYPIC_APIC_GRAD_W get

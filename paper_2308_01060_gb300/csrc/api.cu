@@ -12,6 +12,7 @@
 #include "p2g.cuh"
 #include "pcg.cuh"
 #include "adjoint.cuh"
+#include "fabric.cuh"
 #include "polypic_internal.cuh"
 #include "sort.cuh"
 
@@ -47,8 +48,12 @@ size_t required_ws(const polypic_ctx *c, int64_t nf, int64_t ns) {
     // the grid-update adjoint with the projection: three face arrays, then
     // the projection's scratch
     size_t f = d + face_bytes(c->geom) + 4 * 256;
+    // the fabric forces: a slot per lattice id (at most one per solid
+    // particle) and three velocity components per solid particle
+    size_t fb = (size_t)ns * 16 + 1024;
     size_t m = a > b ? a : b;
     m = m > f ? m : f;
+    m = m > fb ? m : fb;
     m = m > e ? m : e;
     return m + 4096;
 }
@@ -427,6 +432,145 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
     if ((s = do_g2p(ctx, gf, fluid_in, fluid_out, params->dt, st)) != POLYPIC_OK) return s;
     if (solid && (s = do_g2p(ctx, gs, solid_in, solid_out, params->dt, st)) != POLYPIC_OK) return s;
     return POLYPIC_OK;
+}
+
+namespace {
+
+bool fabric_ok(const polypic_fabric_params *f) {
+    return f && f->verts_per_side >= 0 && std::isfinite(f->rest_length) && f->rest_length >= 0.0f &&
+           std::isfinite(f->k_stretch) && std::isfinite(f->k_shear) && std::isfinite(f->k_bend) &&
+           std::isfinite(f->damping) && std::isfinite(f->absorb_rate) &&
+           f->absorb_rate >= 0.0f && std::isfinite(f->absorb_capacity) &&
+           std::isfinite(f->absorb_max_fraction) && f->absorb_max_fraction >= 0.0f &&
+           f->absorb_max_fraction <= 1.0f;
+}
+
+bool forces_on(const polypic_fabric_params *f) {
+    return f->verts_per_side > 0 && (f->k_stretch != 0.0f || f->k_shear != 0.0f ||
+                                     f->k_bend != 0.0f || f->damping != 0.0f);
+}
+
+polypic_status do_fabric_forces(polypic_ctx *c, polypic_particles *p,
+                                const polypic_fabric_params *f, float dt, void *ws,
+                                size_t ws_bytes, cudaStream_t s) {
+    if (p->count == 0) return POLYPIC_OK;
+    FabricForceArgs A{};
+    A.count = p->count;
+    const int R = c->cfg.num_modes;
+    float *coeff = static_cast<float *>(p->coeff);
+    for (int a = 0; a < 3; ++a) {
+        A.x[a] = p->x[a];
+        A.vel[a] = coeff + (size_t)a * R * (size_t)p->count;
+    }
+    A.mass = p->mass;
+    A.mass_abs = p->mass_abs;
+    A.id = p->id;
+    A.m = f->verts_per_side;
+    A.h = f->rest_length;
+    A.k_stretch = f->k_stretch;
+    A.k_shear = f->k_shear;
+    A.k_bend = f->k_bend;
+    A.damping = f->damping;
+    A.dt = dt;
+    Workspace W{static_cast<char *>(ws), ws_bytes, 0};
+    if (fabric_scratch_bytes(p->count, A.m) > ws_bytes) return POLYPIC_ERR_WORKSPACE;
+    return from_cuda(fabric_forces(A, W, s));
+}
+
+polypic_status do_absorb(polypic_ctx *c, polypic_particles *fl, polypic_particles *so,
+                         const polypic_fabric_params *f, float dt, cudaStream_t s) {
+    if (f->absorb_rate == 0.0f || fl->count == 0 || so->count == 0) return POLYPIC_OK;
+    AbsorbCall A{};
+    A.num_keys = c->num_keys;
+    A.fluid_cell_start = fl->cell_start;
+    A.fluid_perm = fl->perm;
+    A.solid_cell_start = so->cell_start;
+    A.solid_perm = so->perm;
+    A.fluid_mass = fl->mass;
+    A.solid_mass = so->mass;
+    A.mass_abs = so->mass_abs;
+    A.rate = f->absorb_rate;
+    A.dt = dt;
+    A.capacity = f->absorb_capacity;
+    A.max_fraction = f->absorb_max_fraction;
+    return from_cuda(absorb(A, s));
+}
+
+polypic_status check_fabric_solid(polypic_ctx *c, const polypic_particles *p, bool need_id) {
+    if (!p || !p->mass || (p->count > 0 && !p->coeff)) return POLYPIC_ERR_INVALID_ARG;
+    if (need_id && p->count > 0 && !p->id) return POLYPIC_ERR_INVALID_ARG;
+    if (c->cfg.coeff_format != POLYPIC_COEFF_F32) return POLYPIC_ERR_UNSUPPORTED;
+    return POLYPIC_OK;
+}
+
+}  // namespace
+
+polypic_status polypic_fabric_forces(polypic_ctx *ctx, polypic_particles *solid,
+                                     const polypic_fabric_params *fabric, float dt, void *ws,
+                                     size_t ws_bytes, void *stream) {
+    if (!ctx || !fabric_ok(fabric) || !std::isfinite(dt)) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s;
+    if ((s = check_positions(solid)) != POLYPIC_OK) return s;
+    if ((s = check_fabric_solid(ctx, solid, true)) != POLYPIC_OK) return s;
+    if (!forces_on(fabric)) return POLYPIC_OK;
+    if (!ws || ((uintptr_t)ws & 255u) != 0) return POLYPIC_ERR_WORKSPACE;
+    return do_fabric_forces(ctx, solid, fabric, dt, ws, ws_bytes, as_stream(stream));
+}
+
+polypic_status polypic_absorb(polypic_ctx *ctx, polypic_particles *fluid,
+                              polypic_particles *solid, const polypic_fabric_params *fabric,
+                              float dt, void *stream) {
+    if (!ctx || !fabric_ok(fabric) || !std::isfinite(dt)) return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s;
+    if ((s = check_sorted(fluid)) != POLYPIC_OK) return s;
+    if ((s = check_sorted(solid)) != POLYPIC_OK) return s;
+    if (!fluid->mass || !solid->mass || !solid->mass_abs) return POLYPIC_ERR_INVALID_ARG;
+    return do_absorb(ctx, fluid, solid, fabric, dt, as_stream(stream));
+}
+
+polypic_status polypic_step_coupled(polypic_ctx *ctx, polypic_particles *fluid_in,
+                                    polypic_particles *fluid_out, polypic_particles *solid_in,
+                                    polypic_particles *solid_out, polypic_grid *gf,
+                                    polypic_grid *gs, const polypic_update_params *params,
+                                    const polypic_fabric_params *fabric, void *ws,
+                                    size_t ws_bytes, void *stream) {
+    if (!ctx || !solid_in || !solid_out || !gs || !fabric_ok(fabric))
+        return POLYPIC_ERR_INVALID_ARG;
+    polypic_status s;
+    if ((s = check_sorted(fluid_in)) != POLYPIC_OK) return s;
+    if (fluid_in->count > 0 && !fluid_in->key) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_coeff(ctx, fluid_in)) != POLYPIC_OK) return s;
+    if ((s = check_g2p_out(ctx, fluid_in, fluid_out)) != POLYPIC_OK) return s;
+    if ((s = check_sorted(solid_in)) != POLYPIC_OK) return s;
+    if (solid_in->count > 0 && !solid_in->key) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_coeff(ctx, solid_in)) != POLYPIC_OK) return s;
+    if ((s = check_g2p_out(ctx, solid_in, solid_out)) != POLYPIC_OK) return s;
+    if (!solid_in->mass_abs) return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_fabric_solid(ctx, solid_in, true)) != POLYPIC_OK) return s;
+    if (solid_in->count > 0 && (!solid_out->id || solid_out->id == solid_in->id))
+        return POLYPIC_ERR_INVALID_ARG;
+    if (!grid_ok(gf, true, true, true) || !grid_ok(gs, true, true, true))
+        return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_params(params)) != POLYPIC_OK) return s;
+    const int64_t nmax = max64(fluid_in->count, solid_in->count);
+    if ((s = check_ws(ctx, nmax, ws, ws_bytes)) != POLYPIC_OK) return s;
+    if (ws_bytes < required_ws(ctx, fluid_in->count, solid_in->count)) return POLYPIC_ERR_WORKSPACE;
+    cudaStream_t st = as_stream(stream);
+    if ((s = do_sort(ctx, fluid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
+    if ((s = do_sort(ctx, solid_in, ws, ws_bytes, st)) != POLYPIC_OK) return s;
+    if ((s = do_absorb(ctx, fluid_in, solid_in, fabric, params->dt, st)) != POLYPIC_OK) return s;
+    if (forces_on(fabric) &&
+        (s = do_fabric_forces(ctx, solid_in, fabric, params->dt, ws, ws_bytes, st)) != POLYPIC_OK)
+        return s;
+    if ((s = do_p2g(ctx, fluid_in, gf, ws, ws_bytes, st, nullptr, params->dt)) != POLYPIC_OK)
+        return s;
+    if ((s = do_p2g(ctx, solid_in, gs, ws, ws_bytes, st, nullptr, params->dt)) != POLYPIC_OK)
+        return s;
+    if ((s = do_grid_update(ctx, gf, gs, fluid_in, params, ws, ws_bytes, st)) != POLYPIC_OK)
+        return s;
+    if ((s = do_g2p(ctx, gf, fluid_in, fluid_out, params->dt, st)) != POLYPIC_OK) return s;
+    if ((s = do_g2p(ctx, gs, solid_in, solid_out, params->dt, st)) != POLYPIC_OK) return s;
+    return from_cuda(gather_ids(solid_in->id, solid_in->perm, solid_in->count, solid_out->id, st));
 }
 
 polypic_status polypic_g2p_adjoint(polypic_ctx *ctx, const polypic_grid *g,

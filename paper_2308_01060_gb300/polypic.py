@@ -16,6 +16,7 @@ import os
 from dataclasses import dataclass, field
 from typing import List, Optional
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -51,7 +52,15 @@ class Config(ctypes.Structure):
 class Particles(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int64), ("x", _vp * 3), ("mass", _vp), ("mass_abs", _vp),
                 ("coeff", _vp), ("coeff_scale", _vp), ("key", _vp), ("perm", _vp),
-                ("cell_start", _vp)]
+                ("cell_start", _vp), ("id", _vp)]
+
+
+class FabricParams(ctypes.Structure):
+    _fields_ = [("verts_per_side", ctypes.c_int32), ("rest_length", ctypes.c_float),
+                ("k_stretch", ctypes.c_float), ("k_shear", ctypes.c_float),
+                ("k_bend", ctypes.c_float), ("damping", ctypes.c_float),
+                ("absorb_rate", ctypes.c_float), ("absorb_capacity", ctypes.c_float),
+                ("absorb_max_fraction", ctypes.c_float)]
 
 
 class Grid(ctypes.Structure):
@@ -72,7 +81,7 @@ EXPORTS = [
     "polypic_p2g_mapped", "polypic_p2g_noalloc",
     "polypic_grid_update", "polypic_g2p", "polypic_step", "polypic_g2p_adjoint",
     "polypic_grid_update_adjoint", "polypic_p2g_adjoint", "polypic_check_device_status",
-    "polypic_status_string",
+    "polypic_status_string", "polypic_fabric_forces", "polypic_absorb", "polypic_step_coupled",
 ]
 
 
@@ -113,6 +122,13 @@ def load_library(path: str = LIB_PATH):
         "polypic_p2g_adjoint": (st, [_vp, P(Particles), P(Grid), P(Particles), ctypes.c_int32, _vp,
                                      ctypes.c_size_t, _vp]),
         "polypic_check_device_status": (st, [_vp, _vp]),
+        "polypic_fabric_forces": (st, [_vp, P(Particles), P(FabricParams), ctypes.c_float, _vp,
+                                       ctypes.c_size_t, _vp]),
+        "polypic_absorb": (st, [_vp, P(Particles), P(Particles), P(FabricParams), ctypes.c_float,
+                                _vp]),
+        "polypic_step_coupled": (st, [_vp, P(Particles), P(Particles), P(Particles),
+                                      P(Particles), P(Grid), P(Grid), P(UpdateParams),
+                                      P(FabricParams), _vp, ctypes.c_size_t, _vp]),
         "polypic_status_string": (ctypes.c_char_p, [st]),
     }
     for name, (res, args) in sigs.items():
@@ -157,6 +173,7 @@ class ParticleState:
     cell_start: torch.Tensor
     mass_abs: Optional[torch.Tensor] = None
     scale: Optional[torch.Tensor] = None
+    id: Optional[torch.Tensor] = None
 
     @property
     def count(self) -> int:
@@ -174,6 +191,7 @@ class ParticleState:
         s.key = self.key.data_ptr()
         s.perm = self.perm.data_ptr()
         s.cell_start = self.cell_start.data_ptr()
+        s.id = None if self.id is None else self.id.data_ptr()
         return s
 
 
@@ -273,7 +291,8 @@ class Context:
     def coeff_dtype(self):
         return {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[self.coeff_format]
 
-    def new_particles(self, count: int, solid: bool = False, device="cuda") -> ParticleState:
+    def new_particles(self, count: int, solid: bool = False, device="cuda",
+                      ids: bool = False) -> ParticleState:
         R = self.num_modes
         return ParticleState(
             x=torch.empty((3, count), dtype=torch.float32, device=device),
@@ -285,6 +304,7 @@ class Context:
             mass_abs=torch.zeros(count, dtype=torch.float32, device=device) if solid else None,
             scale=(torch.zeros(count, dtype=torch.float32, device=device)
                    if self.coeff_format != "f32" else None),
+            id=torch.zeros(count, dtype=torch.int32, device=device) if ids else None,
         )
 
     def new_grid(self, device="cuda", vel=True) -> GridState:
@@ -381,6 +401,58 @@ def polypic_step(ctx: Context, fluid_in: ParticleState, fluid_out: ParticleState
                                        ref(cgs), ref(up), wp, wb, _stream(stream)), "polypic_step")
 
 
+@dataclass
+class FabricSettings:
+    """The fabric and absorption stand-ins (see polypic_fabric_params)."""
+    verts_per_side: int
+    rest_length: float
+    k_stretch: float = 0.0
+    k_shear: float = 0.0
+    k_bend: float = 0.0
+    damping: float = 0.0
+    absorb_rate: float = 0.0
+    absorb_capacity: float = 1.0
+    absorb_max_fraction: float = 0.5
+
+    def c_struct(self) -> FabricParams:
+        f = FabricParams()
+        for k in ("verts_per_side", "rest_length", "k_stretch", "k_shear", "k_bend", "damping",
+                  "absorb_rate", "absorb_capacity", "absorb_max_fraction"):
+            setattr(f, k, getattr(self, k))
+        return f
+
+
+def polypic_fabric_forces(ctx: Context, solid: ParticleState, fabric: FabricSettings, dt: float,
+                          ws: torch.Tensor, stream=None):
+    cs, cf = solid.c_struct(), fabric.c_struct()
+    wp, wb = _ws(ws)
+    _check(load_library().polypic_fabric_forces(ctx.handle, ctypes.byref(cs), ctypes.byref(cf),
+                                                float(dt), wp, wb, _stream(stream)),
+           "polypic_fabric_forces")
+
+
+def polypic_absorb(ctx: Context, fluid: ParticleState, solid: ParticleState,
+                   fabric: FabricSettings, dt: float, stream=None):
+    cfl, cs, cf = fluid.c_struct(), solid.c_struct(), fabric.c_struct()
+    _check(load_library().polypic_absorb(ctx.handle, ctypes.byref(cfl), ctypes.byref(cs),
+                                         ctypes.byref(cf), float(dt), _stream(stream)),
+           "polypic_absorb")
+
+
+def polypic_step_coupled(ctx: Context, fluid_in: ParticleState, fluid_out: ParticleState,
+                         solid_in: ParticleState, solid_out: ParticleState, gf: GridState,
+                         gs: GridState, params: UpdateSettings, fabric: FabricSettings,
+                         ws: torch.Tensor, stream=None):
+    fi, fo, si, so = (fluid_in.c_struct(), fluid_out.c_struct(), solid_in.c_struct(),
+                      solid_out.c_struct())
+    cgf, cgs, up, cf = gf.c_struct(), gs.c_struct(), params.c_struct(), fabric.c_struct()
+    wp, wb = _ws(ws)
+    _check(load_library().polypic_step_coupled(
+        ctx.handle, ctypes.byref(fi), ctypes.byref(fo), ctypes.byref(si), ctypes.byref(so),
+        ctypes.byref(cgf), ctypes.byref(cgs), ctypes.byref(up), ctypes.byref(cf), wp, wb,
+        _stream(stream)), "polypic_step_coupled")
+
+
 def polypic_g2p_adjoint(ctx: Context, g: GridState, p_in: ParticleState, dt: float,
                         bar_out: ParticleState, bar_grid: GridState, bar_in: ParticleState,
                         ws: torch.Tensor, accumulate: bool = False, stream=None):
@@ -428,12 +500,15 @@ def polypic_check_device_status(ctx: Context, stream=None) -> int:
 
 # ------------------------------------------------------------------ conveniences
 
-def upload_particles(ctx: Context, x, mass, coeff=None, mass_abs=None, device="cuda") -> ParticleState:
+def upload_particles(ctx: Context, x, mass, coeff=None, mass_abs=None, device="cuda",
+                     ids=None) -> ParticleState:
     """Copy host arrays (NumPy or torch) into a new ParticleState (FP32
     coefficients are copied as given; 16-bit contexts start from zero codes
-    and get theirs from G2P)."""
+    and get theirs from G2P; ids: the labels polypic_step_coupled carries)."""
     P = int(x.shape[1])
-    ps = ctx.new_particles(P, solid=mass_abs is not None, device=device)
+    ps = ctx.new_particles(P, solid=mass_abs is not None, device=device, ids=ids is not None)
+    if ids is not None:
+        ps.id.copy_(torch.as_tensor(np.asarray(ids).astype(np.int64).astype(np.int32)))
     ps.x.copy_(torch.as_tensor(x, dtype=torch.float32))
     ps.mass.copy_(torch.as_tensor(mass, dtype=torch.float32))
     if mass_abs is not None:
