@@ -57,7 +57,7 @@ def parse_args():
                     help="streams (each with its own device buffers) the e2e steps rotate over")
     ap.add_argument("--large-steps", type=int, default=100,
                     help="steps of the 256^3 fluid + fabric row per coefficient format")
-    ap.add_argument("--rows", default="coupled,update,projection,adjoint,large",
+    ap.add_argument("--rows", default="coupled,fabric,update,projection,adjoint,large",
                     help="the other rows of the path, each timed on its own workload")
     return ap.parse_args()
 
@@ -398,6 +398,65 @@ def run_rows(pp, torch, scenes, device, hbm, which, iters=10, warmup=3, large_st
             **gbs(nbytes, ms),
             "bytes_note": "P2G+G2P algorithmic bytes of both phases over the whole step "
                           "(sort, two P2G, drag update, two G2P)",
+            "status": pp.STATUS_NAMES.get(pp.polypic_check_device_status(ctx))}
+        del ctx, fi, si, fo, so, gf, gs, ws
+
+    if "fabric" in which:
+        # the same splash with the fabric and absorption stand-ins in the step
+        sc = scenes.splash_scene(n=128, R_fluid=27, R_solid=27)
+        m = int(sc.meta.get("sheet_vertices", 256 * 256) ** 0.5 + 0.5)
+        h = 0.8 / (m - 1)
+        ctx = pp.Context(sc.n, sc.dx, 27)
+        fi = pp.upload_particles(ctx, sc.fluid.x, sc.fluid.mass, sc.fluid.coeff, device=device)
+        si = pp.upload_particles(ctx, sc.solid.x, sc.solid.mass, None, mass_abs=sc.solid.mass_abs,
+                                 device=device, ids=np.arange(sc.solid.n))
+        fo = ctx.new_particles(fi.count, device=device)
+        so = ctx.new_particles(si.count, solid=True, device=device, ids=True)
+        gf, gs = ctx.new_grid(device=device), ctx.new_grid(device=device)
+        ws = ctx.workspace(fi.count, si.count, device=device)
+        prm = pp.UpdateSettings(dt=sc.dt, drag_k=5.0)
+        fab = pp.FabricSettings(verts_per_side=m, rest_length=h, k_stretch=20.0, k_shear=8.0,
+                                k_bend=2.0, damping=1e-4, absorb_rate=5.0, absorb_capacity=2.0,
+                                absorb_max_fraction=0.2)
+        st = {"f": (fi, fo), "s": (si, so)}
+
+        def cstep():
+            (a, b), (c, d) = st["f"], st["s"]
+            pp.polypic_step_coupled(ctx, a, b, c, d, gf, gs, prm, fab, ws, stream=stream)
+            st["f"], st["s"] = (b, a), (d, c)
+
+        def total_mass():
+            (a, _), (c, _) = st["f"], st["s"]
+            return float(a.mass.double().sum().item() + c.mass_abs.double().sum().item())
+        # 150 untimed steps first: the sphere (2 m/s, 5 cells above the sheet)
+        # reaches the sheet, so the timed steps absorb and stretch it
+        for _ in range(150 + warmup):
+            cstep()
+        m0 = total_mass()
+        ms = time_calls(torch, cstep, iters, flush, stream)
+        for _ in range(40):
+            cstep()
+        torch.cuda.synchronize()
+        m1 = total_mass()
+        (a, _), (c, _) = st["f"], st["s"]
+        ms_forces = time_calls(torch, lambda: pp.polypic_fabric_forces(ctx, c, fab, 0.0, ws,
+                                                                       stream=stream),
+                               iters, flush, stream)
+        pp.polypic_sort(ctx, a, ws, stream)
+        pp.polypic_sort(ctx, c, ws, stream)
+        ms_absorb = time_calls(torch, lambda: pp.polypic_absorb(ctx, a, c, fab, sc.dt,
+                                                                stream=stream),
+                               iters, flush, stream)
+        rows["f3_fabric_step"] = {
+            "workload": f"splash 128^3 with the stand-ins: fluid sphere {fi.count} + sheet "
+                        f"{si.count} particles ({m}^2 lattice, springs k 20/8/2 N/m, damping "
+                        "1e-4 kg/s; absorption rate 5/s, capacity 2, at most 20% of a cell's "
+                        "fluid per step), 27 modes FP32, drag K 5",
+            "ms": round(ms, 4), "value": round((fi.count + si.count) / (ms * 1e-3) / 1e6, 1),
+            "unit": UNIT, "ms_fabric_forces": round(ms_forces, 4),
+            "ms_absorb": round(ms_absorb, 4),
+            "mass_drift_rel": abs(m1 - m0) / m0, "absorbed_kg": float(c.mass_abs.double().sum()),
+            "stability": state_stats(pp, torch, c, sc.dt, sc.dx, 150 + warmup + iters + 40),
             "status": pp.STATUS_NAMES.get(pp.polypic_check_device_status(ctx))}
         del ctx, fi, si, fo, so, gf, gs, ws
 
