@@ -293,6 +293,29 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
                             const polypic_update_params *params, void *ws, size_t ws_bytes,
                             void *stream);
 
+/* Fused transfer: the G2P of step n and the P2G of step n + 1 in one pass
+ * (Section 3: only the transfers differ from the host simulator's step, so
+ * the new coefficients can feed the next P2G directly).  From the grid
+ * velocity g->vel (step n, after the update) and the sorted state `in`,
+ * writes the new positions, masses (and m_abs) of every particle to `out` in
+ * slot order, with the same bits as polypic_g2p, and the P2G of that new
+ * state -- m and mv of Eqs 1-5 and 13 with the freshly fitted coefficients --
+ * to g_next->mass and g_next->mom, without storing the coefficients of the
+ * particles that stay in their cell: out->coeff receives only those of the
+ * particles whose new position lies in another cell (the movers; the other
+ * entries are left as they were).  The movers go through `spill`, a
+ * caller-owned phase whose count is its capacity (x, mass, mass_abs when
+ * `in` has it, coeff, key, perm, cell_start): more movers than that returns
+ * POLYPIC_ERR_WORKSPACE, g_next then holding the stayers' share only.  The
+ * host reads the mover count once (a stream synchronisation).  FP32
+ * coefficients, constant map and the truncation fit only (UNSUPPORTED
+ * otherwise).  Deterministic: bit-identical from run to run (its sums run
+ * in another order than polypic_p2g's, so the two agree to rounding). */
+polypic_status polypic_g2p2g(polypic_ctx *ctx, const polypic_grid *g,
+                             const polypic_particles *in, polypic_particles *out,
+                             polypic_particles *spill, polypic_grid *g_next, float dt, void *ws,
+                             size_t ws_bytes, void *stream);
+
 /* Fabric forces (stand-in): for every vertex particle of `solid` (id <
  * m^2), with d = x_j - x_i, L = |d|, e = d / L over the lattice neighbours
  * present, f = sum k (L - L0) e + c ((v_j - v_i) . e) e, and the velocity

@@ -13,6 +13,7 @@
 #include "pcg.cuh"
 #include "adjoint.cuh"
 #include "fabric.cuh"
+#include "g2p2g.cuh"
 #include "polypic_internal.cuh"
 #include "sort.cuh"
 
@@ -432,6 +433,108 @@ polypic_status polypic_step(polypic_ctx *ctx, polypic_particles *fluid_in,
     if ((s = do_g2p(ctx, gf, fluid_in, fluid_out, params->dt, st)) != POLYPIC_OK) return s;
     if (solid && (s = do_g2p(ctx, gs, solid_in, solid_out, params->dt, st)) != POLYPIC_OK) return s;
     return POLYPIC_OK;
+}
+
+polypic_status polypic_g2p2g(polypic_ctx *ctx, const polypic_grid *g,
+                             const polypic_particles *in, polypic_particles *out,
+                             polypic_particles *spill, polypic_grid *g_next, float dt, void *ws,
+                             size_t ws_bytes, void *stream) {
+    if (!ctx) return POLYPIC_ERR_INVALID_ARG;
+    if (ctx->cfg.coeff_format != POLYPIC_COEFF_F32 || mapped(ctx) ||
+        ctx->cfg.apic_variant == POLYPIC_APIC_GRAD_W)
+        return POLYPIC_ERR_UNSUPPORTED;
+    polypic_status s;
+    if ((s = check_sorted(in)) != POLYPIC_OK) return s;
+    if ((s = check_g2p_out(ctx, in, out)) != POLYPIC_OK) return s;
+    if (!std::isfinite(dt)) return POLYPIC_ERR_INVALID_ARG;
+    if (!grid_ok(g, false, false, true) || !grid_ok(g_next, true, true, false))
+        return POLYPIC_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (g_next->mass[a] == g->vel[b] || g_next->mom[a] == g->vel[b])
+                return POLYPIC_ERR_INVALID_ARG;
+    if (!spill || spill->count < 0 || spill->count >= ((int64_t)1 << 31))
+        return POLYPIC_ERR_INVALID_ARG;
+    if (spill->count > 0 && (!spill->x[0] || !spill->x[1] || !spill->x[2] || !spill->mass ||
+                             !spill->coeff || !spill->key || !spill->perm))
+        return POLYPIC_ERR_INVALID_ARG;
+    if (!spill->cell_start || (in->mass_abs && spill->count > 0 && !spill->mass_abs))
+        return POLYPIC_ERR_INVALID_ARG;
+    if ((s = check_ws(ctx, in->count, ws, ws_bytes)) != POLYPIC_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    const int64_t tiles = ctx->num_keys / 256;
+    const int R = ctx->cfg.num_modes;
+    Workspace W{static_cast<char *>(ws), ws_bytes, 0};
+    P2GArgs P = p2g_args(ctx, in, 0.0f);
+    P.scratch = W.take<float>((size_t)tiles * kTileFloats);
+    P.tile_live = W.take<uint8_t>((size_t)tiles);
+    uint8_t *moved = W.take<uint8_t>((size_t)in->count + 1);
+    uint32_t *counts = W.take<uint32_t>((size_t)tiles);
+    uint32_t *offsets = W.take<uint32_t>((size_t)tiles + 1);
+    if (W.overflow) return POLYPIC_ERR_WORKSPACE;
+    G2P2GArgs Q{};
+    Q.p2g = P;
+    Q.x = in->x[0];
+    Q.y = in->x[1];
+    Q.z = in->x[2];
+    for (int a = 0; a < 3; ++a) Q.vel[a] = g->vel[a];
+    Q.dt = dt;
+    Q.inv1 = (float)(1.0 / ctx->cfg.dx);
+    Q.inv2 = (float)(1.0 / (ctx->cfg.dx * ctx->cfg.dx));
+    Q.ox = out->x[0];
+    Q.oy = out->x[1];
+    Q.oz = out->x[2];
+    Q.omass = out->mass;
+    Q.omass_abs = in->mass_abs ? out->mass_abs : nullptr;
+    Q.ocoeff = static_cast<float *>(out->coeff);
+    Q.moved = moved;
+    if (g2p2g_tiles(Q, R, st) != cudaSuccess) return POLYPIC_ERR_CUDA;
+    float *gm[3] = {g_next->mass[0], g_next->mass[1], g_next->mass[2]};
+    float *gp[3] = {g_next->mom[0], g_next->mom[1], g_next->mom[2]};
+    if (p2g_reduce(P, gm, gp, false, st) != cudaSuccess) return POLYPIC_ERR_CUDA;
+    if (in->count == 0) return POLYPIC_OK;
+    // the movers: a compact spill phase in slot order, sorted and added on
+    if (count_and_scan_movers(in->cell_start, moved, tiles, counts, offsets, st) != cudaSuccess)
+        return POLYPIC_ERR_CUDA;
+    SpillArgs S{};
+    S.count = in->count;
+    S.ntiles = tiles;
+    S.R = R;
+    S.capacity = (uint32_t)spill->count;
+    S.cell_start = in->cell_start;
+    S.offsets = offsets;
+    S.moved = moved;
+    S.ox = out->x[0];
+    S.oy = out->x[1];
+    S.oz = out->x[2];
+    S.omass = out->mass;
+    S.omass_abs = Q.omass_abs;
+    S.ocoeff = Q.ocoeff;
+    S.x = spill->x[0];
+    S.y = spill->x[1];
+    S.z = spill->x[2];
+    S.mass = spill->mass;
+    S.mass_abs = in->mass_abs ? spill->mass_abs : nullptr;
+    S.coeff = static_cast<float *>(spill->coeff);
+    if (compact_movers(S, st) != cudaSuccess) return POLYPIC_ERR_CUDA;
+    uint32_t total = 0;
+    if (cudaMemcpyAsync(&total, offsets + tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return POLYPIC_ERR_CUDA;
+    if ((int64_t)total > spill->count) return POLYPIC_ERR_WORKSPACE;
+    if (total == 0) return POLYPIC_OK;
+    polypic_particles sp = *spill;
+    sp.count = total;
+    sp.mass_abs = S.mass_abs;
+    sp.coeff_scale = nullptr;
+    if ((s = do_sort(ctx, &sp, ws, ws_bytes, st)) != POLYPIC_OK) return s;
+    P2GArgs P2 = p2g_args(ctx, &sp, 0.0f);
+    Workspace W2{static_cast<char *>(ws), ws_bytes, 0};
+    P2.scratch = W2.take<float>((size_t)tiles * kTileFloats);
+    P2.tile_live = W2.take<uint8_t>((size_t)tiles);
+    if (W2.overflow) return POLYPIC_ERR_WORKSPACE;
+    return from_cuda(p2g_accumulate(P2, gm, gp, R, st));
 }
 
 namespace {

@@ -98,7 +98,7 @@ __device__ __forceinline__ void reduce_node(const GridGeom &g, const uint8_t *s_
     }
     const int dX = g.n[0] + (A == 0), dY = g.n[1] + (A == 1);
     const int64_t idx = ((int64_t)k * dY + j) * dX + i;
-    if (gm) gm[idx] = sm;
+    if (gm) gm[idx] = accumulate ? gm[idx] + sm : sm;
     gp[idx] = accumulate ? gp[idx] + sv : sv;
     if (gv) {
         const int ia = A == 0 ? i : (A == 1 ? j : k);
@@ -279,6 +279,18 @@ cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], floa
     }
     if (e != cudaSuccess) return e;
     return reduce_tiles(P, gm, gp, gv, dt, gravity, false, s);
+}
+
+cudaError_t p2g_reduce(const P2GArgs &P, float *gm[3], float *gp[3], bool accumulate,
+                       cudaStream_t s) {
+    return reduce_tiles(P, gm, gp, nullptr, 0.0f, nullptr, accumulate, s);
+}
+
+cudaError_t p2g_accumulate(const P2GArgs &P, float *gm[3], float *gp[3], int R, cudaStream_t s) {
+    const int grid = (int)(P.nblocks / kP2GWarps);
+    const cudaError_t e = launch_tiles_f32(P, R, grid, s);
+    if (e != cudaSuccess) return e;
+    return reduce_tiles(P, gm, gp, nullptr, 0.0f, nullptr, true, s);
 }
 
 }  // namespace polypic

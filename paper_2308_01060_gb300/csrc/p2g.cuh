@@ -63,6 +63,12 @@ int p2g_builtin_max_tiles();
 // Writes all faces of gm[3] (mass) and gp[3] (momentum); with gv non-NULL
 // also the single-phase grid update (v = mv/m + dt g, zero on wall faces).
 // The phase is in block-interleaved slot order, read through perm.
+// Reduces the tile regions already in P.scratch into gm, gp (added to them
+// with `accumulate`).
+cudaError_t p2g_reduce(const P2GArgs &P, float *gm[3], float *gp[3], bool accumulate,
+                       cudaStream_t s);
+// FP32 P2G whose result is added to gm, gp.
+cudaError_t p2g_accumulate(const P2GArgs &P, float *gm[3], float *gp[3], int R, cudaStream_t s);
 cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], float dt,
                 const float gravity[3], int R, int fmt, cudaStream_t s);
 

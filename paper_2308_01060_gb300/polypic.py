@@ -82,6 +82,7 @@ EXPORTS = [
     "polypic_grid_update", "polypic_g2p", "polypic_step", "polypic_g2p_adjoint",
     "polypic_grid_update_adjoint", "polypic_p2g_adjoint", "polypic_check_device_status",
     "polypic_status_string", "polypic_fabric_forces", "polypic_absorb", "polypic_step_coupled",
+    "polypic_g2p2g",
 ]
 
 
@@ -122,6 +123,8 @@ def load_library(path: str = LIB_PATH):
         "polypic_p2g_adjoint": (st, [_vp, P(Particles), P(Grid), P(Particles), ctypes.c_int32, _vp,
                                      ctypes.c_size_t, _vp]),
         "polypic_check_device_status": (st, [_vp, _vp]),
+        "polypic_g2p2g": (st, [_vp, P(Grid), P(Particles), P(Particles), P(Particles), P(Grid),
+                               ctypes.c_float, _vp, ctypes.c_size_t, _vp]),
         "polypic_fabric_forces": (st, [_vp, P(Particles), P(FabricParams), ctypes.c_float, _vp,
                                        ctypes.c_size_t, _vp]),
         "polypic_absorb": (st, [_vp, P(Particles), P(Particles), P(FabricParams), ctypes.c_float,
@@ -399,6 +402,17 @@ def polypic_step(ctx: Context, fluid_in: ParticleState, fluid_out: ParticleState
     ref = lambda s: ctypes.byref(s) if s is not None else None
     _check(load_library().polypic_step(ctx.handle, ref(fi), ref(fo), ref(si), ref(so), ref(cgf),
                                        ref(cgs), ref(up), wp, wb, _stream(stream)), "polypic_step")
+
+
+def polypic_g2p2g(ctx: Context, g: GridState, p_in: ParticleState, p_out: ParticleState,
+                  spill: ParticleState, g_next: GridState, dt: float, ws: torch.Tensor,
+                  stream=None):
+    cg, ci, co, cs, cn = (g.c_struct(), p_in.c_struct(), p_out.c_struct(), spill.c_struct(),
+                          g_next.c_struct())
+    wp, wb = _ws(ws)
+    _check(load_library().polypic_g2p2g(ctx.handle, ctypes.byref(cg), ctypes.byref(ci),
+                                        ctypes.byref(co), ctypes.byref(cs), ctypes.byref(cn),
+                                        float(dt), wp, wb, _stream(stream)), "polypic_g2p2g")
 
 
 @dataclass
