@@ -49,7 +49,8 @@ def parse_args():
     ap.add_argument("--preroll", type=int, default=200,
                     help="dam-break steps with pressure projection run (untimed) before the "
                          "timed steps, so that they start from the sustained state")
-    ap.add_argument("--variants", default="graph,apic4,apic4_gradw,apic4_affine,affine27,bf16,f16")
+    ap.add_argument("--variants",
+                    default="graph,fused,apic4,apic4_gradw,apic4_affine,affine27,bf16,f16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=8)
@@ -712,6 +713,72 @@ def run_graph(pp, torch, scene, pre, R, steps, warmup, device):
             "status": pp.STATUS_NAMES.get(st)}
 
 
+def run_fused(pp, torch, scene, pre, steps, warmup, device):
+    """The fused transfer on the same workload: each step sorts, runs
+    polypic_g2p2g (G2P of step n with the P2G of step n + 1, the movers
+    through a spill phase) and the grid update, so a step's work is the same
+    as polypic_step's (one sort, one P2G, one update, one G2P per particle)
+    with the staying particles' coefficients kept out of HBM.  The timed
+    loop starts from the pre-rolled state's P2G and update; the per-phase
+    split comes from a second loop with events between the calls."""
+    ctx = pp.Context(scene.n, scene.dx, 27)
+    a, b = state_from(pp, ctx, pre, device)
+    ws = ctx.workspace(a.count, device=device)
+    spill = ctx.new_particles(a.count // 2, device=device)
+    prm = pp.UpdateSettings(dt=scene.dt)
+    stream = torch.cuda.current_stream()
+    gf, gn = ctx.new_grid(device=device), ctx.new_grid(device=device)
+    pp.polypic_sort(ctx, a, ws, stream)
+    pp.polypic_p2g(ctx, a, gf, ws, stream)
+    pp.polypic_grid_update(ctx, gf, prm, stream=stream)
+    st = {"a": a, "b": b, "g": gf, "n": gn}
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        pp.polypic_g2p2g(ctx, st["g"], st["a"], st["b"], spill, st["n"], scene.dt, ws, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        pp.polypic_grid_update(ctx, st["n"], prm, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+        pp.polypic_sort(ctx, st["b"], ws, stream)
+        if ev is not None:
+            ev[3].record(stream)
+        st["a"], st["b"], st["g"], st["n"] = st["b"], st["a"], st["n"], st["g"]
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    s0, s1 = E(), E()
+    s0.record(stream)
+    for _ in range(steps):
+        step()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1) / steps
+    evs = [[E() for _ in range(4)] for _ in range(steps)]
+    for k in range(steps):
+        step(evs[k])
+    torch.cuda.synchronize()
+    ph = np.zeros(3)
+    for e in evs:
+        ph += [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
+    ph /= steps
+    # share of particles that changed cell in the last step (state a's slots
+    # against the new positions of the same particles)
+    old, new = st["b"], st["a"]        # the last step's input (its slot order) and output
+    inv = np.float32(1.0 / scene.dx)
+    k_old = torch.floor(old.x[:, old.perm.long()] * inv)
+    k_new = torch.floor(new.x * inv)
+    moved = float((k_old != k_new).any(dim=0).float().mean().item())
+    return {"ms_per_step": ms, "value": a.count / (ms * 1e-3) / 1e6,
+            "phase_ms": {"g2p2g": round(ph[0], 4), "grid_update": round(ph[1], 4),
+                         "sort": round(ph[2], 4)},
+            "movers_share": round(moved, 4),
+            "status": pp.STATUS_NAMES.get(pp.polypic_check_device_status(ctx))}
+
+
 def run_e2e(pp, torch, scene, pre, R, steps, device, lanes=2):
     """Through the C ABI with host buffers: every step copies the particle
     state in from pinned host memory, runs polypic_step, and copies the new
@@ -913,6 +980,15 @@ def our_arm(args):
         "f16": (27, "f16", {}),
     }
     for v in [s for s in args.variants.split(",") if s]:
+        if v == "fused":
+            r = run_fused(pp, torch, scene, pre, args.steps, args.warmup, device)
+            variants[v] = {"modes": 27, "coeff_format": "f32",
+                           "note": "sort + polypic_g2p2g + grid update per step: the new "
+                                   "coefficients of particles that stay in their cell never "
+                                   "reach HBM; movers go through a spill phase (one host read "
+                                   "of their count per step)",
+                           **r, "speedup_vs_f32_step": round(ms_step / r["ms_per_step"], 3)}
+            continue
         if v == "graph":
             r = run_graph(pp, torch, scene, pre, 27, args.steps, args.warmup, device)
             variants[v] = {"modes": 27, "coeff_format": "f32",
