@@ -211,52 +211,59 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t n, const uint32_t *__re
 }
 
 // ---------------------------------------------------------------- cell order
-// Every layout deals a set of 32 cells ("lanes") round-robin: round r lists
-// the r-th particle (ascending input index, i.e. the stable order) of every
-// lane whose cell holds more than r, lanes ascending, from slot `base` on.
-// One warp per lane set.  A lane finds its cell's r-th index by selection over
-// the cell's arrival-ordered range [s0, s0 + n) (the smallest index above the
-// previous one: indices are distinct), which costs n^2 loads, so cells holding
+// The block-interleaved layout deals the 32 cells of a block round-robin:
+// round r lists the r-th particle (ascending input index, i.e. the stable
+// order) of every cell holding more than r, cells ascending, from the block's
+// first slot on.  One warp per block.  The particle in round r of cell c sits
+// at slot S(r) + |{c' < c : n_c' > r}|, S(r) = sum over the block's cells of
+// min(n, r); a warp tabulates S and the live masks once.  Each particle's
+// round is its rank in its cell: the number of smaller indices in the cell's
+// arrival-ordered range (indices are distinct).  The warp's lanes share the
+// block's particles (lane l takes l, l + 32, ...), so a warp costs the sum of
+// n^2 over its cells / 32 loads, not the fullest cell's n^2.  Cells holding
 // more than kSelectMax particles are listed for k_crowded_cells instead and
 // their slots are left to it.
-__device__ __forceinline__ void deal_rounds(const uint32_t *__restrict__ in, uint32_t k,
-                                            uint32_t s0, uint32_t n, uint32_t base,
-                                            uint32_t *__restrict__ out,
-                                            uint32_t *__restrict__ crowded,
-                                            uint32_t *__restrict__ num_crowded) {
-    const int lane = threadIdx.x & 31;
-    const bool select = n <= (uint32_t)kSelectMax;
-    if (!select) crowded[atomicAdd(num_crowded, 1u)] = k;
-    const uint32_t maxn = __reduce_max_sync(0xffffffffu, select ? n : 0u);
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t off = 0, floor_idx = 0;
-    for (uint32_t r = 0; r < maxn; ++r) {
-        const unsigned mask = __ballot_sync(0xffffffffu, n > r);
-        if (select && n > r) {
-            uint32_t best = 0xffffffffu;
-            for (uint32_t j = 0; j < n; ++j) {
-                const uint32_t e = __ldg(in + s0 + j);
-                best = (e >= floor_idx && e < best) ? e : best;
-            }
-            out[base + off + __popc(mask & lt)] = best;
-            floor_idx = best + 1u;
-        }
-        off += __popc(mask);
-    }
-}
-
-// Block-interleaved layout: lane set = the 32 keys of a block (keys ascending).
 __global__ void __launch_bounds__(256) k_cell_order(const uint32_t *__restrict__ in,
                                                     const uint32_t *__restrict__ cs,
                                                     uint32_t *__restrict__ out, uint32_t nblocks,
                                                     uint32_t *__restrict__ crowded,
                                                     uint32_t *__restrict__ num_crowded) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t b = blockIdx.x * 8 + (threadIdx.x >> 5);
+    __shared__ uint32_t s_tab[8][2][kSelectMax];
+    __shared__ uint32_t s_start[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t b = blockIdx.x * 8 + w;
     if (b >= nblocks) return;  // warp-uniform
     const uint32_t k = b * 32 + lane;
-    const uint32_t s0 = cs[k];
-    deal_rounds(in, k, s0, cs[k + 1] - s0, cs[b * 32], out, crowded, num_crowded);
+    const uint32_t s0 = cs[k], n = cs[k + 1] - s0;
+    const uint32_t base = cs[b * 32], end = cs[b * 32 + 32];
+    const bool select = n <= (uint32_t)kSelectMax;
+    if (!select) crowded[atomicAdd(num_crowded, 1u)] = k;
+    const uint32_t maxn = __reduce_max_sync(0xffffffffu, select ? n : 0u);
+    uint32_t *tabS = s_tab[w][0], *tabM = s_tab[w][1];
+    for (uint32_t r = 0; r < maxn; ++r) {
+        const uint32_t sr = __reduce_add_sync(0xffffffffu, min(n, r));
+        const uint32_t mr = __ballot_sync(0xffffffffu, n > r);
+        if (lane == 0) {
+            tabS[r] = sr;
+            tabM[r] = mr;
+        }
+    }
+    s_start[w][lane] = s0;
+    if (lane == 0) s_start[w][32] = end;
+    __syncwarp();
+    for (uint32_t i = base + lane; i < end; i += 32) {
+        // the cell of arrival slot i: the last lane whose start is <= i
+        int c = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (s_start[w][c + step] <= i) c += step;
+        const uint32_t cs0 = s_start[w][c], cn = s_start[w][c + 1] - cs0;
+        if (cn > (uint32_t)kSelectMax) continue;  // a crowded cell
+        const uint32_t e = __ldg(in + i);
+        uint32_t rank = 0;
+        for (uint32_t j = 0; j < cn; ++j) rank += __ldg(in + cs0 + j) < e ? 1u : 0u;
+        out[base + tabS[rank] + __popc(tabM[rank] & ((1u << c) - 1u))] = e;
+    }
 }
 
 // Cells holding more than kSelectMax particles, one CTA per cell: a stable
