@@ -278,15 +278,20 @@ __global__ void __launch_bounds__(1024) k_scan_movers(const uint32_t *counts, in
 
 // The movers of each tile, in slot order, to the spill set at the tile's
 // offset: positions, masses, the 3R coefficients (rows of the spill's own
-// count, the total number of movers).  Nothing is written past `capacity`.
+// count, the total number of movers).  Per chunk of 256 slots the CTA first
+// lists its movers in shared memory, then copies their coefficients with
+// every thread busy (consecutive threads write consecutive spill entries of
+// one row).  Nothing is written past `capacity`.
 __global__ void __launch_bounds__(256) k_compact_movers(SpillArgs S) {
     __shared__ uint32_t s_w[8];
+    __shared__ uint32_t s_src[256];
     const uint32_t tile = blockIdx.x;
     const uint32_t jb = S.cell_start[tile * 256], je = S.cell_start[tile * 256 + 256];
     const uint32_t total = S.offsets[S.ntiles];
     if (total > S.capacity) return;
     uint32_t next = S.offsets[tile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rows = 3 * S.R;
     for (uint32_t j0 = jb; j0 < je; j0 += 256) {
         const uint32_t j = j0 + threadIdx.x;
         const bool mv = j < je && S.moved[j];
@@ -299,14 +304,19 @@ __global__ void __launch_bounds__(256) k_compact_movers(SpillArgs S) {
             all += s_w[w];
         }
         if (mv) {
-            const uint32_t d = next + before + __popc(bal & ((1u << lane) - 1u));
+            const uint32_t i = before + __popc(bal & ((1u << lane) - 1u));
+            const uint32_t d = next + i;
+            s_src[i] = j;
             S.x[d] = S.ox[j];
             S.y[d] = S.oy[j];
             S.z[d] = S.oz[j];
             S.mass[d] = S.omass[j];
             if (S.mass_abs) S.mass_abs[d] = S.omass_abs[j];
-            for (int r = 0; r < 3 * S.R; ++r)
-                S.coeff[(int64_t)r * total + d] = S.ocoeff[(int64_t)r * S.count + j];
+        }
+        __syncthreads();
+        for (uint32_t item = threadIdx.x; item < all * (uint32_t)rows; item += 256) {
+            const uint32_t i = item % all, r = item / all;
+            S.coeff[(int64_t)r * total + next + i] = S.ocoeff[(int64_t)r * S.count + s_src[i]];
         }
         next += all;
         __syncthreads();
