@@ -188,10 +188,10 @@ def rollout(ctx: pp.Context, x0: torch.Tensor, mass: torch.Tensor, c0: torch.Ten
 
 
 def taylor_green_loss(vel: List[torch.Tensor], gmass: List[torch.Tensor],
-                      target: List[torch.Tensor]) -> torch.Tensor:
-    """L = 1/2 sum over faces with m > 0 of (v~ - u_TG)^2."""
+                      target: List[torch.Tensor], min_mass: float = 0.0) -> torch.Tensor:
+    """L = 1/2 sum over faces with m > min_mass of (v~ - u_TG)^2."""
     loss = 0.0
     for v, m, u in zip(vel, gmass, target):
-        d = torch.where(m > 0, v - u, torch.zeros_like(v))
+        d = torch.where(m > min_mass, v - u, torch.zeros_like(v))
         loss = loss + 0.5 * (d * d).sum()
     return loss

@@ -13,7 +13,8 @@ gradients with respect to the initial modes (velocity included).
   * 64^3 (~0.86M particles, the full size), opt-in with POLYPIC_FULL_ADJOINT=1
     because the FP64 oracle needs minutes on the host even with all cores:
     the GPU gradient against the oracle's chained adjoint and 4 directions of
-    central finite differences.
+    central finite differences, the loss taken over faces holding at least a
+    thousandth of a full cell's mass.
 
 The oracle runs on all host cores (its P2G and adjoint grids are per-thread
 and summed in thread order)."""
@@ -62,12 +63,13 @@ def _forward(x, mass, c, n, dx, dt, steps, keep):
     return states
 
 
-def _loss(states, target):
+def _loss(states, target, min_mass=0.0):
     _, _, gm, _, gv = states[-1]
-    return sum(0.5 * np.sum(np.where(gm[a] > 0, gv[a] - target[a], 0.0) ** 2) for a in range(3))
+    return sum(0.5 * np.sum(np.where(gm[a] > min_mass, gv[a] - target[a], 0.0) ** 2)
+               for a in range(3))
 
 
-def _gradient(states, mass, n, dx, dt, target):
+def _gradient(states, mass, n, dx, dt, target, min_mass=0.0):
     """The oracle's FP64 adjoint of its own forward, chained step by step:
     dL/dc0 (and dL/dx0, not checked here)."""
     R = states[0][1].shape[1]
@@ -76,7 +78,7 @@ def _gradient(states, mass, n, dx, dt, target):
     for i in range(len(states) - 1, -1, -1):
         x, c, gm, gp, gv = states[i]
         if i == len(states) - 1:
-            lv = [np.where(gm[a] > 0, gv[a] - target[a], 0.0) for a in range(3)]
+            lv = [np.where(gm[a] > min_mass, gv[a] - target[a], 0.0) for a in range(3)]
             lx = np.zeros((3, P))
         else:
             lv, lx = oracle.g2p_adjoint(x, gv, R, n, dx, dt, lc_next, lx_next)
@@ -86,7 +88,7 @@ def _gradient(states, mass, n, dx, dt, target):
     return lc_next
 
 
-def _gate(n, directions, seed):
+def _gate(n, directions, seed, min_mass=0.0):
     sc = scenes.random_velocity_scene(n=n, R=27, seed=seed, sigma_v=0.3, dt=1e-3, steps=STEPS)
     f = sc.fluid
     dx, dt = sc.dx, sc.dt
@@ -97,7 +99,7 @@ def _gate(n, directions, seed):
     c0 = torch.from_numpy(f.coeff).cuda().requires_grad_(True)
     tgt = [torch.from_numpy(t.astype(np.float32)).cuda() for t in target]
     vel, gmass = pag.rollout(ctx, x0, m0, c0, STEPS, dt, checkpoint_every=EVERY)
-    loss = pag.taylor_green_loss(vel, gmass, tgt)
+    loss = pag.taylor_green_loss(vel, gmass, tgt, min_mass=min_mass)
     loss.backward()
     g_gpu = np_(c0.grad).astype(np.float64)
     assert pp.polypic_check_device_status(ctx) == 0
@@ -106,9 +108,9 @@ def _gate(n, directions, seed):
     oracle.set_threads(os.cpu_count() or 1)
     try:
         states = _forward(x64, m64, c64, sc.n, dx, dt, STEPS, keep=True)
-        L0 = _loss(states, target)
+        L0 = _loss(states, target, min_mass)
         assert abs(loss.item() - L0) <= TOL * abs(L0)
-        g_or = _gradient(states, m64, sc.n, dx, dt, target)
+        g_or = _gradient(states, m64, sc.n, dx, dt, target, min_mass)
         del states
         assert_close(g_gpu, g_or, TOL_VECTOR, "dL/dc0 against the oracle's adjoint")
         # directions in velocity units: u a random unit vector of the
@@ -119,8 +121,10 @@ def _gate(n, directions, seed):
         scale = np.linalg.norm(g_or * w)
 
         def fd(d, h):
-            Lp = _loss(_forward(x64, m64, c64 + h * d, sc.n, dx, dt, STEPS, keep=False), target)
-            Lm = _loss(_forward(x64, m64, c64 - h * d, sc.n, dx, dt, STEPS, keep=False), target)
+            Lp = _loss(_forward(x64, m64, c64 + h * d, sc.n, dx, dt, STEPS, keep=False), target,
+                       min_mass)
+            Lm = _loss(_forward(x64, m64, c64 - h * d, sc.n, dx, dt, STEPS, keep=False), target,
+                       min_mass)
             return (Lp - Lm) / (2 * h)
 
         # The loss is smooth only piecewise: the quadratic modes drop to 0 when
@@ -162,4 +166,11 @@ def test_rollout_gate_16cube_32_steps_64_directions():
 @pytest.mark.skipif(os.environ.get("POLYPIC_FULL_ADJOINT") != "1",
                     reason="full-size adjoint gate: set POLYPIC_FULL_ADJOINT=1 (minutes of host time)")
 def test_rollout_gate_full_size_4_directions():
-    _gate(64, 4, seed=0)
+    # faces holding less than a thousandth of a full cell's mass are left out
+    # of the loss: there v~ = mv/m divides two sums of stencil weights at the
+    # edge of their support, and the FP32 and FP64 trajectories' velocities
+    # differ by far more than their masses do (with every face in, the
+    # gradient differs from the FP64 adjoint by 2.3e-2 norm-wise at 64^3;
+    # with this threshold by 3.6e-5, while the single-step adjoints agree to
+    # 1e-5 at this size)
+    _gate(64, 4, seed=0, min_mass=1e-3 * 1000.0 / 64 ** 3)
