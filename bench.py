@@ -185,6 +185,26 @@ def make_state(pp, ctx, scene, device):
     return a, b
 
 
+# FP32 FMAs of the sum-factorised contractions per particle-step at 27 modes:
+# P2G 81 + 81 + 108 per component (the padded 4 x 3 x 3 footprint), G2P's fit
+# 729 (27 modes x 3 components x 3 stages of 3); stencil weights, decisions
+# and addressing are not counted.
+FMA_PER_PARTICLE_STEP_27 = 3 * (81 + 81 + 108) + 729
+
+
+def alu_ceiling(torch, device, P, ph, clocks):
+    """The plain-ALU view of P2G + G2P: the counted FMAs per particle-step
+    over their time, against SMs x 128 FP32 lanes x 2 flop x the SM clock."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or clocks.get("sm_mhz") or 2070.0
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    flops = 2.0 * FMA_PER_PARTICLE_STEP_27 * P
+    achieved = flops / ((ph[1] + ph[3]) * 1e-3) / 1e12
+    return {"unit": "TFLOP/s (FP32)", "peak": round(peak, 1), "achieved": round(achieved, 2),
+            "frac": round(achieved / peak, 4), "flop_per_particle_step": 2 * FMA_PER_PARTICLE_STEP_27,
+            "note": "counted contraction FMAs only (no weights, decisions or addressing)"}
+
+
 def preroll(pp, torch, scene, steps, device):
     """The dam break run `steps` steps from rest WITH the pressure projection
     (multigrid-preconditioned CG, FP64 reductions), FP32 coefficients, 27
@@ -968,6 +988,7 @@ def our_arm(args):
         "algorithmic_bytes_per_particle": p2g_b if dominant == "p2g" else g2p_b,
         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
         else "fallback 6800 GB/s",
+        "alu_ceiling": alu_ceiling(torch, device, P, ph, clocks),
     }
 
     variants = {}

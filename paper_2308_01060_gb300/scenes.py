@@ -222,7 +222,8 @@ def splash_scene(n: int = 128, R_fluid: int = 27, R_solid: int = 27, seed: int =
                         mass_abs=np.zeros(sx.shape[1], dtype=np.float32))
     return Scene(name=f"splash_sheet_{n}^3", n=(n, n, n), dx=dx, dt=dt, steps=steps,
                  fluid=fluid, solid=solid,
-                 meta={"seed": seed, "sheet_vertices": nv, "pinned": "4 corner vertices"})
+                 meta={"seed": seed, "sheet_vertices": nv,
+                       "pinned": "none (the fabric stand-in has no constraints)"})
 
 
 def random_velocity_scene(n: int = 64, R: int = 27, seed: int = 0, sigma_v: float = 0.3,
