@@ -155,8 +155,8 @@ typedef struct polypic_update_params {
 
 /* Stand-ins for the fabric mechanics and the absorption, which the paper
  * takes from Fei et al. (Sections 3.4 and 4; Eqs 18-20 take m_abs as given).
- *   verts_per_side  m: the sheet's vertex particles carry lattice ids k m + i
- *                   (ids >= m^2: element particles, no springs)
+ *   verts_per_side  m <= 65535: the sheet's vertex particles carry lattice
+ *                   ids k m + i (ids >= m^2: element particles, no springs)
  *   rest_length     h, the lattice spacing at rest
  *   k_stretch, k_shear, k_bend  spring constants (N/m) of the springs to the
  *                   neighbours at (+-1, 0), (0, +-1); (+-1, +-1); (+-2, 0),

@@ -540,7 +540,8 @@ polypic_status polypic_g2p2g(polypic_ctx *ctx, const polypic_grid *g,
 namespace {
 
 bool fabric_ok(const polypic_fabric_params *f) {
-    return f && f->verts_per_side >= 0 && std::isfinite(f->rest_length) && f->rest_length >= 0.0f &&
+    return f && f->verts_per_side >= 0 && f->verts_per_side <= 65535 &&
+           std::isfinite(f->rest_length) && f->rest_length >= 0.0f &&
            std::isfinite(f->k_stretch) && std::isfinite(f->k_shear) && std::isfinite(f->k_bend) &&
            std::isfinite(f->damping) && std::isfinite(f->absorb_rate) &&
            f->absorb_rate >= 0.0f && std::isfinite(f->absorb_capacity) &&
