@@ -75,3 +75,13 @@ def test_host_validation_without_gpu(lib):
     assert L.polypic_p2g_mapped(None, None, None, float("nan"), None, 0, None) == 1
     assert L.polypic_p2g_noalloc(None, None, None, None) == 1
     assert L.polypic_step(None, None, None, None, None, None, None, None, None, 0, None) == 1
+    # the fused transfer, the stand-ins and the whole-update adjoint refuse a
+    # missing context before touching anything
+    assert L.polypic_g2p2g(None, None, None, None, None, None, 1e-3, None, 0, None) == 1
+    fab = pp.FabricParams()
+    assert L.polypic_fabric_forces(None, None, ctypes.byref(fab), 1e-3, None, 0, None) == 1
+    assert L.polypic_absorb(None, None, None, ctypes.byref(fab), 1e-3, None) == 1
+    assert L.polypic_step_coupled(None, None, None, None, None, None, None, None,
+                                  ctypes.byref(fab), None, 0, None) == 1
+    assert L.polypic_grid_update_adjoint(None, None, None, None, None, None, None, None, None,
+                                         None, 0, None) == 1
