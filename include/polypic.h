@@ -379,7 +379,8 @@ polypic_status polypic_g2p_adjoint(polypic_ctx *ctx, const polypic_grid *g,
  *     fields of the fluid cells, so the wall-zeroed bar_fluid_out->vel is
  *     projected exactly as the forward projects a velocity (same fluid cells
  *     from fluid_particles->cell_start, same CG to params->pcg_rtol; needs
- *     the workspace; NOT_CONVERGED as for the forward);
+ *     the workspace; NOT_CONVERGED as for the forward, and then bar_fluid_in
+ *     and bar_solid_in are not written);
  *   walls: no gradient on the wall faces;
  *   drag (solid grid, drag_k > 0, faces holding both masses): the
  *     transposed Jacobian of (v_f, v_s) -> (v_f', v_s') and the drag's
