@@ -575,7 +575,7 @@ def run_rows(pp, torch, scenes, device, hbm, which, iters=10, warmup=3, large_st
         del ctx, ps, ws, g, bar_out, bar_grid, bar_mid, bar_in
     if "large" in which:
         rows["cfg_large_fluid_fabric_256"] = run_large(pp, torch, scenes, device,
-                                                       steps=large_steps, timed=10)
+                                                       steps=large_steps, timed=10, hbm=hbm)
     del flush
     torch.cuda.empty_cache()
     return rows
@@ -601,7 +601,7 @@ def field_on_grid(torch, scene, ctx, device):
     return out
 
 
-def run_large(pp, torch, scenes, device, steps, timed):
+def run_large(pp, torch, scenes, device, steps, timed, hbm=None):
     """Large fluid + fabric at 256^3: ~64M fluid particles (the lower half-box
     at 8 per cell, a vortical initial field) and a 1024^2-vertex sheet (3.1M
     vertex and element particles), 27 modes, dt 2.5e-4, FP32 coefficients
@@ -681,9 +681,16 @@ def run_large(pp, torch, scenes, device, steps, timed):
         torch.cuda.synchronize()
         st = pp.polypic_check_device_status(ctx)
         ms = t_tr / timed
+        pb, gb = algorithmic_bytes(27, fmt)
+        nbytes = f.n * (pb + gb) + sol.n * (pb + 4 + gb + 4)   # + m_abs read and written
+        gbs = nbytes / (ms * 1e-3) / 1e9
         out[fmt] = {"ms_transfers_per_step": round(ms, 3),
                     "ms_update_and_projection_per_step": round(t_upd / timed, 3),
                     "value": round((f.n + sol.n) / (ms * 1e-3) / 1e6, 1), "unit": UNIT,
+                    "achieved_gbs": round(gbs, 1),
+                    "frac_of_peak": round(gbs / hbm, 4) if hbm else None,
+                    "bytes_note": "P2G + G2P algorithmic bytes of both phases over the "
+                                  "transfer time (the sorts included)",
                     "grid_momentum_error_vs_f32": err,
                     "stability": state_stats(pp, torch, fa, sc.dt, sc.dx, steps),
                     "status": pp.STATUS_NAMES.get(st)}
