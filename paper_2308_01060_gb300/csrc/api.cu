@@ -228,7 +228,7 @@ polypic_status do_grid_update(polypic_ctx *c, polypic_grid *fluid, polypic_grid 
     if (st != POLYPIC_OK || !u->project) return st;
     Workspace W{static_cast<char *>(ws), ws_bytes, 0};
     return pcg_project(c->geom, c->num_keys, fp->cell_start, fluid->vel, u->dt, u->rho,
-                       u->pcg_maxiter, u->pcg_rtol, c->d_status, W, s);
+                       u->pcg_maxiter, u->pcg_rtol, c->d_status, W, s, &c->pcg_graphs);
 }
 
 }  // namespace
@@ -292,6 +292,7 @@ polypic_status polypic_create(const polypic_config *cfg, polypic_ctx **out) {
 void polypic_destroy(polypic_ctx *ctx) {
     if (!ctx) return;
     if (ctx->d_status) cudaFree(ctx->d_status);
+    pcg_graphs_free(ctx->pcg_graphs);
     delete ctx;
 }
 
@@ -757,7 +758,8 @@ polypic_status polypic_grid_update_adjoint(polypic_ctx *ctx, const polypic_grid 
         if (wall_zeroed_copy(ctx->geom, bar_fluid_out->vel, lam, st) != cudaSuccess)
             return POLYPIC_ERR_CUDA;
         s = pcg_project(ctx->geom, ctx->num_keys, fluid_particles->cell_start, lam, params->dt,
-                        params->rho, params->pcg_maxiter, params->pcg_rtol, ctx->d_status, W, st);
+                        params->rho, params->pcg_maxiter, params->pcg_rtol, ctx->d_status, W, st,
+                        &ctx->pcg_graphs);
         if (s != POLYPIC_OK) return s;
         for (int a = 0; a < 3; ++a) U.lv[a] = lam[a];
     }

@@ -23,6 +23,8 @@
 // so CG keeps its guarantees.
 #include <cmath>
 
+#include <new>
+
 #include "pcg.cuh"
 
 namespace polypic {
@@ -487,9 +489,100 @@ static cudaError_t mg_vcycle(const Multigrid &M, double *partial, int nb, cudaSt
     return cudaGetLastError();
 }
 
+// Iterations it0 .. it0 + batch - 1 of the CG loop: the new direction and
+// its product with A, the step, the residual norm, the V-cycle, r . z.
+static void launch_batch(const GridGeom &g, PcgBuffers &B, const Multigrid &M, int nb, int it0,
+                         int batch, cudaStream_t s) {
+    for (int b = 0; b < batch; ++b) {
+        // directions alternate between d and d2
+        const bool odd = (it0 + b) & 1;
+        float *d_in = odd ? B.d2 : B.d, *d_out = odd ? B.d : B.d2;
+        k_apply<<<nb, kPcgThreads, 0, s>>>(g, B, d_in, d_out, it0 + b == 0);
+        k_final<<<1, kPcgThreads, 0, s>>>(B.partial, nb, B.scal, kPAp, -1);
+        k_update<<<nb, kPcgThreads, 0, s>>>(g, B, d_out);
+        k_final<<<1, kPcgThreads, 0, s>>>(B.partial, nb, B.scal, kRr, -1);
+        mg_vcycle(M, B.partial, nb, s);
+        k_final<<<1, kPcgThreads, 0, s>>>(B.partial, nb, B.scal, kRzNext, -1);
+        k_rotate<<<1, 1, 0, s>>>(B.scal);
+    }
+}
+
+// Two workspace layouts are kept (the forward projection and the adjoint's,
+// whose vectors sit behind three face arrays), the older one replaced.
+struct PcgGraphs {
+    cudaStream_t side = nullptr;   // capture stream (the caller's may be the legacy one)
+    struct Entry {
+        const float *key = nullptr;                    // B.x of the captured layout
+        cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [1]: the batch from iteration 0
+        uint64_t used = 0;
+    } entry[2];
+    uint64_t clock = 0;
+};
+
+static void drop(PcgGraphs::Entry &E) {
+    for (auto &e : E.exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+    E.key = nullptr;
+}
+
+void pcg_graphs_free(PcgGraphs *G) {
+    if (!G) return;
+    for (auto &E : G->entry) drop(E);
+    if (G->side) cudaStreamDestroy(G->side);
+    delete G;
+}
+
+// The captured graph of a full batch (kCheckEvery iterations from an even
+// iteration count), captured on first use for this workspace; nullptr if the
+// capture is not possible here (the batch is then launched directly).
+static cudaGraphExec_t batch_graph(PcgGraphs *&G, const GridGeom &g, PcgBuffers &B,
+                                   const Multigrid &M, int nb, bool first) {
+    if (!G) G = new (std::nothrow) PcgGraphs;
+    if (!G) return nullptr;
+    PcgGraphs::Entry *E = G->entry[0].key == B.x ? &G->entry[0]
+                          : G->entry[1].key == B.x ? &G->entry[1] : nullptr;
+    if (!E) {
+        E = G->entry[0].used <= G->entry[1].used ? &G->entry[0] : &G->entry[1];
+        drop(*E);
+        E->key = B.x;
+    }
+    E->used = ++G->clock;
+    cudaGraphExec_t &ex = E->exec[first ? 1 : 0];
+    if (ex) return ex;
+    if (!G->side && cudaStreamCreateWithFlags(&G->side, cudaStreamNonBlocking) != cudaSuccess) {
+        G->side = nullptr;
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaStreamBeginCapture(G->side, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    // a later batch is the loop from any even iteration count but 0: the same
+    // kernels with k_apply's `first` off
+    launch_batch(g, B, M, nb, first ? 0 : kCheckEvery, kCheckEvery, G->side);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e1 = cudaStreamEndCapture(G->side, &graph);
+    if (e1 != cudaSuccess || !graph) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) {
+        ex = nullptr;
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return ex;
+}
+
 polypic_status pcg_project(const GridGeom &g, int64_t num_keys, const uint32_t *cell_start,
                            float *vel[3], float dt, float rho, int maxiter, double rtol,
-                           uint32_t *status, Workspace &ws, cudaStream_t s) {
+                           uint32_t *status, Workspace &ws, cudaStream_t s, PcgGraphs **graphs) {
     (void)num_keys;
     const int64_t nc = (int64_t)g.n[0] * g.n[1] * g.n[2];
     PcgBuffers B;
@@ -563,17 +656,15 @@ polypic_status pcg_project(const GridGeom &g, int64_t num_keys, const uint32_t *
     int it = 0;
     while (!converged && it < maxiter) {
         const int batch = std::min(kCheckEvery, maxiter - it);
-        for (int b = 0; b < batch; ++b) {
-            // directions alternate between d and d2
-            const bool odd = (it + b) & 1;
-            float *d_in = odd ? B.d2 : B.d, *d_out = odd ? B.d : B.d2;
-            k_apply<<<nb, kPcgThreads, 0, s>>>(g, B, d_in, d_out, it + b == 0);
-            k_final<<<1, kPcgThreads, 0, s>>>(B.partial, nb, B.scal, kPAp, -1);
-            k_update<<<nb, kPcgThreads, 0, s>>>(g, B, d_out);
-            k_final<<<1, kPcgThreads, 0, s>>>(B.partial, nb, B.scal, kRr, -1);
-            mg_vcycle(M, B.partial, nb, s);
-            k_final<<<1, kPcgThreads, 0, s>>>(B.partial, nb, B.scal, kRzNext, -1);
-            k_rotate<<<1, 1, 0, s>>>(B.scal);
+        // a full batch replays its captured graph (its kernels and arguments
+        // depend only on the workspace and on whether it is the first)
+        cudaGraphExec_t ex = batch == kCheckEvery && graphs
+                                 ? batch_graph(*graphs, g, B, M, nb, it == 0)
+                                 : nullptr;
+        if (ex) {
+            if (cudaGraphLaunch(ex, s) != cudaSuccess) return POLYPIC_ERR_CUDA;
+        } else {
+            launch_batch(g, B, M, nb, it, batch, s);
         }
         if (!ok()) return POLYPIC_ERR_CUDA;
         it += batch;

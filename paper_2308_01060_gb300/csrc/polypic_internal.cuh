@@ -233,10 +233,15 @@ struct Workspace {
 }  // namespace polypic
 
 // The opaque context behind polypic_ctx.
+namespace polypic {
+struct PcgGraphs;
+}
+
 struct polypic_ctx {
     polypic_config cfg;
     polypic::GridGeom geom;
     int64_t num_keys;
     int device;
     uint32_t *d_status;   // device status word
+    polypic::PcgGraphs *pcg_graphs = nullptr;   // the projection's captured batches
 };
