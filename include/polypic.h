@@ -265,7 +265,12 @@ polypic_status polypic_p2g_noalloc(polypic_ctx *ctx, const polypic_particles *p,
  * a multigrid V-cycle on cells
  * holding fluid particles, FP64 dot products and norms) needs
  * fluid_particles->cell_start.  Writes fluid->vel (and solid->vel).
- * `solid` and `fluid_particles` may be NULL. */
+ * `solid` and `fluid_particles` may be NULL.  The projection runs its CG in
+ * batches of 8 iterations between host reads of the residual (so it cannot
+ * be captured into a CUDA graph by the caller); the context captures the
+ * batches itself once per workspace address, on a stream of its own, keeps
+ * them until polypic_destroy and replays them on `stream`.  A context must
+ * not be used by two host threads at once. */
 polypic_status polypic_grid_update(polypic_ctx *ctx, polypic_grid *fluid, polypic_grid *solid,
                                    const polypic_particles *fluid_particles,
                                    const polypic_update_params *params, void *ws,
