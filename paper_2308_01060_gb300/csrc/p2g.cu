@@ -273,7 +273,8 @@ cudaError_t p2g(const P2GArgs &P, float *gm[3], float *gp[3], float *gv[3], floa
         if (fmt != POLYPIC_COEFF_F32) return cudaErrorInvalidValue;
         e = launch_tiles_aff(P, R, grid, s);
     } else if (fmt == POLYPIC_COEFF_F32) {
-        e = launch_tiles_f32(P, R, grid, s);
+        // a solid phase (a sheet) crosses a block in few of its cells: lane teams
+        e = P.mass_abs ? launch_tiles_teams(P, R, grid, s) : launch_tiles_f32(P, R, grid, s);
     } else {
         e = launch_tiles_16(P, R, fmt, grid, s);
     }
