@@ -85,3 +85,17 @@ def test_host_validation_without_gpu(lib):
                                   ctypes.byref(fab), None, 0, None) == 1
     assert L.polypic_grid_update_adjoint(None, None, None, None, None, None, None, None, None,
                                          None, 0, None) == 1
+
+
+def test_header_is_plain_c():
+    """include/polypic.h compiles as C99 and as C++ (the ABI uses no C++ types)."""
+    import shutil
+    import subprocess
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                       "polypic.h")
+    for cc, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++17")):
+        if not shutil.which(cc):
+            pytest.skip(f"{cc} not found")
+        r = subprocess.run([cc, std, "-Wall", "-Werror", "-fsyntax-only", "-x", lang, hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
