@@ -911,18 +911,21 @@ def reference_arm(args):
     scene = scenes.dam_break_scene(n=args.n, R=27)
     f = scene.fluid
     cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
-    S = 10000 * cores
+    S = min(10000 * cores, f.n)
     x = f.x[:, :S]
     m = f.mass[:S]
     c = np.zeros((3, 27, S))
-    for _ in range(max(args.warmup, 0)):
-        oracle.step(x, m, c, scene.n, scene.dx, scene.dt)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        c_new, x_new, _ = oracle.step(x, m, c, scene.n, scene.dx, scene.dt)
-        x, c = x_new, c_new
-    el = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    try:
+        for _ in range(max(args.warmup, 0)):
+            oracle.step(x, m, c, scene.n, scene.dx, scene.dt)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            c_new, x_new, _ = oracle.step(x, m, c, scene.n, scene.dx, scene.dt)
+            x, c = x_new, c_new
+        el = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
     value = S * args.steps / el / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,

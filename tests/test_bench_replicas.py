@@ -62,3 +62,34 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with contextlib.redirect_stdout(buf):
         assert bench.reference_arm(args) == 0
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch):
+    """Rank 0 of the reference arm on a small grid: one JSON line with the
+    contract's keys, the oracle's sample no larger than the scene, and the
+    e2e and cpu_baseline objects describing the same run."""
+    import json
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--n", "16",
+                                      "--steps", "1", "--warmup", "0"])
+    args = bench.parse_args()
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        assert bench.reference_arm(args) == 0
+    lines = [ln for ln in buf.getvalue().splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 0
+    from paper_2308_01060_gb300 import scenes
+    n_scene = scenes.dam_break_scene(n=16, R=27).fluid.n
+    assert 0 < line["config"]["sample_particles_per_step"] <= n_scene
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
