@@ -1,0 +1,251 @@
+"""Mutation check of the oracle's pins.
+
+Each entry below plants one plausible mistake in a copy of
+oracle/polypic_oracle.c -- a dropped term, a flipped sign, a wrong index or
+operand, a transposed matrix, a missing guard, wall or clamp -- compiles it,
+and runs the host pins (tests/test_oracle_*.py and tests/test_slot_layout.py)
+against that copy in a child process.  Every mutant must make the pins fail:
+a mistake anywhere in the oracle's arithmetic that the pins let through would
+leave the GPU parity tests comparing against an unverified reference.  A
+control run of the unmodified copy must pass, so that a broken harness cannot
+count as a caught mutant.
+
+The mutants cover the cell key and the stable sort, the quadratic B-spline and
+its derivative, the staggered stencil and its moments (Eq 14's
+orthogonalisation), the mode order and mode values (Eq 11), P2G (Eqs 1-5, 13,
+15-18), Eq 12's affine map, the grid update (gravity, drag, walls, empty
+faces), the G2P fit with its guard and the advection clamp (Section 3.3),
+Eq 10's gradient form, the three adjoints with their position terms, the
+pressure projection, and the fabric and absorption stand-ins.
+"""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "polypic_oracle.c")
+PINS = ["tests/test_oracle_basis.py", "tests/test_oracle_transfers.py",
+        "tests/test_oracle_update_adjoint.py", "tests/test_oracle_fabric.py",
+        "tests/test_slot_layout.py"]
+
+# (name, text in polypic_oracle.c, replacement, which occurrence (0-based))
+MUTANTS = [
+    # cell key and sort
+    ("key transposed", "key[p] = (uint32_t)(((int64_t)k * ny + j) * nx + i);",
+     "key[p] = (uint32_t)(((int64_t)i * ny + j) * nz + k);", 0),
+    ("sort not stable", "for (int64_t p = 0; p < np; ++p) perm[fill[key[p]]++] = (uint32_t)p;",
+     "for (int64_t p = np - 1; p >= 0; --p) perm[fill[key[p]]++] = (uint32_t)p;", 0),
+    ("cell decided in FP64", "float v = x * inv_dx;\n    float f = floorf(v);",
+     "float f = (float)floor((double)x / (1.0 / (double)inv_dx));", 0),
+    # kernel N and dN/dr
+    ("outer weight halved", "{ double b = 1.5 - a; return 0.5 * b * b; }",
+     "{ double b = 1.5 - a; return 0.25 * b * b; }", 0),
+    ("inner derivative sign", "if (a < 0.5) return -2.0 * r;", "if (a < 0.5) return 2.0 * r;", 0),
+    ("outer derivative sign", "if (a < 1.5) return -sgn * (1.5 - a);",
+     "if (a < 1.5) return sgn * (1.5 - a);", 0),
+    # stencil, moments, basis
+    ("stagger swapped", "double X = xb / dx - (face ? 0.0 : 0.5);",
+     "double X = xb / dx - (face ? 0.5 : 0.0);", 0),
+    ("offset sign", "s->z[k] = (node - X) * dx;", "s->z[k] = (X - node) * dx;", 0),
+    ("kappa sign", "s->kappa = mu[3] / mu[2];", "s->kappa = -mu[3] / mu[2];", 0),
+    ("moment derivative sign",
+     "dmu[n] += s->dw[k] * zpow[n] - (n > 0 ? (double)n * s->w[k] * zpow[n - 1] : 0.0);",
+     "dmu[n] += s->dw[k] * zpow[n] + (n > 0 ? (double)n * s->w[k] * zpow[n - 1] : 0.0);", 0),
+    ("guard band narrowed", "s->guard = q32 < 0x1p-10f ? 1 : 0;",
+     "s->guard = q32 < 0x1p-12f ? 1 : 0;", 0),
+    ("quadratic basis constant", "return z * z - s->kappa * z - s->mu2;",
+     "return z * z - s->kappa * z + s->mu2;", 0),
+    ("basis derivative drops dkappa",
+     "return 2.0 * z * dz - s->dkappa * z - s->kappa * dz - s->dmu2;",
+     "return 2.0 * z * dz - s->kappa * dz - s->dmu2;", 0),
+    ("valid region widened", "return vx >= 1.0f && vx < (float)(nx - 1) &&",
+     "return vx >= 0.5f && vx < (float)(nx - 1) &&", 0),
+    # mode order and values
+    ("multilinear modes reordered", "{1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};",
+     "{1, 0, 1}, {1, 1, 0}, {0, 1, 1}, {1, 1, 1}};", 0),
+    ("quadratic modes in (a, b, c) order",
+     "for (int c = 0; c < 3; ++c)\n        for (int b = 0; b < 3; ++b)\n"
+     "            for (int a = 0; a < 3; ++a)",
+     "for (int a = 0; a < 3; ++a)\n        for (int b = 0; b < 3; ++b)\n"
+     "            for (int c = 0; c < 3; ++c)", 0),
+    ("mode value wrong degree", "basis_f(&st[1], g_modes[r][1], zz[1]) *",
+     "basis_f(&st[1], g_modes[r][2], zz[1]) *", 0),
+    # Eq 12 affine map
+    ("affine C transposed", "coeff[((int64_t)a * R + 1 + b) * np + p] : 0.0;",
+     "coeff[((int64_t)b * R + 1 + a) * np + p] : 0.0;", 0),
+    ("affine map transposed", "zm[i] = M[i][0] * zz[0] + M[i][1] * zz[1] + M[i][2] * zz[2];",
+     "zm[i] = M[0][i] * zz[0] + M[1][i] * zz[1] + M[2][i] * zz[2];", 0),
+    ("affine minus dt", "A[a][b] = (a == b ? 1.0 : 0.0) + dt * c;",
+     "A[a][b] = (a == b ? 1.0 : 0.0) - dt * c;", 0),
+    # P2G
+    ("P2G drops m_abs", "double mt = mass[p] + (mass_abs ? mass_abs[p] : 0.0);\n    double M[3][3];",
+     "double mt = mass[p];\n    double M[3][3];", 0),
+    ("P2G coefficient layout", "S += coeff[((int64_t)a * R + r) * np + p] * mode_value(st, r, zz);",
+     "S += coeff[((int64_t)r * 3 + a) * np + p] * mode_value(st, r, zz);", 0),
+    ("P2G mass unweighted", "gm[a][idx] += mt * w;", "gm[a][idx] += w;", 0),
+    ("P2G threads sum the wrong grid", "for (size_t i = 0; i < cnt[a]; ++i) gp[a][i] += base[cnt[a] + i];",
+     "for (size_t i = 0; i < cnt[a]; ++i) gp[a][i] += base[i];", 0),
+    # grid update
+    ("gravity sign", "vf += dt * g[a];", "vf -= dt * g[a];", 0),
+    ("drag weights swapped", "vf = mean + ms / (mf + ms) * u;", "vf = mean + mf / (mf + ms) * u;", 0),
+    ("upper wall kept", "if (ia == 0 || ia == d[a] - 1) v[((size_t)k * d[1] + j) * d[0] + i] = 0.0;",
+     "if (ia == 0) v[((size_t)k * d[1] + j) * d[0] + i] = 0.0;", 0),
+    ("empty face not zero", "double vf = fm[a][i] > 0.0 ? fp[a][i] / fm[a][i] : 0.0;",
+     "double vf = fm[a][i] > 0.0 ? fp[a][i] / fm[a][i] : 1.0;", 0),
+    # G2P fit, guard, advection, Eq 10
+    ("fit denominator unsquared", "den[r] += w * s * s;\n                        }\n"
+     "                        if (apic_grad)",
+     "den[r] += w * s;\n                        }\n                        if (apic_grad)", 0),
+    ("fit guard removed", "double c = guarded ? 0.0 : num[r] / den[r];",
+     "double c = num[r] / den[r];", 0),
+    ("fit guard on the wrong axis", "(g_modes[r][1] == 2 && st[1].guard) ||",
+     "(g_modes[r][1] == 2 && st[0].guard) ||", 0),
+    ("clamp margin", "double lo = 1.5 * dx, hi = ((double)n3[a] - 1.5) * dx;\n"
+     "            double xn = pos[a] + dt * vp[a];",
+     "double lo = 1.0 * dx, hi = ((double)n3[a] - 1.5) * dx;\n"
+     "            double xn = pos[a] + dt * vp[a];", 0),
+    ("advection sign", "double xn = pos[a] + dt * vp[a];", "double xn = pos[a] - dt * vp[a];", 0),
+    ("grad w on the wrong axis", "gradw[1] += st[0].w[kx] * st[1].dw[ky] * st[2].w[kz] * v;",
+     "gradw[1] += st[0].dw[kx] * st[1].w[ky] * st[2].w[kz] * v;", 0),
+    # P2G adjoint
+    ("P2G adjoint drops the mass", "acc_c[r] += mt * w * s * LP;", "acc_c[r] += w * s * LP;", 0),
+    ("P2G adjoint drops the mass term", "lpos[b][p] += mt * (dwb * (S * LP + LM) + w * dS * LP);",
+     "lpos[b][p] += mt * (dwb * (S * LP) + w * dS * LP);", 0),
+    ("P2G adjoint offset derivative sign", "ds *= (e == b) ? basis_df(&st[e], deg, zz[e], -1.0)",
+     "ds *= (e == b) ? basis_df(&st[e], deg, zz[e], 1.0)", 0),
+    # G2P adjoint
+    # (halving the 2 w s ds term of dden would be an equivalent mutant: summed
+    # over the stencil it vanishes, since d f_a / d x_p lies in the span of
+    # the lower-degree factors, to which f_a is orthogonal)
+    ("G2P adjoint denominator drops dw", "dden[r][b] += dwb * s * s + 2.0 * w * s * ds;",
+     "dden[r][b] += 2.0 * w * s * ds;", 0),
+    ("G2P adjoint numerator drops ds", "dnum[r][b] += (dwb * s + w * ds) * v;",
+     "dnum[r][b] += (dwb * s) * v;", 0),
+    ("G2P adjoint advection without dt", "mu[0] += dt * lpo[a][p];", "mu[0] += lpo[a][p];", 0),
+    ("G2P adjoint quotient rule sign", "lpos[b][p] += mu[r] * (dnum[r][b] - c * dden[r][b]) / den[r];",
+     "lpos[b][p] += mu[r] * (dnum[r][b] + c * dden[r][b]) / den[r];", 0),
+    ("G2P adjoint position guard removed", "if (guarded || mu[r] == 0.0) continue;",
+     "if (mu[r] == 0.0) continue;", 0),
+    ("G2P adjoint grid guard removed", "if (guarded) continue;\n                        acc +=",
+     "acc +=", 0),
+    ("G2P adjoint wrong denominator", "acc += mu[r] * w * mode_value(st, r, zz) / den[r];",
+     "acc += mu[r] * w * mode_value(st, r, zz) / den[0];", 0),
+    # pressure projection
+    ("projection rhs sign", "b[c] = -(rho * dx * dx / dt) * div;", "b[c] = (rho * dx * dx / dt) * div;", 0),
+    ("projection gradient sign", "dt / (rho * dx) * (pressure[ch] - pressure[cl]);",
+     "dt / (rho * dx) * (pressure[cl] - pressure[ch]);", 0),
+    ("Laplacian misses a neighbour", "if (k < nz - 1 && fluid[CIDX(i, j, k + 1)]) s -= src[CIDX(i, j, k + 1)];",
+     "", 0),
+    # grid update adjoint
+    ("update adjoint projection sign", "lf[a][((size_t)k * d[1] + j) * d[0] + i] += ql - qh;",
+     "lf[a][((size_t)k * d[1] + j) * d[0] + i] += qh - ql;", 0),
+    ("update adjoint divergence sign", "if (ijk[a] > 0) acc += lf", "if (ijk[a] > 0) acc -= lf", 0),
+    ("update adjoint wall faces in G^T", "if (ijk[a] + 1 < n3[a]) acc -= lf", "acc -= lf", 0),
+    ("update adjoint walls kept", "double lvf = wall ? 0.0 : lf[a][idx];", "double lvf = lf[a][idx];", 0),
+    ("update adjoint drag weights", "double lf_new = lvf * (wb + wa / Dd) + lvs * (wb - wb / Dd);",
+     "double lf_new = lvf * (wa + wb / Dd) + lvs * (wb - wb / Dd);", 0),
+    ("update adjoint drops du/dm", "dmf = lvf * (mean_f + wa_f * u + wa * u_f)",
+     "dmf = lvf * (mean_f + wa_f * u)", 0),
+    ("update adjoint mean derivative sign", "mean_s = (vs - mean) / M;", "mean_s = (mean - vs) / M;", 0),
+    ("update adjoint solid row", "double ls_new = lvf * (wa - wa / Dd) + lvs * (wa + wb / Dd);",
+     "double ls_new = lvf * (wa - wa / Dd) + lvs * (wa + wa / Dd);", 0),
+    ("update adjoint without gravity", "double vf = fp[a][idx] / mf + dt * g[a];",
+     "double vf = fp[a][idx] / mf;", 0),
+    ("update adjoint drops the drag mass term", "lsm[a][idx] = dms - lvs * sp[a][idx] / (ms * ms);",
+     "lsm[a][idx] = -lvs * sp[a][idx] / (ms * ms);", 0),
+    # fabric and absorption stand-ins
+    ("shear rest length", "double L0 = s < 4 ? h : s < 8 ? h * sqrt(2.0) : 2.0 * h;",
+     "double L0 = s < 4 ? h : s < 8 ? h : 2.0 * h;", 0),
+    ("damper sign", "f[a] += (kk * (L - L0) + damping * rv) * d[a] / L;",
+     "f[a] += (kk * (L - L0) - damping * rv) * d[a] / L;", 0),
+    ("spring direction", "d[a] = pos[a][q] - pos[a][p];", "d[a] = pos[a][p] - pos[a][q];", 0),
+    ("no bending springs", "for (int s = 0; s < 12; ++s) {", "for (int s = 0; s < 8; ++s) {", 0),
+    ("fabric ignores m_abs",
+     "double mt = mass[p] + (mass_abs ? mass_abs[p] : 0.0);\n        for (int a = 0; a < 3; ++a) dv",
+     "double mt = mass[p];\n        for (int a = 0; a < 3; ++a) dv", 0),
+    ("bending stiffness", "double kk = s < 4 ? k_stretch : s < 8 ? k_shear : k_bend;",
+     "double kk = s < 4 ? k_stretch : s < 8 ? k_shear : k_shear;", 0),
+    ("absorption taken equally", "if (D > 0.0) fmass[q] -= fmass[q] * D / Mf[c];",
+     "if (D > 0.0) fmass[q] -= D / 2.0;", 0),
+    ("absorption without capacity", "d[p] = room > 0.0 ? (want < room ? want : room) : 0.0;",
+     "d[p] = want;", 0),
+    ("absorption without the fluid limit",
+     "double D = Dd[c] < max_fraction * Mf[c] ? Dd[c] : max_fraction * Mf[c];\n"
+     "        if (D > 0.0) mass_abs",
+     "double D = Dd[c];\n        if (D > 0.0) mass_abs", 0),
+]
+
+_BOOT = ("import sys, oracle\n"
+         "oracle._SRC, oracle._LIB_PATH = sys.argv[1], sys.argv[2]\n"
+         "import pytest\n"
+         "sys.exit(pytest.main(sys.argv[3:]))\n")
+
+
+def _mutate(text, old, new, occurrence):
+    at = -1
+    for _ in range(occurrence + 1):
+        at = text.find(old, at + 1)
+        assert at >= 0, f"text not found in the oracle (occurrence {occurrence}): {old!r}"
+    return text[:at] + new + text[at + len(old):]
+
+
+def _run(workdir, source):
+    """Compile `source` in workdir and run the pins against it; returns
+    (exit code, last lines of the output)."""
+    os.makedirs(workdir, exist_ok=True)
+    src = os.path.join(workdir, "polypic_oracle.c")
+    with open(src, "w") as f:
+        f.write(source)
+    lib = os.path.join(workdir, "liboracle.so")
+    cmd = [sys.executable, "-c", _BOOT, src, lib, "-x", "-q", "-p", "no:cacheprovider",
+           "--noconftest", "-W", "ignore::pytest.PytestUnknownMarkWarning", *PINS]
+    env = dict(os.environ, OMP_NUM_THREADS="1", PYTHONDONTWRITEBYTECODE="1")
+    try:
+        r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900, env=env)
+    except subprocess.TimeoutExpired:
+        return None, "timed out"
+    tail = "\n".join((r.stdout + r.stderr).strip().splitlines()[-3:])
+    return r.returncode, tail
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    base = str(tmp_path_factory.mktemp("oracle_mutants"))
+    with open(SRC) as f:
+        text = f.read()
+    jobs = {"control": text}
+    for name, old, new, occ in MUTANTS:
+        jobs[name] = _mutate(text, old, new, occ)
+    names = list(jobs)
+    workers = max(1, min(len(names), os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {n: ex.submit(_run, os.path.join(base, f"m{i:02d}"), jobs[n])
+                for i, n in enumerate(names)}
+        res = {n: futs[n].result() for n in names}
+    shutil.rmtree(base, ignore_errors=True)
+    return res
+
+
+def test_mutants_are_distinct_and_found():
+    with open(SRC) as f:
+        text = f.read()
+    names = [m[0] for m in MUTANTS]
+    assert len(set(names)) == len(names)
+    for name, old, new, occ in MUTANTS:
+        assert old != new, name
+        assert _mutate(text, old, new, occ) != text, name
+
+
+def test_unmodified_copy_passes_the_pins(outcomes):
+    rc, tail = outcomes["control"]
+    assert rc == 0, tail
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_pins_catch_the_mutant(outcomes, name):
+    rc, tail = outcomes[name]
+    assert rc not in (0, None), f"{name}: the pins did not catch it ({tail})"

@@ -79,6 +79,34 @@ def test_key_uses_fp32_product():
     assert key[0] == (9 * 32 + 9) * 32 + i
 
 
+def test_key_rounds_the_product_in_fp32_on_a_non_power_of_two_grid():
+    """On a 48-cell axis, the largest FP32 position below each cell boundary
+    k / 48 whose FP32 product with inv_dx = 48 rounds up to k lies in cell k,
+    although the exact product is below k: the cell is the floor of the
+    product rounded once in FP32, not of the exact or FP64 quotient."""
+    from fractions import Fraction
+    n = (48, 8, 8)
+    dx = 1.0 / 48
+    inv = np.float32(48.0)
+    xs, ks = [], []
+    for k in range(2, 47):
+        x = np.float32(k / 48)
+        while Fraction(float(x)) >= Fraction(k, 48):
+            x = np.nextafter(x, np.float32(0))
+        if np.floor(x * inv) == k:                 # FP32 product rounds up
+            assert Fraction(float(x)) * 48 < k     # the exact one does not
+            xs.append(x)
+            ks.append(k)
+    assert len(xs) >= 10
+    P = len(xs)
+    y, z = np.float32(4.5 / 48), np.float32(3.5 / 48)
+    x = np.stack([np.array(xs, np.float32), np.full(P, y), np.full(P, z)])
+    key = oracle.keys(x, n, dx)
+    j, kz = int(np.floor(y * inv)), int(np.floor(z * inv))
+    assert (j, kz) == (4, 3)
+    assert np.array_equal(key, (kz * n[1] + j) * n[0] + np.array(ks))
+
+
 # --------------------------------------------------------------------- P2G
 
 @pytest.mark.parametrize("R", [1, 4, 8, 27])
@@ -329,6 +357,59 @@ def test_advection_clamps_to_margin():
     assert np.all(xn >= lo - 1e-15) and np.all(xn <= hi + 1e-15)
     # velocities carry x down, y up, z down: every particle ends on a bound
     assert np.allclose(xn[0], lo) and np.allclose(xn[1], hi) and np.allclose(xn[2], lo)
+
+
+def test_transfers_refuse_particles_outside_the_valid_region():
+    """The valid region [dx, (n - 1) dx) per axis (decided in FP32) is where
+    every 3-node stencil of every face grid lies inside that grid: at its
+    lower and upper edges the stencils touch the first and last nodes, and a
+    particle a little outside is refused by P2G, G2P and both adjoints."""
+    n = (8, 8, 8)
+    dx = 1 / 8
+    for face in (0, 1):
+        d = 8 + face
+        lo = oracle.stencil_1d(dx, dx, face)[0]
+        hi = oracle.stencil_1d(np.nextafter(np.float32(7 * dx), np.float32(0)), dx, face)[0]
+        assert lo == 0 and hi + 2 == d - 1      # inside, and no room to spare
+    inside = np.array([[dx, 4.5 * dx], [4.5 * dx, 4.5 * dx], [4.5 * dx, 6.9 * dx]])
+    oracle.p2g(inside, np.ones(2), np.zeros((3, 1, 2)), n, dx)
+    gv = [np.zeros(oracle.face_shape(a, n)) for a in range(3)]
+    for bad in (0.9 * dx, 7.05 * dx):
+        for axis in range(3):
+            x = np.full((3, 1), 4.5 * dx)
+            x[axis, 0] = bad
+            with pytest.raises(oracle.OracleError):
+                oracle.p2g(x, np.ones(1), np.zeros((3, 1, 1)), n, dx)
+            with pytest.raises(oracle.OracleError):
+                oracle.g2p(x, gv, 1, n, dx, 0.0)
+            with pytest.raises(oracle.OracleError):
+                oracle.p2g_adjoint(x, np.ones(1), np.zeros((3, 1, 1)), n, dx, gv, gv)
+            with pytest.raises(oracle.OracleError):
+                oracle.g2p_adjoint(x, gv, 1, n, dx, 0.0, np.zeros((3, 1, 1)), np.zeros((3, 1)))
+
+
+def test_empty_faces_get_zero_velocity_before_gravity():
+    """Eq 5 divides only where m > 0; a face holding no mass gets v = 0, so
+    after the update its velocity is dt g on interior faces and 0 on walls,
+    whatever its momentum entry holds (reading 11: m > 0 exactly)."""
+    rng = np.random.default_rng(42)
+    n = (6, 5, 7)
+    fm = [rng.uniform(0.5, 2, oracle.face_shape(a, n)) for a in range(3)]
+    fp = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+    empty = [rng.uniform(size=m.shape) < 0.3 for m in fm]
+    for a in range(3):
+        fm[a][empty[a]] = 0.0
+    dt, g = 2e-3, (0.5, -9.81, 1.5)
+    v = oracle.grid_update(n, dt, g, fm, fp)
+    for a in range(3):
+        idx = [slice(None)] * 3
+        idx[2 - a] = slice(1, -1)
+        inner = np.zeros(fm[a].shape, bool)
+        inner[tuple(idx)] = True
+        assert np.all(v[a][empty[a] & inner] == dt * g[a])
+        full = ~empty[a] & inner
+        assert np.allclose(v[a][full], fp[a][full] / fm[a][full] + dt * g[a], rtol=1e-15)
+        assert np.all(v[a][~inner] == 0.0)
 
 
 def test_two_phase_drag_solves_implicit_euler():
