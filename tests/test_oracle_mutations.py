@@ -1,10 +1,11 @@
 """Mutation check of the oracle's pins.
 
-Each entry below plants one plausible mistake in a copy of
-oracle/polypic_oracle.c -- a dropped term, a flipped sign, a wrong index or
-operand, a transposed matrix, a missing guard, wall or clamp -- compiles it,
-and runs the host pins (tests/test_oracle_*.py and tests/test_slot_layout.py)
-against that copy in a child process.  Every mutant must make the pins fail:
+Each entry below plants one plausible mistake in a copy of the oracle package
+-- in polypic_oracle.c, its ctypes wrappers or the all-pairs evaluator: a
+dropped term, a flipped sign, a wrong index or operand, a transposed matrix,
+a missing guard, wall or clamp -- compiles the copy, and runs the host pins
+(tests/test_oracle_*.py and tests/test_slot_layout.py) against it in a child
+process.  Every mutant must make the pins fail:
 a mistake anywhere in the oracle's arithmetic that the pins let through would
 leave the GPU parity tests comparing against an unverified reference.  A
 control run of the unmodified copy must pass, so that a broken harness cannot
@@ -179,10 +180,40 @@ MUTANTS = [
      "double D = Dd[c];\n        if (D > 0.0) mass_abs", 0),
 ]
 
-_BOOT = ("import sys, oracle\n"
-         "oracle._SRC, oracle._LIB_PATH = sys.argv[1], sys.argv[2]\n"
-         "import pytest\n"
-         "sys.exit(pytest.main(sys.argv[3:]))\n")
+# The same for the oracle's Python layer (the ctypes wrappers, the step they
+# compose, and the all-pairs NumPy evaluator the stencil oracle is pinned to):
+# (name, file in oracle/, text, replacement, which occurrence)
+PY_MUTANTS = [
+    ("grid arrays x slowest", "__init__.py", "    return (d[2], d[1], d[0])",
+     "    return (d[0], d[1], d[2])", 0),
+    ("keys with the axes swapped", "__init__.py",
+     "_p(x32[2], ctypes.c_float), int(n[0]), int(n[1]), int(n[2]),",
+     "_p(x32[2], ctypes.c_float), int(n[1]), int(n[0]), int(n[2]),", 0),
+    ("gravity components swapped", "__init__.py",
+     "float(gravity[1]), float(gravity[2]), float(drag_k),",
+     "float(gravity[2]), float(gravity[1]), float(drag_k),", 0),
+    ("step fits the momentum", "__init__.py", "    c_new, x_new = g2p(x, gv, R, n, dx, dt)",
+     "    c_new, x_new = g2p(x, gp, R, n, dx, dt)", 0),
+    ("affine map with -dt", "__init__.py",
+     "int(bool(map_affine)), float(dt), *[_p(g, D) for g in gm],",
+     "int(bool(map_affine)), float(-dt), *[_p(g, D) for g in gm],", 0),
+    ("all-pairs inner weight", "bruteforce.py", "np.where(a < 0.5, 0.75 - a * a,",
+     "np.where(a < 0.5, 0.75 - 0.5 * a * a,", 0),
+    ("all-pairs kappa inverted", "bruteforce.py", "    kappa = mu3 / mu2\n",
+     "    kappa = mu2 / mu3\n", 0),
+    ("all-pairs map transposed", "bruteforce.py", 'xi = np.einsum("bc,ckji->bkji", M, Z)',
+     'xi = np.einsum("cb,ckji->bkji", M, Z)', 0),
+    ("all-pairs C transposed", "bruteforce.py", "C[:, lin[abc]] = coeff[:, r, p]",
+     "C[lin[abc], :] = coeff[:, r, p]", 0),
+    ("all-pairs fit denominator", "bruteforce.py",
+     "den = np.tensordot(s * s, w, axes=([1, 2, 3], [0, 1, 2]))",
+     "den = np.tensordot(s, w, axes=([1, 2, 3], [0, 1, 2]))", 0),
+    ("all-pairs mode degrees swapped", "bruteforce.py",
+     'np.einsum("k,j,i->kji", ax[2][1][c], ax[1][1][b], ax[0][1][a])',
+     'np.einsum("k,j,i->kji", ax[2][1][a], ax[1][1][b], ax[0][1][c])', 0),
+]
+
+ORACLE = os.path.join(ROOT, "oracle")
 
 
 def _mutate(text, old, new, occurrence):
@@ -193,19 +224,32 @@ def _mutate(text, old, new, occurrence):
     return text[:at] + new + text[at + len(old):]
 
 
-def _run(workdir, source):
-    """Compile `source` in workdir and run the pins against it; returns
-    (exit code, last lines of the output)."""
-    os.makedirs(workdir, exist_ok=True)
-    src = os.path.join(workdir, "polypic_oracle.c")
-    with open(src, "w") as f:
-        f.write(source)
-    lib = os.path.join(workdir, "liboracle.so")
-    cmd = [sys.executable, "-c", _BOOT, src, lib, "-x", "-q", "-p", "no:cacheprovider",
-           "--noconftest", "-W", "ignore::pytest.PytestUnknownMarkWarning", *PINS]
-    env = dict(os.environ, OMP_NUM_THREADS="1", PYTHONDONTWRITEBYTECODE="1")
+def _jobs():
+    """name -> (file in oracle/, mutated text), the control first."""
+    with open(SRC) as f:
+        jobs = {"control": ("polypic_oracle.c", f.read())}
+    for name, old, new, occ in MUTANTS:
+        jobs[name] = ("polypic_oracle.c", _mutate(jobs["control"][1], old, new, occ))
+    for name, fname, old, new, occ in PY_MUTANTS:
+        with open(os.path.join(ORACLE, fname)) as f:
+            jobs[name] = (fname, _mutate(f.read(), old, new, occ))
+    return jobs
+
+
+def _run(workdir, fname, text):
+    """A copy of oracle/ in workdir with `fname` replaced by `text`, compiled
+    there; the pins run against it (first on the path) in a child process.
+    Returns (exit code, last lines of the output)."""
+    pkg = os.path.join(workdir, "oracle")
+    shutil.copytree(ORACLE, pkg, ignore=shutil.ignore_patterns("*.so", "*.tmp*", "__pycache__"))
+    with open(os.path.join(pkg, fname), "w") as f:
+        f.write(text)
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "--noconftest",
+           "-W", "ignore::pytest.PytestUnknownMarkWarning", *[os.path.join(ROOT, t) for t in PINS]]
+    env = dict(os.environ, OMP_NUM_THREADS="1", PYTHONDONTWRITEBYTECODE="1",
+               PYTHONPATH=os.pathsep.join([workdir, ROOT]))
     try:
-        r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900, env=env)
+        r = subprocess.run(cmd, cwd=workdir, capture_output=True, text=True, timeout=900, env=env)
     except subprocess.TimeoutExpired:
         return None, "timed out"
     tail = "\n".join((r.stdout + r.stderr).strip().splitlines()[-3:])
@@ -215,15 +259,11 @@ def _run(workdir, source):
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
     base = str(tmp_path_factory.mktemp("oracle_mutants"))
-    with open(SRC) as f:
-        text = f.read()
-    jobs = {"control": text}
-    for name, old, new, occ in MUTANTS:
-        jobs[name] = _mutate(text, old, new, occ)
+    jobs = _jobs()
     names = list(jobs)
     workers = max(1, min(len(names), os.cpu_count() or 1))
     with ThreadPoolExecutor(max_workers=workers) as ex:
-        futs = {n: ex.submit(_run, os.path.join(base, f"m{i:02d}"), jobs[n])
+        futs = {n: ex.submit(_run, os.path.join(base, f"m{i:02d}"), *jobs[n])
                 for i, n in enumerate(names)}
         res = {n: futs[n].result() for n in names}
     shutil.rmtree(base, ignore_errors=True)
@@ -231,13 +271,13 @@ def outcomes(tmp_path_factory):
 
 
 def test_mutants_are_distinct_and_found():
-    with open(SRC) as f:
-        text = f.read()
-    names = [m[0] for m in MUTANTS]
-    assert len(set(names)) == len(names)
-    for name, old, new, occ in MUTANTS:
-        assert old != new, name
-        assert _mutate(text, old, new, occ) != text, name
+    names = [m[0] for m in MUTANTS] + [m[0] for m in PY_MUTANTS]
+    assert len(set(names)) == len(names) and "control" not in names
+    jobs = _jobs()
+    for name in names:
+        fname, text = jobs[name]
+        with open(os.path.join(ORACLE, fname)) as f:
+            assert text != f.read(), name
 
 
 def test_unmodified_copy_passes_the_pins(outcomes):
@@ -245,7 +285,7 @@ def test_unmodified_copy_passes_the_pins(outcomes):
     assert rc == 0, tail
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS] + [m[0] for m in PY_MUTANTS])
 def test_pins_catch_the_mutant(outcomes, name):
     rc, tail = outcomes[name]
     assert rc not in (0, None), f"{name}: the pins did not catch it ({tail})"
