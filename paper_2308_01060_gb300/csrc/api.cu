@@ -461,6 +461,7 @@ polypic_status polypic_g2p2g(polypic_ctx *ctx, const polypic_grid *g,
         return POLYPIC_ERR_INVALID_ARG;
     if (!spill->cell_start || (in->mass_abs && spill->count > 0 && !spill->mass_abs))
         return POLYPIC_ERR_INVALID_ARG;
+    if (((uintptr_t)spill->coeff & 3u) != 0) return POLYPIC_ERR_INVALID_ARG;
     if ((s = check_ws(ctx, in->count, ws, ws_bytes)) != POLYPIC_OK) return s;
     cudaStream_t st = as_stream(stream);
     const int64_t tiles = ctx->num_keys / 256;
@@ -603,6 +604,7 @@ polypic_status do_absorb(polypic_ctx *c, polypic_particles *fl, polypic_particle
 
 polypic_status check_fabric_solid(polypic_ctx *c, const polypic_particles *p, bool need_id) {
     if (!p || !p->mass || (p->count > 0 && !p->coeff)) return POLYPIC_ERR_INVALID_ARG;
+    if (((uintptr_t)p->coeff & 3u) != 0) return POLYPIC_ERR_INVALID_ARG;
     if (need_id && p->count > 0 && !p->id) return POLYPIC_ERR_INVALID_ARG;
     if (c->cfg.coeff_format != POLYPIC_COEFF_F32) return POLYPIC_ERR_UNSUPPORTED;
     return POLYPIC_OK;
