@@ -99,3 +99,37 @@ def test_header_is_plain_c():
         r = subprocess.run([cc, std, "-Wall", "-Werror", "-fsyntax-only", "-x", lang, hdr],
                            capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size, field offsets and
+    field sizes that the C compiler gives the header's structures (a
+    mismatch would hand the library misread pointers)."""
+    import json
+    import subprocess
+    from paper_2308_01060_gb300 import polypic as pp
+    pairs = [("polypic_config", pp.Config), ("polypic_particles", pp.Particles),
+             ("polypic_grid", pp.Grid), ("polypic_update_params", pp.UpdateParams),
+             ("polypic_fabric_params", pp.FabricParams)]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "polypic.h"',
+             'int main(void) {', '    printf("{");']
+    for i, (cname, cls) in enumerate(pairs):
+        sep = "," if i else ""
+        lines.append(f'    printf("{sep}\\"{cname}\\": {{\\"size\\": %zu", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf(", \\"{fname}\\": [%zu, %zu]", offsetof({cname}, {fname}), '
+                         f'sizeof((({cname} *)0)->{fname}));')
+        lines.append('    printf("}");')
+    lines += ['    printf("}\\n");', '    return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-o", str(exe), str(src)], check=True)
+    got = json.loads(subprocess.run([str(exe)], check=True, capture_output=True,
+                                    text=True).stdout)
+    for cname, cls in pairs:
+        c = got[cname]
+        assert c["size"] == ctypes.sizeof(cls), cname
+        for fname, ftype in cls._fields_:
+            assert c[fname] == [getattr(cls, fname).offset, ctypes.sizeof(ftype)], (cname, fname)
