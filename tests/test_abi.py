@@ -133,3 +133,53 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert c["size"] == ctypes.sizeof(cls), cname
         for fname, ftype in cls._fields_:
             assert c[fname] == [getattr(cls, fname).offset, ctypes.sizeof(ftype)], (cname, fname)
+
+
+def _c_kind(decl):
+    """Coarse ABI class of a C parameter or return type."""
+    d = decl.strip()
+    if "*" in d or "[" in d:
+        return "ptr"
+    if d == "void":
+        return "void"
+    for key, kind in (("uint32_t", "u32"), ("int32_t", "i32"), ("int64_t", "i64"),
+                      ("size_t", "size"), ("double", "f64"), ("float", "f32"),
+                      ("polypic_status", "i32"), ("int", "i32")):
+        if re.search(rf"\b{key}\b", d):
+            return kind
+    raise AssertionError(f"unclassified C type: {decl!r}")
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return "void"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "ptr"
+    for ct, kind in ((ctypes.c_uint32, "u32"), (ctypes.c_int32, "i32"), (ctypes.c_int64, "i64"),
+                     (ctypes.c_size_t, "size"), (ctypes.c_double, "f64"),
+                     (ctypes.c_float, "f32")):
+        if t is ct:
+            return kind
+    raise AssertionError(f"unclassified ctypes type: {t!r}")
+
+
+def test_binding_signatures_match_the_header(lib):
+    """Each binding declaration has the header prototype's argument count and,
+    argument by argument, its class (pointer, 32/64-bit integer, size_t,
+    float, double), and the same return class."""
+    from paper_2308_01060_gb300 import polypic as pp
+    L = pp.load_library()
+    text = open(os.path.join(ROOT, "include", "polypic.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = re.findall(r"([A-Za-z_][\w \*]*?)\s*\b(polypic_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", text)
+    seen = set()
+    for ret, name, args in protos:
+        seen.add(name)
+        params = [a for a in (p.strip() for p in args.split(",")) if a and a != "void"]
+        fn = getattr(L, name)
+        # the parameter's type: a scalar loses its trailing name
+        want = [_c_kind(p if ("*" in p or "[" in p) else p.rsplit(None, 1)[0]) for p in params]
+        got = [_ctypes_kind(t) for t in fn.argtypes]
+        assert got == want, (name, got, want)
+        assert _ctypes_kind(fn.restype) == _c_kind(ret), (name, fn.restype, ret)
+    assert seen == set(_declared_functions())
