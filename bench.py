@@ -158,6 +158,13 @@ class ClockSampler:
 P2G_TILES_DRAM_BYTES_PER_PARTICLE = (537.27232e6 + 13.886464e6) / 1557376
 
 
+def block_cells(n: int):
+    """Cells per axis of the dam break's seeded block: [0, n/2) x [0, n) x
+    [0, n/2) clipped to the 2-cell margin at every wall."""
+    half = min(n // 2, n - 2) - 2
+    return (half, n - 4, half)
+
+
 def algorithmic_bytes(R: int, fmt: str):
     """Per particle-step bytes of the P2G and G2P calls.  P2G reads x, m and
     c; G2P reads x and writes x and c; the grid term (P2G writes of m and mv,
@@ -1063,9 +1070,11 @@ def our_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {
-                "workload": f"dam_break_{args.n}^3: {args.n // 2}x{args.n}x{args.n // 2}-cell block, "
-                            f"8 particles/cell, 27 modes, FP32 coefficients, dt 5e-4, timed "
-                            f"after {args.preroll} steps with pressure projection",
+                "workload": f"dam_break_{args.n}^3: the {args.n // 2}x{args.n}x{args.n // 2}-cell "
+                            f"corner block inside the 2-cell wall margin "
+                            f"({'x'.join(str(d) for d in block_cells(args.n))} cells), "
+                            f"8 particles/cell ({P} particles), 27 modes, FP32 coefficients, "
+                            f"dt 5e-4, timed after {args.preroll} steps with pressure projection",
                 "preroll": {"steps": args.preroll, "seconds": pre["seconds"],
                             "stability": pre["stability"]},
                 "round_efficiency": main["round_efficiency"],

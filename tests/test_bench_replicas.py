@@ -93,3 +93,12 @@ def test_reference_arm_prints_the_contract_line(monkeypatch):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+@pytest.mark.parametrize("n", [32, 128])
+def test_bench_names_the_realised_dam_break_block(n):
+    """The workload line's block (the corner block clipped to the 2-cell wall
+    margin) times 8 particles per cell is the scene's particle count."""
+    from paper_2308_01060_gb300 import scenes
+    d = bench.block_cells(n)
+    assert d[0] * d[1] * d[2] * 8 == scenes.dam_break_scene(n=n, R=1).fluid.n
