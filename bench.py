@@ -1,8 +1,9 @@
 #!/usr/bin/env python
 """Throughput of the PolyPIC transfer step on one GB300.
 
-Workload: the fluid dam break on a 128^3 grid (a 64 x 128 x 64-cell block at 8
-particles per cell, seeded inside the 2-cell margin: 3,813,248 particles), 27
+Workload: the fluid dam break on a 128^3 grid (the 64 x 128 x 64-cell corner
+block inside the 2-cell wall margin, 62 x 124 x 62 cells at 8 particles per
+cell: 3,813,248 particles), 27
 modes per velocity component, FP32 coefficients, dt = 5e-4, gravity -9.81,
 zero initial velocity.  A step is one pass of the whole transfer path through
 the C ABI: stable cell sort, P2G, grid update, G2P with advection; the
@@ -163,6 +164,14 @@ def block_cells(n: int):
     [0, n/2) clipped to the 2-cell margin at every wall."""
     half = min(n // 2, n - 2) - 2
     return (half, n - 4, half)
+
+
+def workload_name(n: int, P: int, preroll: int) -> str:
+    """The `config.workload` text of the headline line."""
+    d = "x".join(str(c) for c in block_cells(n))
+    return (f"dam_break_{n}^3: the {n // 2}x{n}x{n // 2}-cell corner block inside the 2-cell "
+            f"wall margin ({d} cells), 8 particles/cell ({P} particles), 27 modes, FP32 "
+            f"coefficients, dt 5e-4, timed after {preroll} steps with pressure projection")
 
 
 def algorithmic_bytes(R: int, fmt: str):
@@ -518,8 +527,9 @@ def run_rows(pp, torch, scenes, device, hbm, which, iters=10, warmup=3, large_st
             pr()
             ms_p = time_calls(torch, pr, 3, flush, stream)
             rows["A4_projection"] = {
-                "workload": "dam break 128^3 after 10 steps: 64x128x64 fluid cells, "
-                            "multigrid-preconditioned CG to rtol 1e-6, at most 2000 iterations",
+                "workload": "dam break 128^3 after 10 steps: about 476,656 fluid cells (the "
+                            "62x124x62-cell block), multigrid-preconditioned CG to rtol 1e-6, "
+                            "at most 2000 iterations",
                 "ms_update_and_projection": round(ms_p, 3),
                 "ms_projection": round(ms_p - ms_u, 3),
                 "note": "not in the headline step; the host reads the residual every 8 "
@@ -1070,11 +1080,7 @@ def our_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {
-                "workload": f"dam_break_{args.n}^3: the {args.n // 2}x{args.n}x{args.n // 2}-cell "
-                            f"corner block inside the 2-cell wall margin "
-                            f"({'x'.join(str(d) for d in block_cells(args.n))} cells), "
-                            f"8 particles/cell ({P} particles), 27 modes, FP32 coefficients, "
-                            f"dt 5e-4, timed after {args.preroll} steps with pressure projection",
+                "workload": workload_name(args.n, P, args.preroll),
                 "preroll": {"steps": args.preroll, "seconds": pre["seconds"],
                             "stability": pre["stability"]},
                 "round_efficiency": main["round_efficiency"],

@@ -101,4 +101,8 @@ def test_bench_names_the_realised_dam_break_block(n):
     margin) times 8 particles per cell is the scene's particle count."""
     from paper_2308_01060_gb300 import scenes
     d = bench.block_cells(n)
-    assert d[0] * d[1] * d[2] * 8 == scenes.dam_break_scene(n=n, R=1).fluid.n
+    P = scenes.dam_break_scene(n=n, R=1).fluid.n
+    assert d[0] * d[1] * d[2] * 8 == P
+    text = bench.workload_name(n, P, 200)
+    assert f"dam_break_{n}^3" in text and f"({P} particles)" in text
+    assert "x".join(map(str, d)) + " cells" in text
