@@ -40,6 +40,9 @@ MUTANTS = [
      "key[p] = (uint32_t)(((int64_t)i * ny + j) * nz + k);", 0),
     ("sort not stable", "for (int64_t p = 0; p < np; ++p) perm[fill[key[p]]++] = (uint32_t)p;",
      "for (int64_t p = np - 1; p >= 0; --p) perm[fill[key[p]]++] = (uint32_t)p;", 0),
+    ("upper clamp off by one", "if (f > (float)(n - 1)) return n - 1;",
+     "if (f > (float)(n - 1)) return n - 2;", 0),
+    ("no upper clamp", "if (f > (float)(n - 1)) return n - 1;\n", "", 0),
     ("cell decided in FP64", "float v = x * inv_dx;\n    float f = floorf(v);",
      "float f = (float)floor((double)x / (1.0 / (double)inv_dx));", 0),
     # kernel N and dN/dr

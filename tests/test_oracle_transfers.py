@@ -79,6 +79,24 @@ def test_key_uses_fp32_product():
     assert key[0] == (9 * 32 + 9) * 32 + i
 
 
+def test_key_clamps_positions_outside_the_grid():
+    """The cell is clamp(floor(x inv_dx), 0, n - 1) per axis: positions below
+    0, at or beyond n dx, and NaN land in the edge cells (0 for NaN)."""
+    n = (6, 5, 7)
+    dx = 0.25
+    inside = np.float32(2.5 * dx)
+    cases = [(-0.3 * dx, 0), (-5 * dx, 0), (np.nan, 0)]
+    for b in range(3):
+        cases_b = cases + [(n[b] * dx, n[b] - 1), ((n[b] + 3) * dx, n[b] - 1),
+                           ((n[b] - 0.5) * dx, n[b] - 1)]
+        x = np.full((3, len(cases_b)), inside, np.float32)
+        x[b] = np.array([c[0] for c in cases_b], np.float32)
+        want = np.full((3, len(cases_b)), 2)
+        want[b] = [c[1] for c in cases_b]
+        key = oracle.keys(x, n, dx)
+        assert np.array_equal(key, (want[2] * n[1] + want[1]) * n[0] + want[0]), b
+
+
 def test_key_rounds_the_product_in_fp32_on_a_non_power_of_two_grid():
     """On a 48-cell axis, the largest FP32 position below each cell boundary
     k / 48 whose FP32 product with inv_dx = 48 rounds up to k lies in cell k,
