@@ -45,6 +45,8 @@ MUTANTS = [
     ("no upper clamp", "if (f > (float)(n - 1)) return n - 1;\n", "", 0),
     ("cell decided in FP64", "float v = x * inv_dx;\n    float f = floorf(v);",
      "float f = (float)floor((double)x / (1.0 / (double)inv_dx));", 0),
+    ("cell starts miss the last cell", "for (uint32_t k = 0; k < nkeys; ++k) cell_start[k + 1] += cell_start[k];",
+     "for (uint32_t k = 0; k + 1 < nkeys; ++k) cell_start[k + 1] += cell_start[k];", 0),
     # kernel N and dN/dr
     ("outer weight halved", "{ double b = 1.5 - a; return 0.5 * b * b; }",
      "{ double b = 1.5 - a; return 0.25 * b * b; }", 0),
@@ -91,6 +93,7 @@ MUTANTS = [
     ("P2G coefficient layout", "S += coeff[((int64_t)a * R + r) * np + p] * mode_value(st, r, zz);",
      "S += coeff[((int64_t)r * 3 + a) * np + p] * mode_value(st, r, zz);", 0),
     ("P2G mass unweighted", "gm[a][idx] += mt * w;", "gm[a][idx] += w;", 0),
+    ("P2G momentum unweighted", "gp[a][idx] += mt * w * S;", "gp[a][idx] += w * S;", 0),
     ("P2G threads sum the wrong grid", "for (size_t i = 0; i < cnt[a]; ++i) gp[a][i] += base[cnt[a] + i];",
      "for (size_t i = 0; i < cnt[a]; ++i) gp[a][i] += base[i];", 0),
     # grid update
@@ -98,6 +101,7 @@ MUTANTS = [
     ("drag weights swapped", "vf = mean + ms / (mf + ms) * u;", "vf = mean + mf / (mf + ms) * u;", 0),
     ("upper wall kept", "if (ia == 0 || ia == d[a] - 1) v[((size_t)k * d[1] + j) * d[0] + i] = 0.0;",
      "if (ia == 0) v[((size_t)k * d[1] + j) * d[0] + i] = 0.0;", 0),
+    ("solid walls kept", "if (solid) wall_zero(a, d, sv[a]);", "", 0),
     ("empty face not zero", "double vf = fm[a][i] > 0.0 ? fp[a][i] / fm[a][i] : 0.0;",
      "double vf = fm[a][i] > 0.0 ? fp[a][i] / fm[a][i] : 1.0;", 0),
     # G2P fit, guard, advection, Eq 10
@@ -142,6 +146,10 @@ MUTANTS = [
     ("projection rhs sign", "b[c] = -(rho * dx * dx / dt) * div;", "b[c] = (rho * dx * dx / dt) * div;", 0),
     ("projection gradient sign", "dt / (rho * dx) * (pressure[ch] - pressure[cl]);",
      "dt / (rho * dx) * (pressure[cl] - pressure[ch]);", 0),
+    ("projection skips fluid-air faces", "if (!fluid[cl] && !fluid[ch]) continue;",
+     "if (!fluid[cl] || !fluid[ch]) continue;", 0),
+    ("Laplacian with Dirichlet walls", "diag[c] = (double)((i > 0) + (i < nx - 1) + (j > 0)",
+     "diag[c] = 6.0 + 0.0 * (double)((i > 0) + (i < nx - 1) + (j > 0)", 0),
     ("Laplacian misses a neighbour", "if (k < nz - 1 && fluid[CIDX(i, j, k + 1)]) s -= src[CIDX(i, j, k + 1)];",
      "", 0),
     # grid update adjoint

@@ -564,14 +564,23 @@ def _laplacian_matrix(n, fluid):
     return sp.csr_matrix((vals, (rows, cols)), shape=(len(cells), len(cells))), cells
 
 
-def test_pcg_projection_matches_direct_solve_and_is_divergence_free():
+@pytest.mark.parametrize("region", ["interior", "against the walls"])
+def test_pcg_projection_matches_direct_solve_and_is_divergence_free(region):
+    """The interior region meets air on every side; the corner block (a dam
+    break's column) rests on the floor and two side walls, where the walls
+    are zero-flux (no neighbour term, no diagonal entry), not p = 0."""
     import scipy.sparse.linalg as spla
     rng = np.random.default_rng(80)
     n = (12, 10, 8)
     dx, dt, rho = 1 / 12, 1e-3, 1000.0
     fluid = np.zeros((n[2], n[1], n[0]), dtype=bool)
-    fluid[1:6, 1:8, 2:10] = True
-    fluid[6, 3:5, 4:6] = True
+    if region == "interior":
+        fluid[1:6, 1:8, 2:10] = True
+        fluid[6, 3:5, 4:6] = True
+    else:
+        fluid[0:5, 0:6, 0:7] = True        # z-low, y-low (floor), x-low walls
+        fluid[5, 0:2, 0:3] = True
+        assert fluid[0].any() and fluid[:, 0].any() and fluid[:, :, 0].any()
     v = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
     for a in range(3):       # walls carry no normal velocity
         idx = [slice(None)] * 3
