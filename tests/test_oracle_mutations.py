@@ -68,6 +68,17 @@ MUTANTS = [
     ("basis derivative drops dkappa",
      "return 2.0 * z * dz - s->dkappa * z - s->kappa * dz - s->dmu2;",
      "return 2.0 * z * dz - s->kappa * dz - s->dmu2;", 0),
+    ("upper edge accepted", "vx >= 1.0f && vx < (float)(nx - 1)",
+     "vx >= 1.0f && vx <= (float)(nx - 1)", 0),
+    ("lower edge refused", "vx >= 1.0f && vx < (float)(nx - 1)",
+     "vx > 1.0f && vx < (float)(nx - 1)", 0),
+    # (flipping the sign of the mu3 dmu2 term of dkappa would be equivalent:
+    # mu2 = dx^2 / 4 at every t, so dmu2 = 0)
+    ("kappa derivative dropped",
+     "s->dkappa = (dmu[3] * mu[2] - mu[3] * dmu[2]) / (mu[2] * mu[2]);",
+     "s->dkappa = (0.0 * dmu[3] * mu[2] - mu[3] * dmu[2]) / (mu[2] * mu[2]);", 0),
+    ("basis derivative halves z^2", "return 2.0 * z * dz - s->dkappa",
+     "return z * dz - s->dkappa", 0),
     ("valid region widened", "return vx >= 1.0f && vx < (float)(nx - 1) &&",
      "return vx >= 0.5f && vx < (float)(nx - 1) &&", 0),
     # mode order and values
@@ -117,6 +128,12 @@ MUTANTS = [
      "double lo = 1.0 * dx, hi = ((double)n3[a] - 1.5) * dx;\n"
      "            double xn = pos[a] + dt * vp[a];", 0),
     ("advection sign", "double xn = pos[a] + dt * vp[a];", "double xn = pos[a] - dt * vp[a];", 0),
+    ("clamp upper margin", "double lo = 1.5 * dx, hi = ((double)n3[a] - 1.5) * dx;\n"
+     "            double xn = pos[a] + dt * vp[a];",
+     "double lo = 1.5 * dx, hi = ((double)n3[a] - 1.0) * dx;\n"
+     "            double xn = pos[a] + dt * vp[a];", 0),
+    ("grad w in shifted mode slots", "if (apic_grad && r >= 1) c = gradw[r - 1];",
+     "if (apic_grad && r >= 1) c = gradw[r % 3];", 0),
     ("grad w on the wrong axis", "gradw[1] += st[0].w[kx] * st[1].dw[ky] * st[2].w[kz] * v;",
      "gradw[1] += st[0].dw[kx] * st[1].w[ky] * st[2].w[kz] * v;", 0),
     # P2G adjoint
@@ -125,7 +142,14 @@ MUTANTS = [
      "lpos[b][p] += mt * (dwb * (S * LP) + w * dS * LP);", 0),
     ("P2G adjoint offset derivative sign", "ds *= (e == b) ? basis_df(&st[e], deg, zz[e], -1.0)",
      "ds *= (e == b) ? basis_df(&st[e], deg, zz[e], 1.0)", 0),
+    ("P2G adjoint weight derivative on the wrong axis",
+     "dwb *= (e == b) ? st[e].dw[k3[e]] : st[e].w[k3[e]];",
+     "dwb *= (e != b) ? st[e].dw[k3[e]] : st[e].w[k3[e]];", 0),
     # G2P adjoint
+    ("G2P adjoint weight derivative on the wrong axis",
+     "dwb *= (e == b) ? st[e].dw[k3[e]] : st[e].w[k3[e]];",
+     "dwb *= (e != b) ? st[e].dw[k3[e]] : st[e].w[k3[e]];", 1),
+    ("G2P adjoint ignores the clamp", "if (xn >= lo && xn <= hi) {", "if (1) {", 0),
     # (halving the 2 w s ds term of dden would be an equivalent mutant: summed
     # over the stencil it vanishes, since d f_a / d x_p lies in the span of
     # the lower-degree factors, to which f_a is orthogonal)
@@ -165,6 +189,8 @@ MUTANTS = [
     ("update adjoint mean derivative sign", "mean_s = (vs - mean) / M;", "mean_s = (mean - vs) / M;", 0),
     ("update adjoint solid row", "double ls_new = lvf * (wa - wa / Dd) + lvs * (wa + wb / Dd);",
      "double ls_new = lvf * (wa - wa / Dd) + lvs * (wa + wa / Dd);", 0),
+    ("update adjoint division sign", "lfm[a][idx] = dmf - lvf * fp[a][idx] / (mf * mf);",
+     "lfm[a][idx] = dmf + lvf * fp[a][idx] / (mf * mf);", 0),
     ("update adjoint without gravity", "double vf = fp[a][idx] / mf + dt * g[a];",
      "double vf = fp[a][idx] / mf;", 0),
     ("update adjoint drops the drag mass term", "lsm[a][idx] = dms - lvs * sp[a][idx] / (ms * ms);",

@@ -392,7 +392,7 @@ def test_transfers_refuse_particles_outside_the_valid_region():
     inside = np.array([[dx, 4.5 * dx], [4.5 * dx, 4.5 * dx], [4.5 * dx, 6.9 * dx]])
     oracle.p2g(inside, np.ones(2), np.zeros((3, 1, 2)), n, dx)
     gv = [np.zeros(oracle.face_shape(a, n)) for a in range(3)]
-    for bad in (0.9 * dx, 7.05 * dx):
+    for bad in (0.9 * dx, 7.0 * dx, 7.05 * dx):      # the upper edge itself is outside
         for axis in range(3):
             x = np.full((3, 1), 4.5 * dx)
             x[axis, 0] = bad
@@ -516,6 +516,38 @@ def test_g2p_adjoint_dot_product_and_position_fd(R):
         dxp = rng.standard_normal(x.shape)
         h = 1e-6 * dx
         fd = (J(x + h * dxp, gv) - J(x - h * dxp, gv)) / (2 * h)
+        an = np.sum(lx * dxp)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), np.abs(lx).sum() * 1e-3)
+
+
+def test_g2p_adjoint_passes_no_gradient_through_a_clamp():
+    """A particle whose advection is clamped to the margin on an axis keeps
+    x' = 1.5 dx there whatever x_p and v~ are: the adjoint passes nothing
+    through the advection on that axis (the fit's position terms stay),
+    against central differences of the clamped forward map."""
+    rng = np.random.default_rng(65)
+    n = (8, 8, 8)
+    dx, dt, R = 1 / 8, 2e-3, 4
+    P = 10
+    x = _safe_positions(rng, P, 8, eps=0.1)
+    x[0] = (1 + rng.uniform(0.62, 0.88, P)) / 8          # cell 1 along x, off the guard
+    gv = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+    gv[0] -= 50.0                                         # x + dt v_x < 1.5 dx: clamped
+    c, xo = oracle.g2p(x, gv, R, n, dx, dt)
+    assert np.all(xo[0] == 1.5 * dx) and np.all(xo[1:] > 1.5 * dx)
+    deg = scenes.mode_degrees(R)
+    mu = rng.standard_normal((3, R, P)) * (dx ** deg)[None, :, None]
+    nu = rng.standard_normal((3, P))
+
+    def J(xx):
+        cc, xx_o = oracle.g2p(xx, gv, R, n, dx, dt)
+        return np.sum(cc * mu) + np.sum(xx_o * nu)
+
+    _, lx = oracle.g2p_adjoint(x, gv, R, n, dx, dt, mu, nu)
+    for _ in range(3):
+        dxp = rng.standard_normal(x.shape)
+        h = 1e-6 * dx
+        fd = (J(x + h * dxp) - J(x - h * dxp)) / (2 * h)
         an = np.sum(lx * dxp)
         assert abs(fd - an) <= 1e-6 * max(abs(an), np.abs(lx).sum() * 1e-3)
 
