@@ -191,6 +191,9 @@ MUTANTS = [
      "double ls_new = lvf * (wa - wa / Dd) + lvs * (wa + wa / Dd);", 0),
     ("update adjoint division sign", "lfm[a][idx] = dmf - lvf * fp[a][idx] / (mf * mf);",
      "lfm[a][idx] = dmf + lvf * fp[a][idx] / (mf * mf);", 0),
+    ("update adjoint keeps the solid walls", "double lvs = (solid && !wall) ? lsv[a][idx] : 0.0;",
+     "double lvs = solid ? lsv[a][idx] : 0.0;", 0),
+    ("update adjoint through empty faces", "lfp[a][idx] = 0.0;", "lfp[a][idx] = lvf;", 0),
     ("update adjoint without gravity", "double vf = fp[a][idx] / mf + dt * g[a];",
      "double vf = fp[a][idx] / mf;", 0),
     ("update adjoint drops the drag mass term", "lsm[a][idx] = dms - lvs * sp[a][idx] / (ms * ms);",
@@ -205,6 +208,7 @@ MUTANTS = [
     ("fabric ignores m_abs",
      "double mt = mass[p] + (mass_abs ? mass_abs[p] : 0.0);\n        for (int a = 0; a < 3; ++a) dv",
      "double mt = mass[p];\n        for (int a = 0; a < 3; ++a) dv", 0),
+    ("springs on element particles", "if (id[p] >= (uint32_t)nv) continue;", "", 0),
     ("bending stiffness", "double kk = s < 4 ? k_stretch : s < 8 ? k_shear : k_bend;",
      "double kk = s < 4 ? k_stretch : s < 8 ? k_shear : k_shear;", 0),
     ("absorption taken equally", "if (D > 0.0) fmass[q] -= fmass[q] * D / Mf[c];",
@@ -234,6 +238,12 @@ PY_MUTANTS = [
     ("affine map with -dt", "__init__.py",
      "int(bool(map_affine)), float(dt), *[_p(g, D) for g in gm],",
      "int(bool(map_affine)), float(-dt), *[_p(g, D) for g in gm],", 0),
+    ("absorption limits swapped", "__init__.py",
+     "float(rate), float(capacity), float(max_fraction))",
+     "float(rate), float(max_fraction), float(capacity))", 0),
+    ("spring families swapped", "__init__.py",
+     "float(k_stretch), float(k_shear), float(k_bend),",
+     "float(k_stretch), float(k_bend), float(k_shear),", 0),
     ("all-pairs inner weight", "bruteforce.py", "np.where(a < 0.5, 0.75 - a * a,",
      "np.where(a < 0.5, 0.75 - 0.5 * a * a,", 0),
     ("all-pairs kappa inverted", "bruteforce.py", "    kappa = mu3 / mu2\n",
