@@ -1,0 +1,156 @@
+"""Property checks of the oracle over edge positions (host only).
+
+The fixed-seed pins draw positions uniformly, which almost never lands on the
+places where a stencil or a decision changes: a position exactly on a cell
+boundary or a stagger offset, one FP32 step beside it, inside the guard band
+1 - 4t^2 < 2^-10, or on the edges of the valid region.  Here Hypothesis
+(derandomised, a bounded number of examples, no example database) draws FP32
+positions that mix such edges with uniform ones, on a power-of-two grid and on
+one whose inverse spacing is not a power of two, and checks what holds at
+every position:
+
+  * the quadratic B-spline stencil: sum w = 1, sum w z = 0, mu2 = dx^2 / 4,
+    kappa = dx t (1 - 4t^2), with the lowest node decided in FP32 (where
+    that decision and the exact position disagree, to within the weight of
+    the node it leaves out, e^2 / 2 for t beyond +-1/2 by e);
+  * P2G conserves mass and the momentum of the constant mode (Eqs 1-5, 13):
+    sum_i m_i = sum_p m_p and sum_i (mv)_i = sum_p m_p c_p0 for any
+    coefficients, since every higher mode sums to zero against the weights;
+  * G2P fits an affine field exactly (Section 3.3: c_0 = v(x_p), the linear
+    modes its gradient, every other mode 0), guarded particles included.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_01060_gb300 import scenes
+
+hyp = pytest.importorskip("hypothesis")
+st = pytest.importorskip("hypothesis.strategies")
+given, settings = hyp.given, hyp.settings
+
+GRIDS = [((8, 8, 8), 1.0 / 8), ((12, 10, 9), 1.0 / 12)]
+SETTINGS = dict(max_examples=60, derandomize=True, deadline=None, database=None,
+                suppress_health_check=list(hyp.HealthCheck))
+
+
+def _valid32(x, n_axis, dx):
+    """The valid region's test as the oracle takes it: fl(x * fl(1/dx)) in
+    [1, n - 1), rounded once in FP32."""
+    v = np.float32(np.float32(x) * np.float32(1.0 / dx))
+    return bool(np.float32(1.0) <= v < np.float32(n_axis - 1))
+
+
+def _edge_positions(n_axis, dx):
+    """FP32 positions in [dx, (n - 1) dx) where something changes: cell
+    boundaries, stagger offsets (half cells), the guard band next to each
+    (t = +-1/2 on either grid), the region's lower edge and the FP32 values
+    beside each of them."""
+    out = []
+    lo, hi = np.float32(dx), np.float32((n_axis - 1) * dx)
+    for k in range(1, n_axis - 1):
+        for frac in (0.0, 0.5, 0.5 - 2e-4, 0.5 + 2e-4, 1e-4, 1 - 1e-4):
+            x = np.float32((k + frac) * dx)
+            for y in (x, np.nextafter(x, np.float32(0)), np.nextafter(x, np.float32(1))):
+                out.append(float(y))
+    for e in (lo, hi):
+        out += [float(e), float(np.nextafter(e, np.float32(0))), float(np.nextafter(e, np.float32(1)))]
+    return sorted({y for y in out if _valid32(y, n_axis, dx)})
+
+
+def _position(n_axis, dx):
+    lo, hi = float(np.float32(dx)), float(np.float32((n_axis - 1) * dx))
+    uniform = st.floats(min_value=lo, max_value=hi, width=32).filter(
+        lambda y: _valid32(y, n_axis, dx))
+    return st.one_of(uniform, st.sampled_from(_edge_positions(n_axis, dx)))
+
+
+@st.composite
+def _particles(draw, n, dx, max_p=12):
+    P = draw(st.integers(min_value=1, max_value=max_p))
+    x = np.array([[draw(_position(n[b], dx)) for _ in range(P)] for b in range(3)],
+                 dtype=np.float32)
+    return x
+
+
+@pytest.mark.parametrize("n,dx", GRIDS)
+@pytest.mark.parametrize("face", [True, False])
+def test_stencil_closed_forms_at_edge_positions(n, dx, face):
+    @settings(**SETTINGS)
+    @given(xb=_position(n[0], dx))
+    def check(xb):
+        base, w, z, mu2, kappa, _ = oracle.stencil_1d(xb, dx, face)
+        # the lowest node, decided in FP32 with one rounding per operation
+        v = np.float32(np.float32(xb) * np.float32(1.0 / dx))
+        X32 = v if face else np.float32(v - np.float32(0.5))
+        assert base == int(np.floor(np.float32(X32 - np.float32(0.5))))
+        X = xb / dx - (0.0 if face else 0.5)
+        t = X - (base + 1)
+        # Where the FP32 decision and the exact position disagree (one FP32
+        # step from a stencil boundary, on a grid whose 1/dx is not a power of
+        # two), t lies beyond +-1/2 by e and the FP64 weights over the three
+        # decided nodes miss the fourth node's N(3/2 - e) = e^2 / 2; elsewhere
+        # e = 0 and the closed forms hold to rounding.
+        e = max(0.0, abs(t) - 0.5)
+        assert e < 1e-5
+        assert abs(w.sum() - 1.0) < 1e-14 + 0.51 * e * e
+        assert abs(np.dot(w, z)) < (1e-14 + e * e) * dx
+        assert abs(mu2 - dx * dx / 4) < (1e-14 + 2 * e * e) * dx * dx
+        assert abs(kappa - dx * t * (1 - 4 * t * t)) < (1e-13 + 10 * e * e) * dx
+        assert np.allclose(z, (np.arange(3) - 1 - t) * dx, rtol=0, atol=1e-14 * dx * 16)
+
+    check()
+
+
+@pytest.mark.parametrize("n,dx", GRIDS)
+def test_p2g_conserves_mass_and_constant_mode_momentum_at_edge_positions(n, dx):
+    @settings(**SETTINGS)
+    @given(x=_particles(n, dx), R=st.sampled_from([1, 4, 8, 27]), seed=st.integers(0, 2 ** 16))
+    def check(x, R, seed):
+        rng = np.random.default_rng(seed)
+        P = x.shape[1]
+        mass = rng.uniform(0.5, 1.5, P)
+        coeff = rng.standard_normal((3, R, P)) / (dx ** scenes.mode_degrees(R))[None, :, None]
+        gm, gp = oracle.p2g(x, mass, coeff, n, dx)
+        for a in range(3):
+            assert abs(gm[a].sum() - mass.sum()) <= 1e-13 * mass.sum()
+            mom = np.dot(mass, coeff[a, 0])
+            scale = np.dot(mass, np.abs(coeff).sum(axis=1)[a] * (1 + dx) ** 2)
+            assert abs(gp[a].sum() - mom) <= 1e-12 * scale
+
+    check()
+
+
+@pytest.mark.parametrize("n,dx", GRIDS)
+def test_g2p_fits_an_affine_field_exactly_at_edge_positions(n, dx):
+    @settings(**SETTINGS)
+    @given(x=_particles(n, dx), R=st.sampled_from([4, 8, 27]), seed=st.integers(0, 2 ** 16))
+    def check(x, R, seed):
+        rng = np.random.default_rng(seed)
+        A = rng.standard_normal(3)
+        B = rng.standard_normal((3, 3))          # v_a(y) = A_a + sum_b B_ab y_b
+        gv = []
+        for a in range(3):
+            d = oracle.face_dims(a, n)
+            k, j, i = np.meshgrid(np.arange(d[2]), np.arange(d[1]), np.arange(d[0]),
+                                  indexing="ij")
+            pos = [(i + (0.0 if a == 0 else 0.5)) * dx, (j + (0.0 if a == 1 else 0.5)) * dx,
+                   (k + (0.0 if a == 2 else 0.5)) * dx]
+            gv.append(A[a] + B[a, 0] * pos[0] + B[a, 1] * pos[1] + B[a, 2] * pos[2])
+        c, _ = oracle.g2p(x, gv, R, n, dx, 0.0)
+        xp = x.astype(np.float64)
+        abc = [oracle.mode_abc(r) for r in range(R)]
+        for a in range(3):
+            v_at = A[a] + B[a] @ xp
+            assert np.allclose(c[a, 0], v_at, rtol=0, atol=1e-11)
+            for r, (da, db, dc) in enumerate(abc):
+                if r == 0:
+                    continue
+                if da + db + dc == 1 and max(da, db, dc) == 1:
+                    want = B[a, [da, db, dc].index(1)]
+                    assert np.allclose(c[a, r], want, rtol=0, atol=1e-9), (a, r)
+                else:
+                    scale = dx ** -(da + db + dc)
+                    assert np.all(np.abs(c[a, r]) <= 1e-9 * scale), (a, r)
+
+    check()
