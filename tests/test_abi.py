@@ -183,3 +183,26 @@ def test_binding_signatures_match_the_header(lib):
         assert got == want, (name, got, want)
         assert _ctypes_kind(fn.restype) == _c_kind(ret), (name, fn.restype, ret)
     assert seen == set(_declared_functions())
+
+
+def test_readme_c_example_compiles_and_links(tmp_path, lib):
+    """The plain-C usage example in README.md builds as C99 against the
+    header and links against libpolypic.so and the CUDA runtime with no
+    undefined symbol (running it needs a GPU)."""
+    import subprocess
+    readme = open(os.path.join(ROOT, "README.md")).read()
+    section = readme[readme.index("## Calling the library from C"):]
+    code = section[section.index("```c\n") + 5:]
+    code = code[:code.index("```")]
+    assert "polypic_step(" in code and "polypic_create(" in code
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("CUDA runtime headers not found")
+    src = tmp_path / "example.c"
+    src.write_text(code)
+    pkg = os.path.join(ROOT, "paper_2308_01060_gb300")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-fPIC", "-shared",
+                    "-I", os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include"),
+                    "-o", str(tmp_path / "libexample.so"), str(src),
+                    "-L", pkg, "-lpolypic", "-L", os.path.join(cuda, "lib64"), "-lcudart",
+                    "-Wl,--no-undefined"], check=True)
