@@ -17,8 +17,13 @@ every position:
     sum_i m_i = sum_p m_p and sum_i (mv)_i = sum_p m_p c_p0 for any
     coefficients, since every higher mode sums to zero against the weights;
   * G2P fits an affine field exactly (Section 3.3: c_0 = v(x_p), the linear
-    modes its gradient, every other mode 0), guarded particles included.
+    modes its gradient, every other mode 0), guarded particles included;
+  * with 27 modes, G2P then P2G gives back an arbitrary grid field wherever
+    no guard fires (the lossless transfer), right up to the guard band;
+  * both adjoints satisfy their dot-product identities at any position.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -32,6 +37,11 @@ given, settings = hyp.given, hyp.settings
 GRIDS = [((8, 8, 8), 1.0 / 8), ((12, 10, 9), 1.0 / 12)]
 SETTINGS = dict(max_examples=60, derandomize=True, deadline=None, database=None,
                 suppress_health_check=list(hyp.HealthCheck))
+
+
+def _unguarded(y, dx):
+    """No guard on this coordinate, on either kind of grid axis."""
+    return not any(oracle.stencil_1d(y, dx, face)[5] for face in (True, False))
 
 
 def _valid32(x, n_axis, dx):
@@ -49,7 +59,11 @@ def _edge_positions(n_axis, dx):
     out = []
     lo, hi = np.float32(dx), np.float32((n_axis - 1) * dx)
     for k in range(1, n_axis - 1):
-        for frac in (0.0, 0.5, 0.5 - 2e-4, 0.5 + 2e-4, 1e-4, 1 - 1e-4):
+        # t = +-1/2 sits at frac 1/2 on a face axis and at frac 0 on the
+        # others; the guard band is |t| within ~2.4e-4 of 1/2, so 1e-4 and
+        # 2e-4 lie inside it and 3e-4 just outside (the worst-conditioned fit)
+        for frac in (0.0, 0.5, 0.5 - 2e-4, 0.5 + 2e-4, 1e-4, 1 - 1e-4,
+                     0.5 - 3e-4, 0.5 + 3e-4, 3e-4, 1 - 3e-4, 0.25, 0.75):
             x = np.float32((k + frac) * dx)
             for y in (x, np.nextafter(x, np.float32(0)), np.nextafter(x, np.float32(1))):
                 out.append(float(y))
@@ -58,17 +72,22 @@ def _edge_positions(n_axis, dx):
     return sorted({y for y in out if _valid32(y, n_axis, dx)})
 
 
-def _position(n_axis, dx):
+@functools.lru_cache(maxsize=None)
+def _position(n_axis, dx, unguarded=False):
     lo, hi = float(np.float32(dx)), float(np.float32((n_axis - 1) * dx))
     uniform = st.floats(min_value=lo, max_value=hi, width=32).filter(
         lambda y: _valid32(y, n_axis, dx))
-    return st.one_of(uniform, st.sampled_from(_edge_positions(n_axis, dx)))
+    edges = _edge_positions(n_axis, dx)
+    if unguarded:
+        uniform = uniform.filter(lambda y: _unguarded(y, dx))
+        edges = [y for y in edges if _unguarded(y, dx)]
+    return st.one_of(uniform, st.sampled_from(edges))
 
 
 @st.composite
-def _particles(draw, n, dx, max_p=12):
+def _particles(draw, n, dx, max_p=12, unguarded=False):
     P = draw(st.integers(min_value=1, max_value=max_p))
-    x = np.array([[draw(_position(n[b], dx)) for _ in range(P)] for b in range(3)],
+    x = np.array([[draw(_position(n[b], dx, unguarded)) for _ in range(P)] for b in range(3)],
                  dtype=np.float32)
     return x
 
@@ -152,5 +171,66 @@ def test_g2p_fits_an_affine_field_exactly_at_edge_positions(n, dx):
                 else:
                     scale = dx ** -(da + db + dc)
                     assert np.all(np.abs(c[a, r]) <= 1e-9 * scale), (a, r)
+
+    check()
+
+
+@pytest.mark.parametrize("n,dx", GRIDS)
+def test_27_mode_round_trip_is_lossless_at_edge_positions(n, dx):
+    """Section 3.3 with 27 modes: the fit spans every function on a
+    particle's 3 x 3 x 3 stencil, so G2P then P2G (positions held) gives back
+    an arbitrary grid field -- m v~ on every face, v~ on every face that holds
+    mass -- wherever the guard leaves the quadratic modes in, however close
+    to t = +-1/2."""
+    @settings(**SETTINGS)
+    @given(x=_particles(n, dx, max_p=8, unguarded=True), seed=st.integers(0, 2 ** 16))
+    def check(x, seed):
+        rng = np.random.default_rng(seed)
+        gv = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+        mass = rng.uniform(0.5, 1.5, x.shape[1])
+        c, _ = oracle.g2p(x, gv, 27, n, dx, 0.0)
+        gm, gp = oracle.p2g(x, mass, c, n, dx)
+        M, V = mass.sum(), max(np.abs(g).max() for g in gv)
+        for a in range(3):
+            # momentum on every face: mv = m v~ (faces no particle reaches: 0)
+            assert np.allclose(gp[a], gm[a] * gv[a], rtol=0, atol=1e-13 * M * V), a
+            # velocity where the face holds real mass (a face reached only by
+            # the far tails of stencils near t = +-1/2 holds ~1e-11 of it, and
+            # mv / m there divides two such sums)
+            held = gm[a] > 1e-6 * M
+            assert np.allclose(gp[a][held] / gm[a][held], gv[a][held], rtol=0, atol=1e-10), a
+
+    check()
+
+
+@pytest.mark.parametrize("n,dx", GRIDS)
+def test_adjoint_dot_product_identities_at_edge_positions(n, dx):
+    """Both transfers are linear in what their adjoints transpose (P2G in c,
+    G2P in v~, the decisions fixed by the positions):
+    <P2G(c), (lm, lp)> - <P2G(0), lm> = <c, P2G^T lp> and
+    <G2P(v~), mu> = <v~, G2P^T mu> at any position, guarded or not."""
+    @settings(**SETTINGS)
+    @given(x=_particles(n, dx, max_p=8), R=st.sampled_from([1, 4, 8, 27]),
+           seed=st.integers(0, 2 ** 16))
+    def check(x, R, seed):
+        rng = np.random.default_rng(seed)
+        P = x.shape[1]
+        deg = scenes.mode_degrees(R)
+        mass = rng.uniform(0.5, 1.5, P)
+        coeff = rng.standard_normal((3, R, P)) / (dx ** deg)[None, :, None]
+        lm = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+        lp = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+        gm, gp = oracle.p2g(x, mass, coeff, n, dx)
+        lc, _ = oracle.p2g_adjoint(x, mass, coeff, n, dx, lm, lp)
+        lhs = sum(np.sum(gp[a] * lp[a]) for a in range(3))
+        rhs = np.sum(lc * coeff)
+        assert abs(lhs - rhs) <= 1e-11 * (np.abs(lc * coeff).sum() + 1e-300)
+        gv = [rng.standard_normal(oracle.face_shape(a, n)) for a in range(3)]
+        mu = rng.standard_normal((3, R, P)) * (dx ** deg)[None, :, None]
+        c, _ = oracle.g2p(x, gv, R, n, dx, 0.0)
+        lv, _ = oracle.g2p_adjoint(x, gv, R, n, dx, 0.0, mu, np.zeros((3, P)))
+        lhs = np.sum(c * mu)
+        rhs = sum(np.sum(lv[a] * gv[a]) for a in range(3))
+        assert abs(lhs - rhs) <= 1e-10 * (np.abs(c * mu).sum() + 1e-300)
 
     check()
